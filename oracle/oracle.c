@@ -1,0 +1,976 @@
+/* CPU oracle of the traffic microsimulation hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY: plain, slow, obviously-correct C used to check the
+ * CUDA library.  It shares no code with the library.  The product path never
+ * loads it.
+ *
+ * Source: Waddell et al., "Architecture for Modular Microsimulation of Real
+ * Estate Markets and Transportation", Sec. 6 ("Traffic microsimulation model"):
+ *   - trip planning by shortest paths under estimated link times (Sec. 6.3.1),
+ *     one tree per origin shared by its trips (Sec. 6 "Simulation scale");
+ *   - free-flow link time t0 = d / s (Eq. 4), here in integer deciseconds;
+ *   - time step dt = 0.5 s (Sec. 6.3.2);
+ *   - car following by the Intelligent Driver Model (Eq. 7);
+ *   - mandatory / discretionary lane changes with an exponential switch toward
+ *     mandatory near the exit, plus lead/lag gap acceptance (Sec. 6.3.2);
+ *   - stop signs (one vehicle at a time) and fixed-time traffic lights (Sec. 6.3.2).
+ * Where the paper is silent the readings used here are listed in the design doc
+ * ("Readings of the paper"); each is repeated at the function that applies it.
+ *
+ * Floating point: every kinematic quantity is IEEE binary32 evaluated in the
+ * written operation order; build with -ffp-contract=off (no fused multiply-add).
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OK 0
+#define EINV -1
+#define ENOMEM_ -2
+#define EUNREACH -4
+#define ESTATE -6
+
+#define CTRL_NONE 0
+#define CTRL_STOP 1
+#define CTRL_SIGNAL 2
+
+#define ST_PENDING 0
+#define ST_ACTIVE 1
+#define ST_ARRIVED 2
+
+#define TURN_THROUGH 0
+#define TURN_LEFT 1
+#define TURN_RIGHT 2
+
+struct orc_sim {
+  /* network */
+  int nn, nl;
+  int64_t *px, *py;
+  uint8_t *ctrl;
+  int32_t *off, *cyc, *grn;
+  int32_t *lf, *lt;
+  float *len, *spd;
+  int *lanes, *cls;
+  float *v0l;               /* car-following desired speed per link */
+  int *lane_base, n_lanes;  /* global lane id = lane_base[link] + lane */
+  int *in_start, *in_list;  /* in-links of each node, ascending link id */
+  int *in_index, *n_in;
+  /* parameters */
+  float dt, hdt2, len_v, s_min;
+  int dt_ds;
+  int ncls;
+  float *pv0, *pT, *pa, *pb, *ps0, *psab;
+  float mp, mathr, mbsafe, mbias, lam, stop_acq;
+  uint64_t seed;
+  int cost_mode, loop;
+  float tau[256];
+  /* demand and routes */
+  int nt;
+  int32_t *orig, *dest, *dep;
+  int32_t *roff, *rl;
+  int routed;
+  /* vehicle state, by trip id */
+  uint8_t *st;
+  int32_t *link, *lane, *cur;
+  float *x, *v;
+  int32_t *ins_step, *arr_step;
+  int8_t *dec;
+  int32_t *holder;          /* per node: trip holding a stop-controlled node, or -1 */
+  /* departure queues: trips by first link, ordered (depart_step, trip id) */
+  int32_t *q_start, *q_items, *q_head;
+  int64_t t, departed, arrived, veh_steps, active_last;
+};
+
+/* ------------------------------------------------------------------ helpers */
+static void* xcalloc(size_t n, size_t sz) { return calloc(n ? n : 1, sz ? sz : 1); }
+static size_t zsz(int n) { return n > 0 ? (size_t)n : 1; }
+
+/* Intelligent Driver Model, Eq. 7, as in Treiber et al. (2000) which Sec. 6 cites:
+ *   dv/dt = a [ 1 - (v/v0)^4 - (s*(v,dv)/s)^2 ],  s* = s0 + max(0, v T + v dv / (2 sqrt(a b))).
+ * Reading: the printed "v dv / 2 sqrt(ab)" is the quotient v dv / (2 sqrt(ab)); the
+ * dynamic part of s* is floored at 0; dv = v - v_lead; the gap s is floored at s_min.
+ * No leader: the interaction term is 0.  Fixed binary32 operation order. */
+static float idm_acc(float a, float sab, float T, float s0, float v0, float s_min,
+                     float s, float v, float vl, int has_leader) {
+  float r = v / v0;
+  float r2 = r * r;
+  float r4 = r2 * r2;
+  float q2 = 0.0f;
+  if (has_leader) {
+    float dv = v - vl;
+    float t1 = v * T;
+    float t2 = (v * dv) / (2.0f * sab);
+    float dyn = t1 + t2;
+    float ss = s0 + fmaxf(0.0f, dyn);
+    float se = fmaxf(s, s_min);
+    float q = ss / se;
+    q2 = q * q;
+  }
+  return a * ((1.0f - r4) - q2);
+}
+
+float orc_idm(float a, float b, float T, float s0, float v0, float s_min,
+              float s, float v, float v_lead, int has_leader) {
+  float sab = sqrtf(a * b);
+  return idm_acc(a, sab, T, s0, v0, s_min, s, v, v_lead, has_leader);
+}
+
+/* Position/speed update over one step (Sec. 6.3.2 gives dt only).  Reading: the
+ * ballistic scheme of Treiber & Kanagaraj (2015): v' = v + a dt; if v' >= 0 then
+ * x' = x + v dt + a dt^2/2, otherwise the vehicle stops inside the step:
+ * x' = x - v^2 / (2 a), v' = 0. */
+static void ballistic(float x, float v, float acc, float dt, float hdt2, float* xo, float* vo) {
+  float vn = v + acc * dt;
+  if (vn >= 0.0f) {
+    float d1 = v * dt;
+    float d2 = acc * hdt2;
+    *xo = x + (d1 + d2);
+    *vo = vn;
+  } else {
+    float den = 2.0f * acc;
+    float dx = -((v * v) / den);
+    *xo = x + dx;
+    *vo = 0.0f;
+  }
+}
+
+void orc_ballistic(float x, float v, float acc, float dt, float* x_out, float* v_out) {
+  float hdt2 = (0.5f * dt) * dt;
+  ballistic(x, v, acc, dt, hdt2, x_out, v_out);
+}
+
+/* Free-flow link time, Eq. 4 (t0 = d / s seconds), as integer deciseconds rounded
+ * half up and at least 1.  Mode 1 uses the routing weight of Sec. 6.3.1,
+ * sqrt(lanes) * length / speed, in the same units. */
+int32_t orc_link_cost(float length_m, float speed_mps, int lanes, int mode) {
+  double d = (double)length_m, s = (double)speed_mps;
+  double t = (mode == 1) ? ((10.0 * sqrt((double)lanes)) * d) / s : (10.0 * d) / s;
+  double c = floor(t + 0.5);
+  if (c < 1.0) c = 1.0;
+  if (c > 2.0e9) c = 2.0e9;
+  return (int32_t)c;
+}
+
+/* SplitMix64 finaliser (Steele, Lea & Flood 2014) of seed ^ (vid << 32 | hop);
+ * the top 8 bits index the mandatory-switch table. */
+uint32_t orc_mand_index(uint64_t seed, int32_t vid, int32_t hop) {
+  uint64_t z = seed ^ ((((uint64_t)(uint32_t)vid) << 32) | (uint64_t)(uint32_t)hop);
+  z += 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  z = z ^ (z >> 31);
+  return (uint32_t)(z >> 56);
+}
+
+/* Mandatory switch (Sec. 6.3.2): a vehicle on the wrong lane turns mandatory with
+ * probability exp(-(d/lambda)^2) at remaining distance d.  With one uniform draw u
+ * per (vehicle, link), it is mandatory once d <= lambda sqrt(-ln u).  u is quantised
+ * to 256 levels (k + 0.5) / 256 so that the threshold is a table lookup. */
+float orc_mand_tau(int k) {
+  return (float)sqrt(-log(((double)k + 0.5) / 256.0));
+}
+
+/* Turn class of the movement a->b->c from integer node positions (exact int64):
+ * through when the heading changes by less than 45 degrees, else left (counter-
+ * clockwise, and U-turns) or right. */
+int orc_turn(int64_t ax, int64_t ay, int64_t bx, int64_t by, int64_t cx, int64_t cy) {
+  int64_t d1x = bx - ax, d1y = by - ay, d2x = cx - bx, d2y = cy - by;
+  int64_t cr = d1x * d2y - d1y * d2x;
+  int64_t dot = d1x * d2x + d1y * d2y;
+  int64_t acr = cr < 0 ? -cr : cr;
+  if (dot > acr) return TURN_THROUGH;
+  if (cr < 0) return TURN_RIGHT;
+  return TURN_LEFT;
+}
+
+/* Fixed-time two-phase signal (Sec. 6.3.2 "traffic lights"; the grid workload
+ * fixes 30 s green / 30 s red): phase time p = (t dt - offset) mod cycle in
+ * deciseconds; north-south approaches are green for p < green, east-west otherwise. */
+int orc_signal_green(int64_t t, int32_t dt_ds, int32_t offset, int32_t cycle, int32_t green, int ew) {
+  int64_t p = (t * (int64_t)dt_ds - (int64_t)offset) % (int64_t)cycle;
+  if (p < 0) p += cycle;
+  int ns_green = p < (int64_t)green;
+  return ew ? !ns_green : ns_green;
+}
+
+/* Dijkstra with a binary heap (the plain definition of single-source shortest
+ * paths; Sec. 6 "Simulation scale" builds one tree per source). */
+typedef struct { int64_t d; int32_t v; } hent;
+static void heap_push(hent* h, int64_t* n, hent e) {
+  int64_t i = (*n)++;
+  h[i] = e;
+  while (i > 0) {
+    int64_t p = (i - 1) / 2;
+    if (h[p].d <= h[i].d) break;
+    hent tmp = h[p]; h[p] = h[i]; h[i] = tmp;
+    i = p;
+  }
+}
+static hent heap_pop(hent* h, int64_t* n) {
+  hent top = h[0];
+  h[0] = h[--(*n)];
+  int64_t i = 0;
+  for (;;) {
+    int64_t l = 2 * i + 1, r = l + 1, m = i;
+    if (l < *n && h[l].d < h[m].d) m = l;
+    if (r < *n && h[r].d < h[m].d) m = r;
+    if (m == i) break;
+    hent tmp = h[m]; h[m] = h[i]; h[i] = tmp;
+    i = m;
+  }
+  return top;
+}
+
+static int dijkstra(int nn, const int* out_start, const int* out_list, const int32_t* lt,
+                    const int32_t* cost, int origin, int64_t* dist, hent* heap) {
+  for (int i = 0; i < nn; i++) dist[i] = INT64_MAX;
+  int64_t hn = 0;
+  dist[origin] = 0;
+  heap_push(heap, &hn, (hent){0, origin});
+  while (hn > 0) {
+    hent e = heap_pop(heap, &hn);
+    if (e.d != dist[e.v]) continue;
+    for (int k = out_start[e.v]; k < out_start[e.v + 1]; k++) {
+      int l = out_list[k];
+      int64_t nd = e.d + cost[l];
+      if (nd < dist[lt[l]]) {
+        dist[lt[l]] = nd;
+        heap_push(heap, &hn, (hent){nd, lt[l]});
+      }
+    }
+  }
+  return OK;
+}
+
+static void build_csr(int n, int m, const int32_t* key, int* start, int* list) {
+  for (int i = 0; i <= n; i++) start[i] = 0;
+  for (int e = 0; e < m; e++) start[key[e] + 1]++;
+  for (int i = 0; i < n; i++) start[i + 1] += start[i];
+  int* fill = (int*)xcalloc(zsz(n), sizeof(int));
+  for (int e = 0; e < m; e++) list[start[key[e]] + fill[key[e]]++] = e; /* ascending link id */
+  free(fill);
+}
+
+int orc_sssp(int32_t n_nodes, int32_t n_links, const int32_t* from, const int32_t* to,
+             const int32_t* cost, int32_t origin, int64_t* dist) {
+  if (n_nodes <= 0 || origin < 0 || origin >= n_nodes) return EINV;
+  int* os = (int*)xcalloc((size_t)n_nodes + 1, sizeof(int));
+  int* ol = (int*)xcalloc((size_t)n_links, sizeof(int));
+  hent* heap = (hent*)xcalloc((size_t)n_links + 1, sizeof(hent));
+  build_csr(n_nodes, n_links, from, os, ol);
+  dijkstra(n_nodes, os, ol, to, cost, origin, dist, heap);
+  free(os); free(ol); free(heap);
+  return OK;
+}
+
+/* ------------------------------------------------------------------ create */
+int orc_create(const orc_network* N, const orc_demand* D, const orc_params* P, orc_sim** out) {
+  if (!N || !D || !P || !out) return EINV;
+  if (N->n_nodes <= 0 || N->n_links <= 0 || D->n_trips < 0) return EINV;
+  if (P->n_class <= 0 || !(P->dt > 0.0f)) return EINV;
+  int dt_ds = (int)lrintf(P->dt * 10.0f);
+  if (dt_ds <= 0 || fabsf((float)dt_ds - P->dt * 10.0f) > 1e-3f) return EINV;
+  orc_sim* S = (orc_sim*)xcalloc(1, sizeof(orc_sim));
+  int nn = N->n_nodes, nl = N->n_links;
+  S->nn = nn; S->nl = nl;
+  S->px = (int64_t*)xcalloc(nn, 8); S->py = (int64_t*)xcalloc(nn, 8);
+  S->ctrl = (uint8_t*)xcalloc(nn, 1);
+  S->off = (int32_t*)xcalloc(nn, 4); S->cyc = (int32_t*)xcalloc(nn, 4); S->grn = (int32_t*)xcalloc(nn, 4);
+  for (int i = 0; i < nn; i++) {
+    S->px[i] = N->node_x_dm[i]; S->py[i] = N->node_y_dm[i];
+    S->ctrl[i] = N->node_control[i];
+    S->off[i] = N->signal_offset_ds[i]; S->cyc[i] = N->signal_cycle_ds[i]; S->grn[i] = N->signal_green_ds[i];
+    if (S->ctrl[i] > 2 || (S->ctrl[i] == CTRL_SIGNAL && S->cyc[i] <= 0)) { orc_destroy(S); return EINV; }
+  }
+  S->lf = (int32_t*)xcalloc(nl, 4); S->lt = (int32_t*)xcalloc(nl, 4);
+  S->len = (float*)xcalloc(nl, 4); S->spd = (float*)xcalloc(nl, 4);
+  S->lanes = (int*)xcalloc(nl, sizeof(int)); S->cls = (int*)xcalloc(nl, sizeof(int));
+  S->v0l = (float*)xcalloc(nl, 4);
+  S->lane_base = (int*)xcalloc(nl + 1, sizeof(int));
+  S->ncls = P->n_class;
+  S->pv0 = (float*)xcalloc(S->ncls, 4); S->pT = (float*)xcalloc(S->ncls, 4);
+  S->pa = (float*)xcalloc(S->ncls, 4); S->pb = (float*)xcalloc(S->ncls, 4);
+  S->ps0 = (float*)xcalloc(S->ncls, 4); S->psab = (float*)xcalloc(S->ncls, 4);
+  for (int c = 0; c < S->ncls; c++) {
+    S->pv0[c] = P->v0[c]; S->pT[c] = P->T[c]; S->pa[c] = P->a[c]; S->pb[c] = P->b[c]; S->ps0[c] = P->s0[c];
+    if (!(S->pa[c] > 0.0f) || !(S->pb[c] > 0.0f) || !(S->pT[c] >= 0.0f) || !(S->ps0[c] >= 0.0f)) { orc_destroy(S); return EINV; }
+    S->psab[c] = sqrtf(S->pa[c] * S->pb[c]);
+  }
+  int nlanes = 0;
+  for (int e = 0; e < nl; e++) {
+    S->lf[e] = N->link_from[e]; S->lt[e] = N->link_to[e];
+    S->len[e] = N->link_length_m[e]; S->spd[e] = N->link_speed_mps[e];
+    S->lanes[e] = N->link_lanes[e]; S->cls[e] = N->link_class[e];
+    if (S->lf[e] < 0 || S->lf[e] >= nn || S->lt[e] < 0 || S->lt[e] >= nn || S->lanes[e] < 1 || S->lanes[e] > 8 ||
+        !(S->len[e] > 0.0f) || !(S->spd[e] > 0.0f) || S->cls[e] >= S->ncls) { orc_destroy(S); return EINV; }
+    S->v0l[e] = S->pv0[S->cls[e]] > 0.0f ? S->pv0[S->cls[e]] : S->spd[e];
+    S->lane_base[e] = nlanes;
+    nlanes += S->lanes[e];
+  }
+  S->lane_base[nl] = nlanes;
+  S->n_lanes = nlanes;
+  S->in_start = (int*)xcalloc(nn + 1, sizeof(int)); S->in_list = (int*)xcalloc(nl, sizeof(int));
+  build_csr(nn, nl, S->lt, S->in_start, S->in_list);
+  S->in_index = (int*)xcalloc(nl, sizeof(int)); S->n_in = (int*)xcalloc(nn, sizeof(int));
+  for (int n = 0; n < nn; n++) {
+    S->n_in[n] = S->in_start[n + 1] - S->in_start[n];
+    for (int k = S->in_start[n]; k < S->in_start[n + 1]; k++) S->in_index[S->in_list[k]] = k - S->in_start[n];
+  }
+  S->dt = P->dt; S->hdt2 = (0.5f * P->dt) * P->dt; S->dt_ds = dt_ds;
+  S->len_v = P->veh_len; S->s_min = P->s_min;
+  S->mp = P->mobil_p; S->mathr = P->mobil_athr; S->mbsafe = P->mobil_bsafe; S->mbias = P->mobil_bias_right;
+  S->lam = P->lambda_mand; S->stop_acq = P->stop_acquire_m;
+  S->seed = P->seed; S->cost_mode = P->cost_mode; S->loop = P->loop_routes;
+  for (int k = 0; k < 256; k++) S->tau[k] = orc_mand_tau(k);
+  int nt = D->n_trips;
+  S->nt = nt;
+  S->orig = (int32_t*)xcalloc(nt, 4); S->dest = (int32_t*)xcalloc(nt, 4); S->dep = (int32_t*)xcalloc(nt, 4);
+  for (int i = 0; i < nt; i++) {
+    S->orig[i] = D->origin[i]; S->dest[i] = D->dest[i]; S->dep[i] = D->depart_step[i];
+    if (S->orig[i] < 0 || S->orig[i] >= nn || S->dest[i] < 0 || S->dest[i] >= nn) { orc_destroy(S); return EINV; }
+  }
+  S->roff = (int32_t*)xcalloc(nt + 1, 4);
+  S->st = (uint8_t*)xcalloc(nt, 1);
+  S->link = (int32_t*)xcalloc(nt, 4); S->lane = (int32_t*)xcalloc(nt, 4); S->cur = (int32_t*)xcalloc(nt, 4);
+  S->x = (float*)xcalloc(nt, 4); S->v = (float*)xcalloc(nt, 4);
+  S->ins_step = (int32_t*)xcalloc(nt, 4); S->arr_step = (int32_t*)xcalloc(nt, 4);
+  S->dec = (int8_t*)xcalloc(nt, 1);
+  S->holder = (int32_t*)xcalloc(nn, 4);
+  for (int i = 0; i < nn; i++) S->holder[i] = -1;
+  for (int i = 0; i < nt; i++) { S->link[i] = -1; S->ins_step[i] = -1; S->arr_step[i] = -1; }
+  S->q_start = (int32_t*)xcalloc(nl + 1, 4); S->q_items = (int32_t*)xcalloc(nt, 4); S->q_head = (int32_t*)xcalloc(nl, 4);
+  *out = S;
+  return OK;
+}
+
+void orc_destroy(orc_sim* S) {
+  if (!S) return;
+  void* ptrs[] = {S->px, S->py, S->ctrl, S->off, S->cyc, S->grn, S->lf, S->lt, S->len, S->spd, S->lanes, S->cls,
+                  S->v0l, S->lane_base, S->in_start, S->in_list, S->in_index, S->n_in, S->pv0, S->pT, S->pa,
+                  S->pb, S->ps0, S->psab, S->orig, S->dest, S->dep, S->roff, S->rl, S->st, S->link, S->lane,
+                  S->cur, S->x, S->v, S->ins_step, S->arr_step, S->dec, S->holder, S->q_start, S->q_items,
+                  S->q_head};
+  for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); i++) free(ptrs[i]);
+  free(S);
+}
+
+/* ------------------------------------------------------------------ routes */
+static int route_len(const orc_sim* S, int i) { return S->roff[i + 1] - S->roff[i]; }
+
+/* Next link after hop k of trip i, or -1 at the end of a non-looping route. */
+static int next_link(const orc_sim* S, int i, int k) {
+  int n = route_len(S, i);
+  if (k + 1 < n) return S->rl[S->roff[i] + k + 1];
+  if (S->loop) return S->rl[S->roff[i] + (k + 1) % n];
+  return -1;
+}
+
+/* Departure queues: per first link, trips not yet on the road ordered by
+ * (depart_step, trip id). */
+static const int32_t* g_dep;
+static int cmp_trip(const void* A, const void* B) {
+  int a = *(const int*)A, b = *(const int*)B;
+  if (g_dep[a] != g_dep[b]) return g_dep[a] < g_dep[b] ? -1 : 1;
+  return a < b ? -1 : (a > b);
+}
+
+static void rebuild_queues(orc_sim* S) {
+  int nl = S->nl, nt = S->nt;
+  for (int e = 0; e <= nl; e++) S->q_start[e] = 0;
+  for (int i = 0; i < nt; i++)
+    if (S->st[i] == ST_PENDING) S->q_start[S->rl[S->roff[i]] + 1]++;
+  for (int e = 0; e < nl; e++) S->q_start[e + 1] += S->q_start[e];
+  int* fill = (int*)xcalloc(nl, sizeof(int));
+  for (int i = 0; i < nt; i++)
+    if (S->st[i] == ST_PENDING) { int e = S->rl[S->roff[i]]; S->q_items[S->q_start[e] + fill[e]++] = i; }
+  free(fill);
+  g_dep = S->dep;
+  for (int e = 0; e < nl; e++) {
+    qsort(S->q_items + S->q_start[e], (size_t)(S->q_start[e + 1] - S->q_start[e]), sizeof(int32_t), cmp_trip);
+    S->q_head[e] = S->q_start[e];
+  }
+}
+
+static void reset_state(orc_sim* S) {
+  for (int i = 0; i < S->nt; i++) {
+    S->st[i] = ST_PENDING; S->link[i] = -1; S->lane[i] = 0; S->cur[i] = 0; S->x[i] = 0.0f; S->v[i] = 0.0f;
+    S->ins_step[i] = -1; S->arr_step[i] = -1; S->dec[i] = 0;
+  }
+  for (int n = 0; n < S->nn; n++) S->holder[n] = -1;
+  S->t = 0; S->departed = 0; S->arrived = 0; S->veh_steps = 0; S->active_last = 0;
+}
+
+/* Trip planning (Sec. 6.3.1): every trip follows a shortest path from its origin
+ * node to its destination node; one shortest-path tree per distinct origin is
+ * shared by all trips from it (Sec. 6 "Simulation scale").  Ties between equally
+ * short paths: walking back from the destination, take the lowest-id in-link
+ * (u -> v) with dist[u] + c = dist[v]. */
+int orc_route(orc_sim* S, const int32_t* cost_in) {
+  int nn = S->nn, nl = S->nl, nt = S->nt;
+  int32_t* cost = (int32_t*)xcalloc(nl, 4);
+  for (int e = 0; e < nl; e++) {
+    cost[e] = cost_in ? cost_in[e] : orc_link_cost(S->len[e], S->spd[e], S->lanes[e], S->cost_mode);
+    if (cost[e] < 1) { free(cost); return EINV; }
+  }
+  for (int i = 0; i < nt; i++) if (S->orig[i] == S->dest[i]) { free(cost); return EINV; }
+  int* os = (int*)xcalloc(nn + 1, sizeof(int));
+  int* ol = (int*)xcalloc(nl, sizeof(int));
+  build_csr(nn, nl, S->lf, os, ol);
+  /* trips grouped by origin */
+  int* ts = (int*)xcalloc(nn + 1, sizeof(int));
+  int* tl = (int*)xcalloc(nt, sizeof(int));
+  build_csr(nn, nt, S->orig, ts, tl);
+  int64_t* dist = (int64_t*)xcalloc(nn, 8);
+  hent* heap = (hent*)xcalloc(nl + 1, sizeof(hent));
+  int32_t* rlen = (int32_t*)xcalloc(nt, 4);
+  int32_t** paths = (int32_t**)xcalloc(nt, sizeof(int32_t*));
+  int32_t* tmp = (int32_t*)xcalloc(nn + 1, 4);
+  int rc = OK;
+  for (int o = 0; o < nn && rc == OK; o++) {
+    if (ts[o] == ts[o + 1]) continue;
+    dijkstra(nn, os, ol, S->lt, cost, o, dist, heap);
+    for (int k = ts[o]; k < ts[o + 1]; k++) {
+      int i = tl[k];
+      int d = S->dest[i];
+      if (dist[d] == INT64_MAX) { rc = EUNREACH; break; }
+      int n = 0, v = d;
+      while (v != o) {
+        int pick = -1;
+        for (int q = S->in_start[v]; q < S->in_start[v + 1]; q++) {
+          int e = S->in_list[q];
+          int u = S->lf[e];
+          if (dist[u] != INT64_MAX && dist[u] + cost[e] == dist[v]) { pick = e; break; }
+        }
+        if (pick < 0) { rc = ESTATE; break; }
+        tmp[n++] = pick;
+        v = S->lf[pick];
+      }
+      if (rc != OK) break;
+      rlen[i] = n;
+      paths[i] = (int32_t*)xcalloc(n, 4);
+      for (int j = 0; j < n; j++) paths[i][j] = tmp[n - 1 - j];
+    }
+  }
+  if (rc == OK) {
+    S->roff[0] = 0;
+    for (int i = 0; i < nt; i++) S->roff[i + 1] = S->roff[i] + rlen[i];
+    free(S->rl);
+    S->rl = (int32_t*)xcalloc((size_t)S->roff[nt], 4);
+    for (int i = 0; i < nt; i++) memcpy(S->rl + S->roff[i], paths[i], (size_t)rlen[i] * 4);
+    S->routed = 1;
+    reset_state(S);
+    rebuild_queues(S);
+  }
+  for (int i = 0; i < nt; i++) free(paths[i]);
+  free(paths); free(tmp); free(rlen); free(heap); free(dist); free(ts); free(tl); free(os); free(ol); free(cost);
+  return rc;
+}
+
+int orc_set_routes(orc_sim* S, const int32_t* offsets, const int32_t* links) {
+  int nt = S->nt;
+  if (offsets[0] != 0) return EINV;
+  for (int i = 0; i < nt; i++) {
+    if (offsets[i + 1] <= offsets[i]) return EINV;
+    for (int k = offsets[i]; k < offsets[i + 1]; k++) {
+      if (links[k] < 0 || links[k] >= S->nl) return EINV;
+      if (k > offsets[i] && S->lf[links[k]] != S->lt[links[k - 1]]) return EINV;
+    }
+    if (S->loop && S->lt[links[offsets[i + 1] - 1]] != S->lf[links[offsets[i]]]) return EINV;
+  }
+  for (int i = 0; i <= nt; i++) S->roff[i] = offsets[i];
+  free(S->rl);
+  S->rl = (int32_t*)xcalloc((size_t)offsets[nt], 4);
+  memcpy(S->rl, links, (size_t)offsets[nt] * 4);
+  S->routed = 1;
+  reset_state(S);
+  rebuild_queues(S);
+  return OK;
+}
+
+int orc_route_size(const orc_sim* S, int64_t* n) { *n = S->routed ? S->roff[S->nt] : 0; return S->routed ? OK : ESTATE; }
+
+int orc_read_routes(const orc_sim* S, int32_t* offsets, int32_t* links) {
+  if (!S->routed) return ESTATE;
+  memcpy(offsets, S->roff, (size_t)(S->nt + 1) * 4);
+  memcpy(links, S->rl, (size_t)S->roff[S->nt] * 4);
+  return OK;
+}
+
+int orc_write_state(orc_sim* S, const uint8_t* status, const int32_t* link, const int32_t* lane,
+                    const int32_t* cursor, const float* x, const float* v) {
+  if (!S->routed) return ESTATE;
+  for (int i = 0; i < S->nt; i++) {
+    if (status[i] > ST_ARRIVED) return EINV;
+    if (status[i] == ST_ACTIVE) {
+      int k = cursor[i];
+      if (k < 0 || k >= route_len(S, i) || S->rl[S->roff[i] + k] != link[i]) return EINV;
+      if (lane[i] < 0 || lane[i] >= S->lanes[link[i]]) return EINV;
+      if (!(x[i] >= 0.0f) || !(x[i] <= S->len[link[i]]) || !(v[i] >= 0.0f)) return EINV;
+    }
+  }
+  reset_state(S);
+  for (int i = 0; i < S->nt; i++) {
+    S->st[i] = status[i];
+    if (status[i] == ST_ACTIVE) {
+      S->link[i] = link[i]; S->lane[i] = lane[i]; S->cur[i] = cursor[i];
+      S->x[i] = x[i] + 0.0f; S->v[i] = v[i]; S->ins_step[i] = 0;
+    }
+  }
+  rebuild_queues(S);
+  return OK;
+}
+
+/* ------------------------------------------------------------------ one step */
+/* Per-lane occupancy, ordered by (position, trip id): the function of the paper's
+ * "traffic atlas" (Sec. 6.3.3): the leader of a vehicle is the next vehicle in
+ * its lane. */
+static const float* g_x;
+static int cmp_pos(const void* A, const void* B) {
+  int a = *(const int*)A, b = *(const int*)B;
+  if (g_x[a] != g_x[b]) return g_x[a] < g_x[b] ? -1 : 1;
+  return a < b ? -1 : (a > b);
+}
+
+typedef struct {
+  int* start;   /* [n_lanes + 1] */
+  int* vids;    /* sorted by (lane, x, vid) */
+  int* pos;     /* position of each active trip in vids */
+  int n;
+} occ_t;
+
+static void build_occ(const orc_sim* S, occ_t* O) {
+  int nlan = S->n_lanes;
+  O->start = (int*)xcalloc(nlan + 1, sizeof(int));
+  O->pos = (int*)xcalloc(S->nt, sizeof(int));
+  int n = 0;
+  for (int i = 0; i < S->nt; i++)
+    if (S->st[i] == ST_ACTIVE) { O->start[S->lane_base[S->link[i]] + S->lane[i] + 1]++; n++; }
+  for (int g = 0; g < nlan; g++) O->start[g + 1] += O->start[g];
+  O->vids = (int*)xcalloc(n, sizeof(int));
+  int* fill = (int*)xcalloc(nlan, sizeof(int));
+  for (int i = 0; i < S->nt; i++)
+    if (S->st[i] == ST_ACTIVE) { int g = S->lane_base[S->link[i]] + S->lane[i]; O->vids[O->start[g] + fill[g]++] = i; }
+  free(fill);
+  g_x = S->x;
+  for (int g = 0; g < nlan; g++) qsort(O->vids + O->start[g], (size_t)(O->start[g + 1] - O->start[g]), sizeof(int), cmp_pos);
+  for (int p = 0; p < n; p++) O->pos[O->vids[p]] = p;
+  O->n = n;
+}
+
+static void free_occ(occ_t* O) { free(O->start); free(O->vids); free(O->pos); }
+
+static int lane_id(const orc_sim* S, int e, int l) { return S->lane_base[e] + l; }
+
+/* Lane mask of a movement (bit l set when lane l may make it).  Reading of
+ * Sec. 6.3.2's "necessary change to reach an exit or right/left turn": on a
+ * multi-lane link right turns leave from lane 0 (rightmost), left turns and
+ * U-turns from the leftmost lane, through movements from any lane. */
+static int move_mask(const orc_sim* S, int e, int e2) {
+  int nl = S->lanes[e];
+  int all = (1 << nl) - 1;
+  if (e2 < 0) return all;
+  int a = S->lf[e], b = S->lt[e], c = S->lt[e2];
+  int tc = orc_turn(S->px[a], S->py[a], S->px[b], S->py[b], S->px[c], S->py[c]);
+  if (tc == TURN_RIGHT) return 1;
+  if (tc == TURN_LEFT) return 1 << (nl - 1);
+  return all;
+}
+
+/* Phase group of an approach: east-west when the link runs more along x than y. */
+static int approach_ew(const orc_sim* S, int e) {
+  int64_t dx = S->px[S->lt[e]] - S->px[S->lf[e]];
+  int64_t dy = S->py[S->lt[e]] - S->py[S->lf[e]];
+  if (dx < 0) dx = -dx;
+  if (dy < 0) dy = -dy;
+  return dx >= dy;
+}
+
+/* Round-robin rank of an incoming link at step t (Sec. 6.3.2: "round robin logic"):
+ * the link whose in-index equals t mod n_in ranks first. */
+static int rr_rank(const orc_sim* S, int e, int64_t t) {
+  int n = S->n_in[S->lt[e]];
+  return (int)((S->in_index[e] + n - (int)(t % n)) % n);
+}
+
+/* Whether the stop line of link e is closed to vehicle i at step t: red light for
+ * its approach, or a stop-controlled node held by another vehicle / not yet
+ * acquired by i. */
+static int stopline_closed(const orc_sim* S, int i, int e) {
+  int n = S->lt[e];
+  if (S->ctrl[n] == CTRL_SIGNAL)
+    return !orc_signal_green(S->t, S->dt_ds, S->off[n], S->cyc[n], S->grn[n], approach_ew(S, e));
+  if (S->ctrl[n] == CTRL_STOP) return S->holder[n] != i;
+  return 0;
+}
+
+static float acc_free(const orc_sim* S, int e, float v) {
+  int c = S->cls[e];
+  return idm_acc(S->pa[c], S->psab[c], S->pT[c], S->ps0[c], S->v0l[e], S->s_min, 0.0f, v, 0.0f, 0);
+}
+
+static float acc_gap(const orc_sim* S, int e, float s, float v, float vl) {
+  int c = S->cls[e];
+  return idm_acc(S->pa[c], S->psab[c], S->pT[c], S->ps0[c], S->v0l[e], S->s_min, s, v, vl, 1);
+}
+
+/* Acceleration of vehicle j at (x, v) on link e, lane l when nothing is ahead of it
+ * on e: the leader is the rearmost vehicle of the mapped lane of j's next link
+ * (gap counted across the link end), and a closed stop line acts as a standing
+ * obstacle; the smaller acceleration applies.  On the last link of a route the
+ * road ahead is free. */
+static float acc_front(const orc_sim* S, const occ_t* O, int j, int e, int l, float x, float v) {
+  int nx = next_link(S, j, S->cur[j]);
+  if (nx < 0) return acc_free(S, e, v);
+  int m = l < S->lanes[nx] - 1 ? l : S->lanes[nx] - 1;
+  int g = lane_id(S, nx, m);
+  float a1;
+  if (O->start[g] < O->start[g + 1] && O->vids[O->start[g]] != j) {
+    int r = O->vids[O->start[g]];
+    float s = ((S->len[e] - x) + S->x[r]) - S->len_v;
+    a1 = acc_gap(S, e, s, v, S->v[r]);
+  } else {
+    a1 = acc_free(S, e, v);
+  }
+  if (stopline_closed(S, j, e)) {
+    float a2 = acc_gap(S, e, S->len[e] - x, v, 0.0f);
+    return fminf(a1, a2);
+  }
+  return a1;
+}
+
+static int leader_of(const orc_sim* S, const occ_t* O, int i) {
+  int p = O->pos[i];
+  int g = lane_id(S, S->link[i], S->lane[i]);
+  return (p + 1 < O->start[g + 1]) ? O->vids[p + 1] : -1;
+}
+static int follower_of(const orc_sim* S, const occ_t* O, int i) {
+  int p = O->pos[i];
+  int g = lane_id(S, S->link[i], S->lane[i]);
+  return (p > O->start[g]) ? O->vids[p - 1] : -1;
+}
+
+static int key_less(const orc_sim* S, int a, int b) {   /* (x, vid) order */
+  if (S->x[a] != S->x[b]) return S->x[a] < S->x[b];
+  return a < b;
+}
+
+/* Own-lane acceleration (Eq. 7 with the own-lane leader, else acc_front). */
+static float acc_own(const orc_sim* S, const occ_t* O, int i) {
+  int L = leader_of(S, O, i);
+  int e = S->link[i];
+  if (L >= 0) return acc_gap(S, e, (S->x[L] - S->x[i]) - S->len_v, S->v[i], S->v[L]);
+  return acc_front(S, O, i, e, S->lane[i], S->x[i], S->v[i]);
+}
+
+int orc_step(orc_sim* S, int32_t n_steps) {
+  if (!S->routed) return ESTATE;
+  int nt = S->nt;
+  float* a_own = (float*)xcalloc(nt, 4);
+  float* xo = (float*)xcalloc(nt, 4);
+  float* vo = (float*)xcalloc(nt, 4);
+  float* at = (float*)xcalloc(nt, 4);
+  int8_t* intent = (int8_t*)xcalloc(nt, 1);
+  int8_t* change = (int8_t*)xcalloc(nt, 1);
+  uint8_t* cand = (uint8_t*)xcalloc(nt, 1);
+  int* best = (int*)xcalloc(S->n_lanes, sizeof(int));
+  uint8_t* nst = (uint8_t*)xcalloc(nt, 1);
+  int32_t *nlink = (int32_t*)xcalloc(nt, 4), *nlane = (int32_t*)xcalloc(nt, 4), *ncur = (int32_t*)xcalloc(nt, 4);
+  float *nx_ = (float*)xcalloc(nt, 4), *nv = (float*)xcalloc(nt, 4);
+
+  for (int step = 0; step < n_steps; step++) {
+    int64_t t = S->t;
+    occ_t O;
+    build_occ(S, &O);
+    S->veh_steps += O.n;
+    S->active_last = O.n;
+
+    /* stop signs (Sec. 6.3.2): one vehicle at a time.  A free stop-controlled node is
+     * acquired by the front vehicle, within stop_acquire_m of the stop line, of the
+     * incoming lane ranked first by (round-robin rank of its link, lane). */
+    for (int n = 0; n < S->nn; n++) {
+      if (S->ctrl[n] != CTRL_STOP || S->holder[n] >= 0) continue;
+      int bk = 1 << 30, bv = -1;
+      for (int q = S->in_start[n]; q < S->in_start[n + 1]; q++) {
+        int e = S->in_list[q];
+        for (int l = 0; l < S->lanes[e]; l++) {
+          int g = lane_id(S, e, l);
+          if (O.start[g] == O.start[g + 1]) continue;
+          int j = O.vids[O.start[g + 1] - 1];
+          if (next_link(S, j, S->cur[j]) < 0) continue;
+          if (!((S->len[e] - S->x[j]) <= S->stop_acq)) continue;
+          int key = rr_rank(S, e, t) * 256 + l;
+          if (key < bk) { bk = key; bv = j; }
+        }
+      }
+      S->holder[n] = bv;
+    }
+
+    /* own-lane acceleration and tentative move of every vehicle */
+    for (int i = 0; i < nt; i++) {
+      if (S->st[i] != ST_ACTIVE) continue;
+      a_own[i] = acc_own(S, &O, i);
+      ballistic(S->x[i], S->v[i], a_own[i], S->dt, S->hdt2, &xo[i], &vo[i]);
+    }
+
+    /* admission into the next link (Sec. 6.3.2 intersection control): the front
+     * vehicle of a lane whose stop line is open and whose move reaches the link end
+     * is a candidate if it lands behind the rearmost vehicle of its target lane; at
+     * most one candidate enters each target lane per step, the one ranked first by
+     * (round-robin rank of its link, lane). */
+    for (int g = 0; g < S->n_lanes; g++) best[g] = 1 << 30;
+    for (int i = 0; i < nt; i++) {
+      cand[i] = 0;
+      if (S->st[i] != ST_ACTIVE) continue;
+      int e = S->link[i];
+      if (leader_of(S, &O, i) >= 0) continue;
+      int nx = next_link(S, i, S->cur[i]);
+      if (nx < 0 || stopline_closed(S, i, e)) continue;
+      if (!(xo[i] >= S->len[e])) continue;
+      int m = S->lane[i] < S->lanes[nx] - 1 ? S->lane[i] : S->lanes[nx] - 1;
+      int g = lane_id(S, nx, m);
+      if (O.start[g] < O.start[g + 1] && O.vids[O.start[g]] != i) {
+        int r = O.vids[O.start[g]];
+        float land = xo[i] - S->len[e];
+        float room = S->x[r] - S->len_v;
+        if (!(land <= room)) continue;
+      }
+      cand[i] = 1;
+      int key = rr_rank(S, e, t) * 256 + S->lane[i];
+      if (key < best[g]) best[g] = key;
+    }
+
+    /* lane-change decisions (Sec. 6.3.2), from the state at t only.  Reading:
+     * MOBIL (Kesting, Treiber & Helbing 2007) for the discretionary incentive and
+     * its safety criterion for gap acceptance; mandatory when the vehicle is off
+     * the lanes of its next movement and within its drawn switch distance. */
+    for (int i = 0; i < nt; i++) {
+      intent[i] = 0;
+      if (S->st[i] != ST_ACTIVE) continue;
+      int e = S->link[i];
+      int nlan = S->lanes[e];
+      if (nlan < 2) continue;
+      float zone = 2.0f * S->len_v;
+      if (!(S->x[i] >= zone && xo[i] < S->len[e] - zone)) continue;
+      int l = S->lane[i];
+      int nx = next_link(S, i, S->cur[i]);
+      int M = move_mask(S, e, nx);
+      int dirs[2], nd = 0, mand = 0;
+      if ((M >> l) & 1) {
+        if (l + 1 < nlan && ((M >> (l + 1)) & 1)) dirs[nd++] = +1;
+        if (l - 1 >= 0 && ((M >> (l - 1)) & 1)) dirs[nd++] = -1;
+      } else {
+        int ms = 0;
+        while (!((M >> ms) & 1)) ms++;
+        int d = ms > l ? +1 : -1;
+        int ncross = ms > l ? ms - l : l - ms;
+        float thr = (S->lam * (float)ncross) * S->tau[orc_mand_index(S->seed, i, S->cur[i])];
+        float drem = S->len[e] - S->x[i];
+        mand = drem <= thr;
+        dirs[nd++] = d;
+      }
+      int chosen = 0;
+      float chosen_inc = 0.0f, chosen_at = 0.0f;
+      for (int k = 0; k < nd; k++) {
+        int d = dirs[k];
+        int l2 = l + d;
+        int g2 = lane_id(S, e, l2);
+        int Ln = -1, Fn = -1;
+        for (int p = O.start[g2]; p < O.start[g2 + 1]; p++) {
+          int j = O.vids[p];
+          if (key_less(S, j, i)) Fn = j;
+          else if (Ln < 0) Ln = j;
+        }
+        float ac;
+        if (Ln >= 0) {
+          float sl = (S->x[Ln] - S->x[i]) - S->len_v;
+          if (!(sl > 0.0f)) continue;
+          ac = acc_gap(S, e, sl, S->v[i], S->v[Ln]);
+        } else {
+          ac = acc_front(S, &O, i, e, l2, S->x[i], S->v[i]);
+        }
+        if (!(ac >= -S->mbsafe)) continue;
+        float an = 0.0f;
+        if (Fn >= 0) {
+          float sg = (S->x[i] - S->x[Fn]) - S->len_v;
+          if (!(sg > 0.0f)) continue;
+          an = acc_gap(S, e, sg, S->v[Fn], S->v[i]);
+          if (!(an >= -S->mbsafe)) continue;
+        }
+        if (mand) { chosen = d; chosen_at = ac; break; }
+        float dc = ac - a_own[i];
+        float dn = Fn >= 0 ? an - a_own[Fn] : 0.0f;
+        float dn_o = 0.0f;
+        int F = follower_of(S, &O, i);
+        if (F >= 0) {
+          int L = leader_of(S, &O, i);
+          float ao = (L >= 0) ? acc_gap(S, e, (S->x[L] - S->x[F]) - S->len_v, S->v[F], S->v[L])
+                              : acc_front(S, &O, F, e, l, S->x[F], S->v[F]);
+          dn_o = ao - a_own[F];
+        }
+        float inc = dc + S->mp * (dn + dn_o);
+        if (d < 0) inc = inc + S->mbias;
+        if (!(inc > S->mathr)) continue;
+        if (chosen == 0 || inc > chosen_inc) { chosen = d; chosen_inc = inc; chosen_at = ac; }
+      }
+      intent[i] = (int8_t)chosen;
+      at[i] = chosen_at;
+    }
+
+    /* simultaneous changes into one lane (paper silent): a change is cancelled when
+     * another vehicle with a lower trip id changes into the same lane of the same
+     * link less than (vehicle length + s0) away. */
+    for (int i = 0; i < nt; i++) {
+      change[i] = 0;
+      if (S->st[i] != ST_ACTIVE || intent[i] == 0) continue;
+      int e = S->link[i];
+      int tgt = S->lane[i] + intent[i];
+      float thr = S->len_v + S->ps0[S->cls[e]];
+      int cancel = 0;
+      /* changers into lane tgt come from lanes tgt - 1 and tgt + 1 of the same link */
+      for (int src = tgt - 1; src <= tgt + 1 && !cancel; src += 2) {
+        if (src < 0 || src >= S->lanes[e]) continue;
+        int g = lane_id(S, e, src);
+        for (int p = O.start[g]; p < O.start[g + 1] && !cancel; p++) {
+          int j = O.vids[p];
+          if (j >= i || intent[j] == 0 || S->lane[j] + intent[j] != tgt) continue;
+          if (fabsf(S->x[j] - S->x[i]) < thr) cancel = 1;
+        }
+      }
+      if (!cancel) change[i] = intent[i];
+    }
+
+    /* move every vehicle; transitions, arrivals, and vehicles held at the stop line */
+    int64_t arrivals = 0;
+    for (int i = 0; i < nt; i++) {
+      nst[i] = S->st[i]; nlink[i] = S->link[i]; nlane[i] = S->lane[i]; ncur[i] = S->cur[i];
+      nx_[i] = S->x[i]; nv[i] = S->v[i];
+      S->dec[i] = 0;
+      if (S->st[i] != ST_ACTIVE) continue;
+      int e = S->link[i];
+      float acc = change[i] ? at[i] : a_own[i];
+      float x1, v1;
+      ballistic(S->x[i], S->v[i], acc, S->dt, S->hdt2, &x1, &v1);
+      int l1 = S->lane[i] + change[i];
+      S->dec[i] = change[i];
+      int node = S->lt[e];
+      int was_holder = S->ctrl[node] == CTRL_STOP && S->holder[node] == i;
+      if (x1 >= S->len[e]) {
+        int nx = next_link(S, i, S->cur[i]);
+        if (nx < 0) {
+          nst[i] = ST_ARRIVED; nlink[i] = -1; nx_[i] = 0.0f; nv[i] = 0.0f;
+          S->arr_step[i] = (int32_t)t;
+          arrivals++;
+          continue;
+        }
+        int m = S->lane[i] < S->lanes[nx] - 1 ? S->lane[i] : S->lanes[nx] - 1;
+        int g = lane_id(S, nx, m);
+        int won = cand[i] && best[g] == rr_rank(S, e, t) * 256 + S->lane[i];
+        if (won) {
+          nlink[i] = nx; nlane[i] = m;
+          int rlen = route_len(S, i);
+          ncur[i] = S->loop ? (S->cur[i] + 1) % rlen : S->cur[i] + 1;
+          nx_[i] = x1 - S->len[e]; nv[i] = v1;
+          if (was_holder) S->holder[node] = -1;
+        } else {
+          nlane[i] = l1; nx_[i] = S->len[e]; nv[i] = 0.0f;
+        }
+      } else {
+        nlane[i] = l1; nx_[i] = x1; nv[i] = v1;
+      }
+    }
+
+    /* departures (Sec. 6.2.2 OD and departure time): the head of each link's queue
+     * of due trips enters at x = 0, v = 0 in the permitted lane with the largest rear
+     * space (ties to the lowest lane) that received no vehicle from upstream in this
+     * step, when that space is at least s0 + vehicle length. */
+    int64_t ins = 0;
+    for (int e = 0; e < S->nl; e++) {
+      if (S->q_head[e] >= S->q_start[e + 1]) continue;
+      int h = S->q_items[S->q_head[e]];
+      if (S->dep[h] > t) continue;
+      int rlen = route_len(S, h);
+      int e2 = rlen >= 2 ? S->rl[S->roff[h] + 1] : (S->loop ? S->rl[S->roff[h]] : -1);
+      int M = move_mask(S, e, e2);
+      int bl = -1;
+      float brs = 0.0f;
+      for (int l = 0; l < S->lanes[e]; l++) {
+        if (!((M >> l) & 1)) continue;
+        int g = lane_id(S, e, l);
+        if (best[g] != (1 << 30)) continue;
+        float rs = (O.start[g] < O.start[g + 1]) ? S->x[O.vids[O.start[g]]] - S->len_v : INFINITY;
+        if (bl < 0 || rs > brs) { bl = l; brs = rs; }
+      }
+      if (bl < 0) continue;
+      float need = S->ps0[S->cls[e]] + S->len_v;
+      if (!(brs >= need)) continue;
+      nst[h] = ST_ACTIVE; nlink[h] = e; nlane[h] = bl; ncur[h] = 0; nx_[h] = 0.0f; nv[h] = 0.0f;
+      S->ins_step[h] = (int32_t)t;
+      S->q_head[e]++;
+      ins++;
+    }
+
+    memcpy(S->st, nst, (size_t)nt);
+    memcpy(S->link, nlink, (size_t)nt * 4); memcpy(S->lane, nlane, (size_t)nt * 4);
+    memcpy(S->cur, ncur, (size_t)nt * 4);
+    memcpy(S->x, nx_, (size_t)nt * 4); memcpy(S->v, nv, (size_t)nt * 4);
+    S->departed += ins;
+    S->arrived += arrivals;
+    S->t = t + 1;
+    free_occ(&O);
+  }
+  free(a_own); free(xo); free(vo); free(at); free(intent); free(change); free(cand); free(best);
+  free(nst); free(nlink); free(nlane); free(ncur); free(nx_); free(nv);
+  return OK;
+}
+
+/* ------------------------------------------------------------------ outputs */
+int orc_read_state(const orc_sim* S, uint8_t* status, int32_t* link, int32_t* lane, int32_t* cursor,
+                   float* x, float* v, int32_t* insert_step, int32_t* arrive_step, int8_t* lane_change) {
+  for (int i = 0; i < S->nt; i++) {
+    if (status) status[i] = S->st[i];
+    int act = S->st[i] == ST_ACTIVE;
+    if (link) link[i] = act ? S->link[i] : -1;
+    if (lane) lane[i] = act ? S->lane[i] : 0;
+    if (cursor) cursor[i] = act ? S->cur[i] : 0;
+    if (x) x[i] = act ? S->x[i] : 0.0f;
+    if (v) v[i] = act ? S->v[i] : 0.0f;
+    if (insert_step) insert_step[i] = S->ins_step[i];
+    if (arrive_step) arrive_step[i] = S->arr_step[i];
+    if (lane_change) lane_change[i] = S->dec[i];
+  }
+  return OK;
+}
+
+int orc_occupancy(const orc_sim* S, int32_t* lane_start, int32_t* sorted_vid) {
+  occ_t O;
+  build_occ(S, &O);
+  for (int g = 0; g <= S->n_lanes; g++) lane_start[g] = O.start[g];
+  for (int p = 0; p < O.n; p++) sorted_vid[p] = O.vids[p];
+  free_occ(&O);
+  return OK;
+}
+
+int orc_n_lanes(const orc_sim* S) { return S->n_lanes; }
+
+int orc_node_holder(const orc_sim* S, int32_t* holder) {
+  memcpy(holder, S->holder, (size_t)S->nn * 4);
+  return OK;
+}
+
+/* counters: t, departed, waiting (due, not on the road), active, arrived,
+ * vehicle-steps, pending (not yet due), active at the last step start */
+int orc_counters(const orc_sim* S, int64_t out[8]) {
+  int64_t waiting = 0, pending = 0, active = 0;
+  for (int i = 0; i < S->nt; i++) {
+    if (S->st[i] == ST_ACTIVE) active++;
+    else if (S->st[i] == ST_PENDING) {
+      if (S->dep[i] < S->t) waiting++;
+      else pending++;
+    }
+  }
+  out[0] = S->t; out[1] = S->departed; out[2] = waiting; out[3] = active;
+  out[4] = S->arrived; out[5] = S->veh_steps; out[6] = pending; out[7] = S->active_last;
+  return OK;
+}

@@ -1,0 +1,244 @@
+"""ctypes wrapper of the C oracle (test infrastructure only; never used by the product path)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_SO = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with plain gcc (no fused multiply-add, no fast-math)."""
+    with _lock:
+        if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
+                os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+            tmp = _SO + f".{os.getpid()}.tmp"
+            subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math",
+                                   "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, _SO)
+    return _SO
+
+
+class _Net(C.Structure):
+    _fields_ = [("n_nodes", C.c_int32), ("n_links", C.c_int32),
+                ("node_x_dm", C.c_void_p), ("node_y_dm", C.c_void_p), ("node_control", C.c_void_p),
+                ("signal_offset_ds", C.c_void_p), ("signal_cycle_ds", C.c_void_p),
+                ("signal_green_ds", C.c_void_p), ("link_from", C.c_void_p), ("link_to", C.c_void_p),
+                ("link_length_m", C.c_void_p), ("link_speed_mps", C.c_void_p),
+                ("link_lanes", C.c_void_p), ("link_class", C.c_void_p)]
+
+
+class _Dem(C.Structure):
+    _fields_ = [("n_trips", C.c_int32), ("origin", C.c_void_p), ("dest", C.c_void_p),
+                ("depart_step", C.c_void_p)]
+
+
+class _Par(C.Structure):
+    _fields_ = [("dt", C.c_float), ("veh_len", C.c_float), ("s_min", C.c_float),
+                ("n_class", C.c_int32),
+                ("v0", C.c_void_p), ("T", C.c_void_p), ("a", C.c_void_p), ("b", C.c_void_p),
+                ("s0", C.c_void_p),
+                ("mobil_p", C.c_float), ("mobil_athr", C.c_float), ("mobil_bsafe", C.c_float),
+                ("mobil_bias_right", C.c_float), ("lambda_mand", C.c_float),
+                ("stop_acquire_m", C.c_float), ("seed", C.c_uint64),
+                ("cost_mode", C.c_int32), ("loop_routes", C.c_int32)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_SO)
+        vp, i32, i64, f32 = C.c_void_p, C.c_int32, C.c_int64, C.c_float
+        L.orc_create.argtypes = [C.POINTER(_Net), C.POINTER(_Dem), C.POINTER(_Par), C.POINTER(vp)]
+        L.orc_destroy.argtypes = [vp]
+        L.orc_route.argtypes = [vp, vp]
+        L.orc_set_routes.argtypes = [vp, vp, vp]
+        L.orc_route_size.argtypes = [vp, C.POINTER(i64)]
+        L.orc_read_routes.argtypes = [vp, vp, vp]
+        L.orc_write_state.argtypes = [vp] + [vp] * 6
+        L.orc_step.argtypes = [vp, i32]
+        L.orc_read_state.argtypes = [vp] + [vp] * 9
+        L.orc_occupancy.argtypes = [vp, vp, vp]
+        L.orc_n_lanes.argtypes = [vp]
+        L.orc_counters.argtypes = [vp, vp]
+        L.orc_node_holder.argtypes = [vp, vp]
+        L.orc_idm.argtypes = [f32] * 9 + [C.c_int]
+        L.orc_idm.restype = f32
+        L.orc_ballistic.argtypes = [f32, f32, f32, f32, C.POINTER(f32), C.POINTER(f32)]
+        L.orc_link_cost.argtypes = [f32, f32, C.c_int, C.c_int]
+        L.orc_link_cost.restype = i32
+        L.orc_sssp.argtypes = [i32, i32, vp, vp, vp, i32, vp]
+        L.orc_mand_index.argtypes = [C.c_uint64, i32, i32]
+        L.orc_mand_index.restype = C.c_uint32
+        L.orc_mand_tau.argtypes = [C.c_int]
+        L.orc_mand_tau.restype = f32
+        L.orc_turn.argtypes = [i64] * 6
+        L.orc_signal_green.argtypes = [i64, i32, i32, i32, i32, C.c_int]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise OracleError(f"{what} failed with code {rc}")
+
+
+class OracleSim:
+    """One simulation instance of the oracle (same inputs as the CUDA library)."""
+
+    def __init__(self, scenario: dict):
+        L = lib()
+        net, dem, par = scenario["network"], scenario["demand"], scenario["params"]
+        self._keep = []
+
+        def arr(a, dt):
+            a = np.ascontiguousarray(a, dtype=dt)
+            self._keep.append(a)
+            return _p(a)
+        n = _Net(net["n_nodes"], net["n_links"], arr(net["node_x_dm"], np.int32),
+                 arr(net["node_y_dm"], np.int32), arr(net["node_control"], np.uint8),
+                 arr(net["signal_offset_ds"], np.int32), arr(net["signal_cycle_ds"], np.int32),
+                 arr(net["signal_green_ds"], np.int32), arr(net["link_from"], np.int32),
+                 arr(net["link_to"], np.int32), arr(net["link_length_m"], np.float32),
+                 arr(net["link_speed_mps"], np.float32), arr(net["link_lanes"], np.uint8),
+                 arr(net["link_class"], np.uint8))
+        d = _Dem(dem["n_trips"], arr(dem["origin"], np.int32), arr(dem["dest"], np.int32),
+                 arr(dem["depart_step"], np.int32))
+        p = _Par(par["dt"], par["veh_len"], par["s_min"], par["n_class"],
+                 arr(par["v0"], np.float32), arr(par["T"], np.float32), arr(par["a"], np.float32),
+                 arr(par["b"], np.float32), arr(par["s0"], np.float32),
+                 par["mobil_p"], par["mobil_athr"], par["mobil_bsafe"], par["mobil_bias_right"],
+                 par["lambda_mand"], par["stop_acquire_m"], par["seed"] & (2**64 - 1),
+                 par["cost_mode"], par["loop_routes"])
+        h = C.c_void_p()
+        _check(L.orc_create(C.byref(n), C.byref(d), C.byref(p), C.byref(h)), "orc_create")
+        self._keep = []
+        self.h = h
+        self.n_trips = dem["n_trips"]
+        self.n_nodes = net["n_nodes"]
+        self.n_lanes = L.orc_n_lanes(h)
+
+    def close(self):
+        if self.h:
+            lib().orc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def route(self, costs=None):
+        c = None if costs is None else np.ascontiguousarray(costs, np.int32)
+        _check(lib().orc_route(self.h, _p(c)), "orc_route")
+
+    def set_routes(self, offsets, links):
+        o = np.ascontiguousarray(offsets, np.int32)
+        l_ = np.ascontiguousarray(links, np.int32)
+        _check(lib().orc_set_routes(self.h, _p(o), _p(l_)), "orc_set_routes")
+
+    def routes(self):
+        n = C.c_int64()
+        _check(lib().orc_route_size(self.h, C.byref(n)), "orc_route_size")
+        off = np.zeros(self.n_trips + 1, np.int32)
+        links = np.zeros(max(1, n.value), np.int32)
+        _check(lib().orc_read_routes(self.h, _p(off), _p(links)), "orc_read_routes")
+        return off, links[: n.value]
+
+    def write_state(self, st):
+        _check(lib().orc_write_state(
+            self.h, _p(np.ascontiguousarray(st["status"], np.uint8)),
+            _p(np.ascontiguousarray(st["link"], np.int32)),
+            _p(np.ascontiguousarray(st["lane"], np.int32)),
+            _p(np.ascontiguousarray(st["cursor"], np.int32)),
+            _p(np.ascontiguousarray(st["x"], np.float32)),
+            _p(np.ascontiguousarray(st["v"], np.float32))), "orc_write_state")
+
+    def step(self, n=1):
+        _check(lib().orc_step(self.h, int(n)), "orc_step")
+
+    def state(self):
+        n = self.n_trips
+        out = dict(status=np.zeros(n, np.uint8), link=np.zeros(n, np.int32), lane=np.zeros(n, np.int32),
+                   cursor=np.zeros(n, np.int32), x=np.zeros(n, np.float32), v=np.zeros(n, np.float32),
+                   insert_step=np.zeros(n, np.int32), arrive_step=np.zeros(n, np.int32),
+                   lane_change=np.zeros(n, np.int8))
+        _check(lib().orc_read_state(self.h, *[_p(out[k]) for k in
+                                              ("status", "link", "lane", "cursor", "x", "v",
+                                               "insert_step", "arrive_step", "lane_change")]),
+               "orc_read_state")
+        return out
+
+    def occupancy(self):
+        start = np.zeros(self.n_lanes + 1, np.int32)
+        vids = np.zeros(max(1, self.n_trips), np.int32)
+        _check(lib().orc_occupancy(self.h, _p(start), _p(vids)), "orc_occupancy")
+        return start, vids[: start[-1]]
+
+    def counters(self):
+        c = np.zeros(8, np.int64)
+        _check(lib().orc_counters(self.h, _p(c)), "orc_counters")
+        keys = ("t", "departed", "waiting", "active", "arrived", "veh_steps", "pending", "active_last")
+        return {k: int(v) for k, v in zip(keys, c)}
+
+    def node_holder(self):
+        h = np.zeros(self.n_nodes, np.int32)
+        _check(lib().orc_node_holder(self.h, _p(h)), "orc_node_holder")
+        return h
+
+
+def oracle_idm(a, b, T, s0, v0, s_min, s, v, v_lead, has_leader=True):
+    return lib().orc_idm(a, b, T, s0, v0, s_min, s, v, v_lead, int(has_leader))
+
+
+def oracle_ballistic(x, v, acc, dt):
+    xo, vo = C.c_float(), C.c_float()
+    lib().orc_ballistic(x, v, acc, dt, C.byref(xo), C.byref(vo))
+    return xo.value, vo.value
+
+
+def oracle_link_cost(length, speed, lanes=1, mode=0):
+    return lib().orc_link_cost(length, speed, lanes, mode)
+
+
+def oracle_sssp(n_nodes, link_from, link_to, cost, origin):
+    lf = np.ascontiguousarray(link_from, np.int32)
+    lt = np.ascontiguousarray(link_to, np.int32)
+    c = np.ascontiguousarray(cost, np.int32)
+    dist = np.zeros(n_nodes, np.int64)
+    _check(lib().orc_sssp(n_nodes, len(lf), _p(lf), _p(lt), _p(c), origin, _p(dist)), "orc_sssp")
+    return dist
+
+
+def oracle_mand_index(seed, vid, hop):
+    return lib().orc_mand_index(seed & (2**64 - 1), vid, hop)
+
+
+def oracle_mand_tau(k):
+    return lib().orc_mand_tau(k)
+
+
+def oracle_turn(a, b, c):
+    return lib().orc_turn(a[0], a[1], b[0], b[1], c[0], c[1])
+
+
+def oracle_signal_green(t, dt_ds, offset, cycle, green, ew):
+    return lib().orc_signal_green(t, dt_ds, offset, cycle, green, int(ew))
