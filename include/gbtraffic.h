@@ -1,0 +1,201 @@
+/* gbtraffic — GB300 (sm_103a) traffic microsimulation hot path, C ABI.
+ *
+ * Implements the time-stepped microsimulation of Waddell et al., "Architecture
+ * for Modular Microsimulation of Real Estate Markets and Transportation",
+ * Sec. 6 ("Traffic microsimulation model"): vehicles follow precomputed
+ * shortest-path routes on a lane-level network (Sec. 6.2.1, 6.3.1), accelerate
+ * by the Intelligent Driver Model (Eq. 7), change lanes (mandatory /
+ * discretionary with gap acceptance, Sec. 6.3.2) and are admitted through stop
+ * signs and traffic lights (Sec. 6.3.2), with dt = 0.5 s (Sec. 6.3.2).
+ *
+ * Conventions
+ *  - All pointers in the input structs are HOST pointers owned by the caller;
+ *    sim_create copies everything it needs to the device, so the caller may free
+ *    its arrays as soon as sim_create returns.
+ *  - A trip id (vid) is the index of the trip in sim_demand; every per-trip
+ *    output is indexed by vid.  Link and node ids are indices into sim_network.
+ *  - Lanes are numbered 0 (rightmost) to lanes-1 (leftmost); at most 8 per link.
+ *  - All device work is ordered on the stream given by sim_set_stream (default:
+ *    the legacy default stream).  A handle is not thread-safe.
+ *  - Every call returns SIM_OK or a negative SIM_E* code; the message of the
+ *    last failure is available from sim_last_error.  No call aborts, throws or
+ *    traps on the device.  Device-side index checks set an error word that the
+ *    next synchronising call reports as SIM_EDEVICE.
+ */
+#ifndef GBTRAFFIC_H
+#define GBTRAFFIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  SIM_OK = 0,
+  SIM_EINVAL = -1,        /* malformed input or argument */
+  SIM_ENOMEM = -2,        /* device or host allocation failed */
+  SIM_ECUDA = -3,         /* a CUDA runtime call failed */
+  SIM_EUNREACHABLE = -4,  /* a trip's destination cannot be reached from its origin */
+  SIM_ETIMEOUT = -5,      /* a bounded device wait expired */
+  SIM_ESTATE = -6,        /* call out of order (e.g. sim_step before routes exist) */
+  SIM_EDEVICE = -7        /* the device error word was set (index out of range, capacity) */
+};
+
+enum { SIM_CTRL_NONE = 0, SIM_CTRL_STOP = 1, SIM_CTRL_SIGNAL = 2 };
+enum { SIM_PENDING = 0, SIM_ACTIVE = 1, SIM_ARRIVED = 2 };
+
+/* Road network (Sec. 6.2.1: nodes = intersections, directed edges = roads with
+ * speed and lanes; Sec. 4: directed multigraph, self-loops allowed). */
+typedef struct {
+  int32_t n_nodes, n_links;
+  const int32_t* node_x_dm;          /* [n_nodes] position, integer decimetres (turns, signal phases) */
+  const int32_t* node_y_dm;          /* [n_nodes] */
+  const uint8_t* node_control;       /* [n_nodes] SIM_CTRL_* */
+  const int32_t* signal_offset_ds;   /* [n_nodes] offset of the fixed-time plan, deciseconds */
+  const int32_t* signal_cycle_ds;    /* [n_nodes] cycle length, deciseconds (1..65535) */
+  const int32_t* signal_green_ds;    /* [n_nodes] north-south green per cycle, deciseconds */
+  const int32_t* link_from;          /* [n_links] tail node */
+  const int32_t* link_to;            /* [n_links] head node */
+  const float* link_length_m;        /* [n_links] > 0 */
+  const float* link_speed_mps;       /* [n_links] speed limit > 0 */
+  const uint8_t* link_lanes;         /* [n_links] 1..8 */
+  const uint8_t* link_class;         /* [n_links] < sim_params.n_class (selects IDM parameters) */
+} sim_network;
+
+/* Travel demand (Sec. 6.2.2: origin, destination and departure time per vehicle). */
+typedef struct {
+  int32_t n_trips;
+  const int32_t* origin;             /* [n_trips] node id */
+  const int32_t* dest;               /* [n_trips] node id, != origin for routed trips */
+  const int32_t* depart_step;        /* [n_trips] earliest step at which the trip may enter */
+} sim_demand;
+
+#define SIM_MAX_CLASS 256
+
+/* Model parameters.  IDM per link class (Eq. 7); v0 <= 0 uses the link speed
+ * limit (Sec. 6.3.2: "v0 is the edge speed limit"). */
+typedef struct {
+  float dt;                          /* step, seconds; dt*10 must be an integer (0.5 in the paper) */
+  float veh_len;                     /* vehicle length, m */
+  float s_min;                       /* floor of the bumper gap in Eq. 7, m */
+  int32_t n_class;                   /* 1..SIM_MAX_CLASS */
+  const float *v0, *T, *a, *b, *s0;  /* [n_class] host arrays */
+  float mobil_p, mobil_athr, mobil_bsafe, mobil_bias_right;  /* lane-change incentive / safety */
+  float lambda_mand;                 /* mandatory-switch length scale per lane to cross, m */
+  float stop_acquire_m;              /* distance to the stop line within which a stop is acquired, m */
+  uint64_t seed;                     /* draws of the mandatory-switch distance */
+  int32_t cost_mode;                 /* 0: free-flow length/speed; 1: sqrt(lanes)*length/speed */
+  int32_t loop_routes;               /* 1: routes repeat forever (ring roads) */
+} sim_params;
+
+typedef struct sim_handle sim_handle;
+
+/* Counters after the last completed step. */
+typedef struct {
+  int64_t t;            /* steps simulated since the state was set */
+  int64_t departed;     /* trips that entered the network */
+  int64_t waiting;      /* due trips (depart_step < t) not yet on the network */
+  int64_t active;       /* vehicles on the network now */
+  int64_t arrived;      /* trips that reached their destination */
+  int64_t veh_steps;    /* sum over steps of the vehicles advanced in that step */
+  int64_t pending;      /* trips not yet due */
+  int64_t active_last;  /* vehicles advanced in the last step */
+} sim_counters_t;
+
+/* Field bits for sim_read_state. */
+enum {
+  SIM_F_STATUS = 1 << 0, SIM_F_LINK = 1 << 1, SIM_F_LANE = 1 << 2, SIM_F_CURSOR = 1 << 3,
+  SIM_F_X = 1 << 4, SIM_F_V = 1 << 5, SIM_F_INSERT = 1 << 6, SIM_F_ARRIVE = 1 << 7,
+  SIM_F_LANECHANGE = 1 << 8
+};
+
+/* Per-trip state view.  Each pointer addresses n_trips elements (or is NULL when
+ * its field is not requested).  Non-active trips read link -1, lane 0, cursor 0,
+ * x 0, v 0. */
+typedef struct {
+  uint8_t* status;      /* SIM_PENDING / SIM_ACTIVE / SIM_ARRIVED */
+  int32_t* link;        /* current link */
+  int32_t* lane;        /* current lane */
+  int32_t* cursor;      /* index of the current link in the trip's route */
+  float* x;             /* distance from the start of the link, m, in [0, length] */
+  float* v;             /* speed, m/s */
+  int32_t* insert_step; /* step at which the trip entered (-1: not yet; 0 for written state) */
+  int32_t* arrive_step; /* step at which the trip arrived (-1: not yet) */
+  int8_t* lane_change;  /* lane change applied in the last step: -1 right, +1 left, 0 none */
+} sim_state_view;
+
+/* Create a simulation.  Validates and deep-copies the inputs to the device of the
+ * current CUDA context.  Errors: SIM_EINVAL (bad ids, lengths, lanes, classes,
+ * dt), SIM_ENOMEM, SIM_ECUDA.  *out is NULL on failure. */
+int sim_create(const sim_network* net, const sim_demand* dem, const sim_params* par, sim_handle** out);
+
+/* Create one simulation over the disjoint union of n scenarios (independent
+ * networks and demands with their own parameters), advanced together by every
+ * sim_step.  Trip t of scenario k has vid = (sum of n_trips of scenarios < k) + t;
+ * node, link and class ids are offset the same way.  Each scenario evolves exactly
+ * as it would in its own handle.  All scenarios must share dt and loop_routes. */
+int sim_create_batch(int32_t n, const sim_network* const* nets, const sim_demand* const* dems,
+                     const sim_params* const* pars, sim_handle** out);
+
+/* Order all further device work of the handle on this cudaStream_t (NULL = legacy
+ * default stream). */
+int sim_set_stream(sim_handle* h, void* cuda_stream);
+
+/* Trip planning (Sec. 6.3.1, Sec. 6 "Simulation scale"): one shortest-path tree per
+ * distinct origin on the GPU (near-far delta-stepping on integer link costs), and
+ * for every trip the path origin -> destination.  Among equally short paths, the
+ * walk back from the destination takes the lowest-id in-link u->v with
+ * dist[u] + cost = dist[v].  link_cost_ds: host array [n_links] of costs >= 1 in
+ * deciseconds, or NULL for the free-flow cost of Eq. 4,
+ * max(1, floor(10*length/speed + 0.5)) (cost_mode 1: times sqrt(lanes)).
+ * Resets the vehicle state: all trips pending, t = 0.
+ * Errors: SIM_EINVAL (cost < 1, origin == dest), SIM_EUNREACHABLE, SIM_ENOMEM. */
+int sim_route(sim_handle* h, const int32_t* link_cost_ds);
+
+/* Set explicit routes instead: host CSR offsets [n_trips+1] and link ids; each
+ * route must be a connected link sequence (and a cycle when loop_routes).
+ * Resets the vehicle state like sim_route. */
+int sim_set_routes(sim_handle* h, const int32_t* offsets, const int32_t* links);
+
+/* Total number of route hops (for sizing sim_read_routes). */
+int sim_route_size(sim_handle* h, int64_t* n_hops);
+
+/* Copy routes to host: offsets [n_trips+1], links [n_hops], in trip order. */
+int sim_read_routes(sim_handle* h, int32_t* offsets, int32_t* links);
+
+/* Advance the simulation by n_steps steps of dt.  All steps run on the device
+ * without a host round trip.  Errors: SIM_ESTATE (no routes), SIM_EDEVICE. */
+int sim_step(sim_handle* h, int32_t n_steps);
+
+/* Read the per-trip state (fields = OR of SIM_F_*).  on_device = 1: the view's
+ * pointers are device pointers (e.g. from torch tensors) of n_trips elements each;
+ * on_device = 0: host pointers.  The call synchronises the stream. */
+int sim_read_state(sim_handle* h, const sim_state_view* out, uint32_t fields, int on_device);
+
+/* Replace the vehicle state (resume, tests).  Host arrays [n_trips]: status,
+ * link, lane, cursor, x, v (only SIM_ACTIVE trips need link..v).  Active trips
+ * must sit on route[cursor] with 0 <= x <= length; pending trips re-enter the
+ * departure queues; t, counters and stop-sign holders are reset. */
+int sim_write_state(sim_handle* h, const uint8_t* status, const int32_t* link, const int32_t* lane,
+                    const int32_t* cursor, const float* x, const float* v);
+
+/* Per-lane occupancy of the current state, the sorted order the next step uses:
+ * lane_start [n_lanes+1] and sorted_vid [active] (lanes are numbered link by link,
+ * lane 0 first; within a lane by position, then vid).  Host arrays. */
+int sim_occupancy(sim_handle* h, int32_t* lane_start, int32_t* sorted_vid);
+int sim_n_lanes(sim_handle* h, int64_t* n_lanes);
+
+int sim_counters(sim_handle* h, sim_counters_t* out);
+
+/* Message of the last failed call on this handle (or of the last failed
+ * sim_create when h is NULL). */
+const char* sim_last_error(const sim_handle* h);
+
+void sim_destroy(sim_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,904 @@
+// C-ABI of libgbtraffic (declared in include/gbtraffic.h): input validation, network
+// preprocessing, device memory, the trip-planning driver and the CUDA-graph step loop.
+// Waddell et al., Sec. 6 ("Traffic microsimulation model").
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gbt_internal.cuh"
+#include "gbtraffic.h"
+
+namespace gbt {
+void launch_step(const Dev& d, int grid, bool has_stop, cudaStream_t s);
+void launch_occupancy(const Dev& d, int grid, cudaStream_t s);
+int scan_blocks(int n_lanes);
+void launch_state_out(const Dev& d, int grid, cudaStream_t s, uint8_t* status, int32_t* link, int32_t* lane,
+                      int32_t* cursor, float* x, float* v, int32_t* ins, int32_t* arr, int8_t* dec);
+void launch_state_in(const Dev& d, int grid, cudaStream_t s, const uint8_t* status, const int32_t* link,
+                     const int32_t* lane, const int32_t* cursor, const float* x, const float* v);
+void launch_occ_out(const Dev& d, int grid, cudaStream_t s, int32_t* sorted_vid);
+void launch_first_links(const int32_t* roff, const int32_t* routes, int n, int32_t* out, cudaStream_t s);
+}  // namespace gbt
+
+using namespace gbt;
+
+static std::string g_create_error;
+
+struct sim_handle {
+  std::string err;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  int device = 0, sm_count = 0, grid = 0;
+  // sizes
+  int nn = 0, nl = 0, nt = 0, n_lanes = 0, ncls = 0;
+  bool has_stop = false;
+  // host copies
+  std::vector<int32_t> lfrom, lto, depart, origin, dest;
+  std::vector<float> len, spd;
+  std::vector<uint8_t> lanes;
+  std::vector<int32_t> lane_base;
+  int cost_mode = 0, loop = 0;
+  // device
+  std::vector<void*> allocs;
+  Dev d{};
+  int32_t* routes = nullptr;
+  unsigned long long route_cap = 0;
+  int32_t* q_items = nullptr;
+  int32_t* q_end = nullptr;
+  int32_t* q_head = nullptr;
+  int32_t* qlinks = nullptr;
+  bool routed = false;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph = nullptr;
+  bool graph_dirty = true;
+};
+
+namespace {
+
+int fail(sim_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+int cuda_fail(sim_handle* h, cudaError_t e, const char* what) {
+  return fail(h, e == cudaErrorMemoryAllocation ? SIM_ENOMEM : SIM_ECUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                   \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);         \
+  } while (0)
+
+template <class T>
+int dalloc(sim_handle* h, T** p, size_t n) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, (n ? n : 1) * sizeof(T));
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
+  h->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return SIM_OK;
+}
+
+void dfree(sim_handle* h, void* p) {
+  if (!p) return;
+  auto it = std::find(h->allocs.begin(), h->allocs.end(), p);
+  if (it != h->allocs.end()) h->allocs.erase(it);
+  cudaFree(p);
+}
+
+template <class T>
+int upload(sim_handle* h, T** p, const T* src, size_t n) {
+  int rc = dalloc(h, p, n);
+  if (rc) return rc;
+  if (n) CK(cudaMemcpy(*p, src, n * sizeof(T), cudaMemcpyHostToDevice));
+  return SIM_OK;
+}
+
+// ------------------------------------------------------------------ union of scenarios
+struct Flat {
+  int nn = 0, nl = 0, nt = 0, ncls = 0;
+  std::vector<int32_t> nx, ny, off, cyc, grn, lf, lt, orig, dest, dep;
+  std::vector<uint8_t> ctrl, lanes, cls;
+  std::vector<float> len, spd, v0, T, a, b, s0;
+  std::vector<unsigned long long> hseed;
+  sim_params p{};
+};
+
+int flatten(int n, const sim_network* const* nets, const sim_demand* const* dems, const sim_params* const* pars,
+            Flat& F) {
+  if (n <= 0 || !nets || !dems || !pars) return fail(nullptr, SIM_EINVAL, "null or empty scenario list");
+  for (int k = 0; k < n; k++) {
+    const sim_network* N = nets[k];
+    const sim_demand* D = dems[k];
+    const sim_params* P = pars[k];
+    if (!N || !D || !P) return fail(nullptr, SIM_EINVAL, "null scenario input");
+    if (N->n_nodes <= 0 || N->n_links <= 0 || D->n_trips < 0)
+      return fail(nullptr, SIM_EINVAL, "n_nodes and n_links must be > 0, n_trips >= 0");
+    if (!N->node_x_dm || !N->node_y_dm || !N->node_control || !N->signal_offset_ds || !N->signal_cycle_ds ||
+        !N->signal_green_ds || !N->link_from || !N->link_to || !N->link_length_m || !N->link_speed_mps ||
+        !N->link_lanes || !N->link_class)
+      return fail(nullptr, SIM_EINVAL, "null network array");
+    if (D->n_trips > 0 && (!D->origin || !D->dest || !D->depart_step))
+      return fail(nullptr, SIM_EINVAL, "null demand array");
+    if (P->n_class <= 0 || P->n_class > SIM_MAX_CLASS || !P->v0 || !P->T || !P->a || !P->b || !P->s0)
+      return fail(nullptr, SIM_EINVAL, "bad parameter classes");
+    if (k == 0) {
+      F.p = *P;
+    } else {
+      const sim_params& Q = F.p;
+      if (P->dt != Q.dt || P->veh_len != Q.veh_len || P->s_min != Q.s_min || P->mobil_p != Q.mobil_p ||
+          P->mobil_athr != Q.mobil_athr || P->mobil_bsafe != Q.mobil_bsafe ||
+          P->mobil_bias_right != Q.mobil_bias_right || P->lambda_mand != Q.lambda_mand ||
+          P->stop_acquire_m != Q.stop_acquire_m || P->cost_mode != Q.cost_mode || P->loop_routes != Q.loop_routes)
+        return fail(nullptr, SIM_EINVAL, "batched scenarios must share dt and all scalar parameters");
+    }
+    const int nb = F.nn, lb = F.nl, cb = F.ncls;
+    for (int i = 0; i < N->n_nodes; i++) {
+      F.nx.push_back(N->node_x_dm[i]);
+      F.ny.push_back(N->node_y_dm[i]);
+      F.ctrl.push_back(N->node_control[i]);
+      F.off.push_back(N->signal_offset_ds[i]);
+      F.cyc.push_back(N->signal_cycle_ds[i]);
+      F.grn.push_back(N->signal_green_ds[i]);
+    }
+    for (int e = 0; e < N->n_links; e++) {
+      if (N->link_from[e] < 0 || N->link_from[e] >= N->n_nodes || N->link_to[e] < 0 || N->link_to[e] >= N->n_nodes)
+        return fail(nullptr, SIM_EINVAL, "link end node out of range");
+      if (N->link_class[e] >= P->n_class) return fail(nullptr, SIM_EINVAL, "link class out of range");
+      F.lf.push_back(N->link_from[e] + nb);
+      F.lt.push_back(N->link_to[e] + nb);
+      F.len.push_back(N->link_length_m[e]);
+      F.spd.push_back(N->link_speed_mps[e]);
+      F.lanes.push_back(N->link_lanes[e]);
+      F.cls.push_back((uint8_t)(N->link_class[e] + cb));
+    }
+    for (int c = 0; c < P->n_class; c++) {
+      F.v0.push_back(P->v0[c]);
+      F.T.push_back(P->T[c]);
+      F.a.push_back(P->a[c]);
+      F.b.push_back(P->b[c]);
+      F.s0.push_back(P->s0[c]);
+    }
+    for (int i = 0; i < D->n_trips; i++) {
+      if (D->origin[i] < 0 || D->origin[i] >= N->n_nodes || D->dest[i] < 0 || D->dest[i] >= N->n_nodes)
+        return fail(nullptr, SIM_EINVAL, "trip origin/destination out of range");
+      F.orig.push_back(D->origin[i] + nb);
+      F.dest.push_back(D->dest[i] + nb);
+      F.dep.push_back(D->depart_step[i]);
+      // hash base of the mandatory-switch draw: scenario seed and scenario-local trip id
+      F.hseed.push_back((unsigned long long)P->seed ^ ((unsigned long long)(uint32_t)i << 32));
+    }
+    F.nn += N->n_nodes;
+    F.nl += N->n_links;
+    F.nt += D->n_trips;
+    F.ncls += P->n_class;
+    if (F.ncls > SIM_MAX_CLASS) return fail(nullptr, SIM_EINVAL, "too many parameter classes in batch");
+    (void)lb;
+  }
+  return SIM_OK;
+}
+
+int create_from_flat(Flat& F, sim_handle** out) {
+  *out = nullptr;
+  const sim_params& P = F.p;
+  if (!(P.dt > 0.0f)) return fail(nullptr, SIM_EINVAL, "dt must be > 0");
+  const int dt_ds = (int)lrintf(P.dt * 10.0f);
+  if (dt_ds <= 0 || fabsf((float)dt_ds - P.dt * 10.0f) > 1e-3f)
+    return fail(nullptr, SIM_EINVAL, "dt must be a whole number of deciseconds");
+  if (!(P.veh_len > 0.0f) || !(P.s_min > 0.0f)) return fail(nullptr, SIM_EINVAL, "veh_len and s_min must be > 0");
+  for (int c = 0; c < F.ncls; c++)
+    if (!(F.a[c] > 0.0f) || !(F.b[c] > 0.0f) || !(F.T[c] >= 0.0f) || !(F.s0[c] >= 0.0f))
+      return fail(nullptr, SIM_EINVAL, "IDM parameters must satisfy a > 0, b > 0, T >= 0, s0 >= 0");
+  for (int i = 0; i < F.nn; i++) {
+    if (F.ctrl[i] > 2) return fail(nullptr, SIM_EINVAL, "node_control must be 0, 1 or 2");
+    if (F.ctrl[i] == SIM_CTRL_SIGNAL && (F.cyc[i] <= 0 || F.cyc[i] > 65535 || F.grn[i] < 0 || F.grn[i] > 65535))
+      return fail(nullptr, SIM_EINVAL, "signal cycle must be 1..65535 ds and green 0..65535 ds");
+  }
+  for (int e = 0; e < F.nl; e++) {
+    if (F.lanes[e] < 1 || F.lanes[e] > 8) return fail(nullptr, SIM_EINVAL, "lanes must be 1..8");
+    if (!(F.len[e] > 0.0f) || !(F.spd[e] > 0.0f)) return fail(nullptr, SIM_EINVAL, "length and speed must be > 0");
+    const float v0 = F.v0[F.cls[e]] > 0.0f ? F.v0[F.cls[e]] : F.spd[e];
+    if (!(v0 > 0.0f)) return fail(nullptr, SIM_EINVAL, "desired speed must be > 0");
+  }
+
+  sim_handle* h = new sim_handle();
+  h->nn = F.nn;
+  h->nl = F.nl;
+  h->nt = F.nt;
+  h->ncls = F.ncls;
+  h->cost_mode = P.cost_mode;
+  h->loop = P.loop_routes ? 1 : 0;
+  h->lfrom = F.lf;
+  h->lto = F.lt;
+  h->len = F.len;
+  h->spd = F.spd;
+  h->lanes = F.lanes;
+  h->depart = F.dep;
+  h->origin = F.orig;
+  h->dest = F.dest;
+  cudaGetDevice(&h->device);
+  cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+  if (h->sm_count <= 0) h->sm_count = 1;
+  h->grid = h->sm_count * 8;
+
+  // in-links of every node in ascending link id -> round-robin index, in-degree
+  std::vector<int> n_in(F.nn, 0), in_index(F.nl, 0);
+  for (int e = 0; e < F.nl; e++) in_index[e] = n_in[F.lt[e]]++;
+  for (int i = 0; i < F.nn; i++)
+    if (n_in[i] > 255) {
+      delete h;
+      return fail(nullptr, SIM_EINVAL, "node in-degree above 255");
+    }
+  std::vector<LinkRec> recs(F.nl);
+  h->lane_base.resize(F.nl + 1);
+  int nlan = 0;
+  for (int e = 0; e < F.nl; e++) {
+    LinkRec& r = recs[e];
+    memset(&r, 0, sizeof(r));
+    r.len = F.len[e];
+    r.v0 = F.v0[F.cls[e]] > 0.0f ? F.v0[F.cls[e]] : F.spd[e];
+    r.lane_base = nlan;
+    h->lane_base[e] = nlan;
+    nlan += F.lanes[e];
+    const int n = F.lt[e];
+    r.to = n;
+    r.lanes = F.lanes[e];
+    r.cls = F.cls[e];
+    r.ctrl = F.ctrl[n];
+    long long dx = (long long)F.nx[n] - F.nx[F.lf[e]], dy = (long long)F.ny[n] - F.ny[F.lf[e]];
+    r.ew = (llabs(dx) >= llabs(dy)) ? 1 : 0;
+    r.in_index = (uint8_t)in_index[e];
+    r.n_in = (uint8_t)n_in[n];
+    r.sig_cyc = (uint16_t)(F.ctrl[n] == SIM_CTRL_SIGNAL ? F.cyc[n] : 1);
+    r.sig_off = F.off[n];
+    r.sig_grn = (uint16_t)(F.ctrl[n] == SIM_CTRL_SIGNAL ? F.grn[n] : 0);
+    if (F.ctrl[n] == SIM_CTRL_STOP) h->has_stop = true;
+  }
+  h->lane_base[F.nl] = nlan;
+  h->n_lanes = nlan;
+  std::vector<ClassPar> cp(F.ncls);
+  for (int c = 0; c < F.ncls; c++) {
+    float sab = sqrtf(F.a[c] * F.b[c]);
+    cp[c] = ClassPar{F.a[c], 2.0f * sab, F.T[c], F.s0[c]};
+  }
+  // mandatory-switch table: tau[k] = sqrt(-ln((k + 0.5) / 256)) in binary64, rounded once
+  std::vector<float> tau(256);
+  for (int k = 0; k < 256; k++) tau[k] = (float)std::sqrt(-std::log(((double)k + 0.5) / 256.0));
+
+  Dev& d = h->d;
+  int rc = SIM_OK;
+#define TRY(x)            \
+  do {                    \
+    rc = (x);             \
+    if (rc) goto fail_rc; \
+  } while (0)
+  {
+    LinkRec* links;
+    ClassPar* cls;
+    float* taud;
+    TRY(upload(h, &links, recs.data(), recs.size()));
+    TRY(upload(h, &cls, cp.data(), cp.size()));
+    TRY(upload(h, &taud, tau.data(), tau.size()));
+    d.links = links;
+    d.cls = cls;
+    d.tau = taud;
+    int32_t *lf, *nx, *ny, *dep;
+    unsigned long long* hs;
+    TRY(upload(h, &lf, F.lf.data(), F.lf.size()));
+    TRY(upload(h, &nx, F.nx.data(), F.nx.size()));
+    TRY(upload(h, &ny, F.ny.data(), F.ny.size()));
+    TRY(upload(h, &dep, F.dep.data(), F.dep.size()));
+    TRY(upload(h, &hs, F.hseed.data(), F.hseed.size()));
+    d.lfrom = lf;
+    d.node_x = nx;
+    d.node_y = ny;
+    d.depart = dep;
+    d.hseed = hs;
+    d.n_links = F.nl;
+    d.n_nodes = F.nn;
+    d.n_lanes = nlan;
+    d.n_trips = F.nt;
+    d.dt = P.dt;
+    d.hdt2 = (0.5f * P.dt) * P.dt;
+    d.vlen = P.veh_len;
+    d.s_min = P.s_min;
+    d.zone = 2.0f * P.veh_len;
+    d.mp = P.mobil_p;
+    d.mathr = P.mobil_athr;
+    d.mbsafe = P.mobil_bsafe;
+    d.mbias = P.mobil_bias_right;
+    d.lam = P.lambda_mand;
+    d.stop_acq = P.stop_acquire_m;
+    d.dt_ds = dt_ds;
+    d.loop = h->loop;
+    const size_t nt = (size_t)F.nt;
+    TRY(dalloc(h, &d.status, nt));
+    TRY(dalloc(h, &d.ins_step, nt));
+    TRY(dalloc(h, &d.arr_step, nt));
+    TRY(dalloc(h, &d.dec, nt));
+    int32_t *roff, *rlen;
+    TRY(dalloc(h, &roff, nt));
+    TRY(dalloc(h, &rlen, nt));
+    d.roff = roff;
+    d.rlen = rlen;
+    VehBuf* bufs[2] = {&d.A, &d.B};
+    for (VehBuf* b : bufs) {
+      TRY(dalloc(h, &b->x, nt));
+      TRY(dalloc(h, &b->v, nt));
+      TRY(dalloc(h, &b->vid, nt));
+      TRY(dalloc(h, &b->link, nt));
+      TRY(dalloc(h, &b->nxt, nt));
+      TRY(dalloc(h, &b->cur, nt));
+      TRY(dalloc(h, &b->lane, nt));
+    }
+    TRY(dalloc(h, &d.aidx, nt));
+    TRY(dalloc(h, &d.tx, nt));
+    TRY(dalloc(h, &d.tvid, nt));
+    TRY(dalloc(h, &d.tsrc, nt));
+    TRY(dalloc(h, &d.tg, nt));
+    TRY(dalloc(h, &d.a_own, nt));
+    TRY(dalloc(h, &d.xo, nt));
+    TRY(dalloc(h, &d.at, nt));
+    TRY(dalloc(h, &d.intent, nt));
+    TRY(dalloc(h, &d.flags, nt));
+    TRY(dalloc(h, &d.cnt, (size_t)nlan));
+    TRY(dalloc(h, &d.lane_start, (size_t)nlan + 1));
+    TRY(dalloc(h, &d.bsum, (size_t)scan_blocks(nlan) + 1));
+    TRY(dalloc(h, &d.best, (size_t)nlan));
+    TRY(dalloc(h, &d.holder, (size_t)F.nn));
+    TRY(dalloc(h, &d.acq, (size_t)F.nn));
+    TRY(dalloc(h, &d.ctl, 1));
+    if (cudaMemset(d.cnt, 0, (size_t)nlan * 4) != cudaSuccess ||
+        cudaMemset(d.best, 0xFF, (size_t)nlan * 8) != cudaSuccess ||
+        cudaMemset(d.acq, 0xFF, (size_t)F.nn * 8) != cudaSuccess ||
+        cudaMemset(d.holder, 0xFF, (size_t)F.nn * 4) != cudaSuccess ||
+        cudaMemset(d.ctl, 0, sizeof(Ctl)) != cudaSuccess ||
+        cudaMemset(d.A.link, 0xFF, nt ? nt * 4 : 4) != cudaSuccess ||
+        cudaMemset(d.status, 0, nt ? nt : 1) != cudaSuccess) {
+      rc = fail(h, SIM_ECUDA, "initial cudaMemset failed");
+      goto fail_rc;
+    }
+    if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      rc = fail(h, SIM_ECUDA, "cudaStreamCreate failed");
+      goto fail_rc;
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+      rc = fail(h, SIM_ECUDA, "device synchronize after create failed");
+      goto fail_rc;
+    }
+  }
+  *out = h;
+  return SIM_OK;
+fail_rc:
+  g_create_error = h->err;
+  sim_destroy(h);
+  return rc;
+#undef TRY
+}
+
+// ------------------------------------------------------------------ queues
+// Departure queues: per first link, the trips still pending in (depart_step, vid) order.
+int build_queues(sim_handle* h, const std::vector<uint8_t>& status) {
+  const int nt = h->nt, nl = h->nl;
+  std::vector<int32_t> first(nt > 0 ? nt : 1);
+  if (nt > 0) {
+    int32_t* dfirst;
+    int rc = dalloc(h, &dfirst, (size_t)nt);
+    if (rc) return rc;
+    launch_first_links(h->d.roff, h->routes, nt, dfirst, h->stream);
+    cudaError_t e = cudaMemcpyAsync(first.data(), dfirst, (size_t)nt * 4, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    dfree(h, dfirst);
+    if (e != cudaSuccess) return cuda_fail(h, e, "first links");
+  }
+  // stable counting sort by depart_step (vid order kept), then stable by first link
+  std::vector<int32_t> order;
+  order.reserve(nt);
+  for (int i = 0; i < nt; i++)
+    if (status[i] == SIM_PENDING) order.push_back(i);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return h->depart[a] < h->depart[b]; });
+  std::vector<int32_t> qstart(nl + 1, 0);
+  for (int i : order) qstart[first[i] + 1]++;
+  for (int e = 0; e < nl; e++) qstart[e + 1] += qstart[e];
+  std::vector<int32_t> items(order.size() > 0 ? order.size() : 1), fill(qstart.begin(), qstart.end() - 1);
+  for (int i : order) items[fill[first[i]]++] = i;
+  std::vector<int32_t> qend(nl), qhead(nl), ql;
+  for (int e = 0; e < nl; e++) {
+    qhead[e] = qstart[e];
+    qend[e] = qstart[e + 1];
+    if (qend[e] > qhead[e]) ql.push_back(e);
+  }
+  dfree(h, h->q_items);
+  dfree(h, h->q_end);
+  dfree(h, h->q_head);
+  dfree(h, h->qlinks);
+  h->q_items = h->q_end = h->q_head = h->qlinks = nullptr;
+  int rc;
+  if ((rc = upload(h, &h->q_items, items.data(), items.size()))) return rc;
+  if ((rc = upload(h, &h->q_end, qend.data(), qend.size()))) return rc;
+  if ((rc = upload(h, &h->q_head, qhead.data(), qhead.size()))) return rc;
+  if ((rc = upload(h, &h->qlinks, ql.data(), ql.size()))) return rc;
+  h->d.q_items = h->q_items;
+  h->d.q_end = h->q_end;
+  h->d.q_head = h->q_head;
+  h->d.qlinks = h->qlinks;
+  h->d.n_qlinks = (int)ql.size();
+  h->graph_dirty = true;
+  return SIM_OK;
+}
+
+// Reset the dynamic state: all trips pending, no vehicles, t = 0.
+int reset_dynamic(sim_handle* h) {
+  Dev& d = h->d;
+  const size_t nt = (size_t)h->nt;
+  CK(cudaMemsetAsync(d.status, 0, nt ? nt : 1, h->stream));
+  CK(cudaMemsetAsync(d.ins_step, 0xFF, (nt ? nt : 1) * 4, h->stream));
+  CK(cudaMemsetAsync(d.arr_step, 0xFF, (nt ? nt : 1) * 4, h->stream));
+  CK(cudaMemsetAsync(d.dec, 0, nt ? nt : 1, h->stream));
+  CK(cudaMemsetAsync(d.holder, 0xFF, (size_t)h->nn * 4, h->stream));
+  CK(cudaMemsetAsync(d.acq, 0xFF, (size_t)h->nn * 8, h->stream));
+  CK(cudaMemsetAsync(d.best, 0xFF, (size_t)h->n_lanes * 8, h->stream));
+  CK(cudaMemsetAsync(d.cnt, 0, (size_t)h->n_lanes * 4, h->stream));
+  CK(cudaMemsetAsync(d.ctl, 0, sizeof(Ctl), h->stream));
+  return SIM_OK;
+}
+
+int check_device(sim_handle* h) {
+  Ctl c;
+  CK(cudaMemcpyAsync(&c, h->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (c.err) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "device error word 0x%x (info %d) at step %lld", c.err, c.err_info, c.t);
+    return fail(h, SIM_EDEVICE, buf);
+  }
+  return SIM_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+int sim_create(const sim_network* net, const sim_demand* dem, const sim_params* par, sim_handle** out) {
+  if (!out) return fail(nullptr, SIM_EINVAL, "out is NULL");
+  *out = nullptr;
+  Flat F;
+  int rc = flatten(1, &net, &dem, &par, F);
+  if (rc) return rc;
+  return create_from_flat(F, out);
+}
+
+int sim_create_batch(int32_t n, const sim_network* const* nets, const sim_demand* const* dems,
+                     const sim_params* const* pars, sim_handle** out) {
+  if (!out) return fail(nullptr, SIM_EINVAL, "out is NULL");
+  *out = nullptr;
+  Flat F;
+  int rc = flatten(n, nets, dems, pars, F);
+  if (rc) return rc;
+  return create_from_flat(F, out);
+}
+
+int sim_set_stream(sim_handle* h, void* stream) {
+  if (!h) return SIM_EINVAL;
+  h->stream = (cudaStream_t)stream;
+  return SIM_OK;
+}
+
+int sim_route(sim_handle* h, const int32_t* link_cost_ds) {
+  if (!h) return SIM_EINVAL;
+  const int nn = h->nn, nl = h->nl, nt = h->nt;
+  std::vector<int32_t> cost(nl);
+  long long cmax = 1;
+  for (int e = 0; e < nl; e++) {
+    if (link_cost_ds) {
+      cost[e] = link_cost_ds[e];
+    } else {
+      // Eq. 4: t0 = d / s, in deciseconds rounded half up, at least 1 (binary64)
+      const double dd = (double)h->len[e], ss = (double)h->spd[e];
+      const double tt = h->cost_mode == 1 ? ((10.0 * std::sqrt((double)h->lanes[e])) * dd) / ss : (10.0 * dd) / ss;
+      double c = std::floor(tt + 0.5);
+      if (c < 1.0) c = 1.0;
+      if (c > 1.0e6) c = 1.0e6;
+      cost[e] = (int32_t)c;
+    }
+    if (cost[e] < 1 || cost[e] > 1000000) return fail(h, SIM_EINVAL, "link costs must be 1..1e6 ds");
+    cmax = std::max<long long>(cmax, cost[e]);
+  }
+  if ((long long)nn * cmax >= 2000000000LL) return fail(h, SIM_EINVAL, "path costs could overflow int32");
+  for (int i = 0; i < nt; i++)
+    if (h->origin[i] == h->dest[i]) return fail(h, SIM_EINVAL, "trip with origin == destination");
+  // CSR of out-links and in-links (ascending link id), trips by origin
+  std::vector<int32_t> os(nn + 1, 0), ol(nl), is(nn + 1, 0), il(nl), ts(nn + 1, 0), tl(nt > 0 ? nt : 1);
+  for (int e = 0; e < nl; e++) {
+    os[h->lfrom[e] + 1]++;
+    is[h->lto[e] + 1]++;
+  }
+  for (int i = 0; i < nt; i++) ts[h->origin[i] + 1]++;
+  for (int v = 0; v < nn; v++) {
+    os[v + 1] += os[v];
+    is[v + 1] += is[v];
+    ts[v + 1] += ts[v];
+  }
+  {
+    std::vector<int32_t> fo(os.begin(), os.end() - 1), fi(is.begin(), is.end() - 1), ft(ts.begin(), ts.end() - 1);
+    for (int e = 0; e < nl; e++) {
+      ol[fo[h->lfrom[e]]++] = e;
+      il[fi[h->lto[e]]++] = e;
+    }
+    for (int i = 0; i < nt; i++) tl[ft[h->origin[i]]++] = i;
+  }
+  std::vector<int32_t> origins;
+  for (int v = 0; v < nn; v++)
+    if (ts[v + 1] > ts[v]) origins.push_back(v);
+  long long csum = 0;
+  for (int e = 0; e < nl; e++) csum += cost[e];
+  const int delta = (int)std::max<long long>(1, csum / std::max(1, nl));
+
+  const int n_cta = std::max(1, std::min<int>((int)origins.size(), h->sm_count * 2));
+  std::vector<void*> tmp;
+  auto talloc = [&](auto** p, size_t n) -> int {
+    int rc = dalloc(h, p, n);
+    if (!rc) tmp.push_back(*p);
+    return rc;
+  };
+  auto cleanup = [&]() {
+    for (void* p : tmp) dfree(h, p);
+    tmp.clear();
+  };
+  RouteDev R{};
+  int rc = SIM_OK;
+  int32_t *dos, *dol, *dis, *dil, *dlt, *dcost, *dorig, *dts, *dtl, *ddest;
+  if ((rc = talloc(&dos, os.size())) || (rc = talloc(&dol, ol.size())) || (rc = talloc(&dis, is.size())) ||
+      (rc = talloc(&dil, il.size())) || (rc = talloc(&dlt, (size_t)nl)) || (rc = talloc(&dcost, (size_t)nl)) ||
+      (rc = talloc(&dorig, origins.size() + 1)) || (rc = talloc(&dts, ts.size())) ||
+      (rc = talloc(&dtl, tl.size())) || (rc = talloc(&ddest, (size_t)std::max(1, nt)))) {
+    cleanup();
+    return rc;
+  }
+  cudaMemcpy(dos, os.data(), os.size() * 4, cudaMemcpyHostToDevice);
+  cudaMemcpy(dol, ol.data(), ol.size() * 4, cudaMemcpyHostToDevice);
+  cudaMemcpy(dis, is.data(), is.size() * 4, cudaMemcpyHostToDevice);
+  cudaMemcpy(dil, il.data(), il.size() * 4, cudaMemcpyHostToDevice);
+  cudaMemcpy(dlt, h->lto.data(), (size_t)nl * 4, cudaMemcpyHostToDevice);
+  cudaMemcpy(dcost, cost.data(), (size_t)nl * 4, cudaMemcpyHostToDevice);
+  if (!origins.empty()) cudaMemcpy(dorig, origins.data(), origins.size() * 4, cudaMemcpyHostToDevice);
+  cudaMemcpy(dts, ts.data(), ts.size() * 4, cudaMemcpyHostToDevice);
+  cudaMemcpy(dtl, tl.data(), tl.size() * 4, cudaMemcpyHostToDevice);
+  if (nt) cudaMemcpy(ddest, h->dest.data(), (size_t)nt * 4, cudaMemcpyHostToDevice);
+  const size_t per = (size_t)n_cta * (size_t)nn;
+  unsigned long long* ddist;
+  int32_t *qf, *ff, *qa, *qb, *fa, *fb, *cround;
+  unsigned* cep;
+  int* work;
+  if ((rc = talloc(&ddist, per)) || (rc = talloc(&qf, per)) || (rc = talloc(&ff, per)) || (rc = talloc(&qa, per)) ||
+      (rc = talloc(&qb, per)) || (rc = talloc(&fa, per)) || (rc = talloc(&fb, per)) ||
+      (rc = talloc(&cround, (size_t)n_cta)) || (rc = talloc(&cep, (size_t)n_cta)) || (rc = talloc(&work, 1))) {
+    cleanup();
+    return rc;
+  }
+  cudaMemset(ddist, 0xFF, per * 8);
+  cudaMemset(qf, 0, per * 4);
+  cudaMemset(ff, 0, per * 4);
+  cudaMemset(cround, 0, (size_t)n_cta * 4);
+  cudaMemset(cep, 0, (size_t)n_cta * 4);
+  R.nn = nn;
+  R.nl = nl;
+  R.out_start = dos;
+  R.out_link = dol;
+  R.in_start = dis;
+  R.in_link = dil;
+  R.lfrom = h->d.lfrom;
+  R.lto = dlt;
+  R.cost = dcost;
+  R.origins = dorig;
+  R.n_origins = (int)origins.size();
+  R.otrip_start = dts;
+  R.otrip_list = dtl;
+  R.dest = ddest;
+  R.dist = ddist;
+  R.qflag = qf;
+  R.fflag = ff;
+  R.qa = qa;
+  R.qb = qb;
+  R.fa = fa;
+  R.fb = fb;
+  R.cta_epoch = cep;
+  R.cta_round = cround;
+  R.roff = const_cast<int32_t*>(h->d.roff);
+  R.rlen = const_cast<int32_t*>(h->d.rlen);
+  R.work = work;
+  R.delta = delta;
+  R.ctl = h->d.ctl;
+  unsigned long long cap = std::max<unsigned long long>(1024, (unsigned long long)std::max(1, nt) * 256ULL);
+  for (int attempt = 0; attempt < 2; attempt++) {
+    dfree(h, h->routes);
+    h->routes = nullptr;
+    if ((rc = dalloc(h, &h->routes, cap))) {
+      cleanup();
+      return rc;
+    }
+    R.routes = h->routes;
+    R.cap = cap;
+    cudaMemset(work, 0, 4);
+    cudaMemset(h->d.ctl, 0, sizeof(Ctl));
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+      cleanup();
+      return fail(h, SIM_ECUDA, "route setup failed");
+    }
+    if (R.n_origins > 0) launch_route(R, n_cta, h->stream);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+      cleanup();
+      return cuda_fail(h, e, "route kernel");
+    }
+    Ctl c;
+    cudaMemcpy(&c, h->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost);
+    if (c.err & kErrUnreach) {
+      cleanup();
+      char buf[96];
+      snprintf(buf, sizeof buf, "trip %d: destination unreachable", c.err_info);
+      return fail(h, SIM_EUNREACHABLE, buf);
+    }
+    if (c.err) {
+      cleanup();
+      return fail(h, SIM_EDEVICE, "route extraction failed");
+    }
+    h->route_cap = c.route_cursor;
+    if (c.route_cursor <= cap) break;
+    cap = c.route_cursor;
+  }
+  cleanup();
+  h->d.routes = h->routes;
+  if ((rc = reset_dynamic(h))) return rc;
+  std::vector<uint8_t> st(nt, SIM_PENDING);
+  if ((rc = build_queues(h, st))) return rc;
+  CK(cudaStreamSynchronize(h->stream));
+  h->routed = true;
+  h->graph_dirty = true;
+  return SIM_OK;
+}
+
+int sim_set_routes(sim_handle* h, const int32_t* offsets, const int32_t* links) {
+  if (!h || !offsets || !links) return SIM_EINVAL;
+  const int nt = h->nt;
+  if (offsets[0] != 0) return fail(h, SIM_EINVAL, "offsets[0] must be 0");
+  for (int i = 0; i < nt; i++) {
+    if (offsets[i + 1] <= offsets[i]) return fail(h, SIM_EINVAL, "every route needs at least one link");
+    for (int k = offsets[i]; k < offsets[i + 1]; k++) {
+      if (links[k] < 0 || links[k] >= h->nl) return fail(h, SIM_EINVAL, "route link out of range");
+      if (k > offsets[i] && h->lfrom[links[k]] != h->lto[links[k - 1]])
+        return fail(h, SIM_EINVAL, "route links are not connected");
+    }
+    if (h->loop && h->lto[links[offsets[i + 1] - 1]] != h->lfrom[links[offsets[i]]])
+      return fail(h, SIM_EINVAL, "loop route is not a cycle");
+  }
+  const long long total = nt ? offsets[nt] : 0;
+  std::vector<int32_t> off(nt > 0 ? nt : 1), len(nt > 0 ? nt : 1);
+  for (int i = 0; i < nt; i++) {
+    off[i] = offsets[i];
+    len[i] = offsets[i + 1] - offsets[i];
+  }
+  dfree(h, h->routes);
+  h->routes = nullptr;
+  int rc = dalloc(h, &h->routes, (size_t)std::max<long long>(1, total));
+  if (rc) return rc;
+  if (total) CK(cudaMemcpy(h->routes, links, (size_t)total * 4, cudaMemcpyHostToDevice));
+  if (nt) {
+    CK(cudaMemcpy(const_cast<int32_t*>(h->d.roff), off.data(), (size_t)nt * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(const_cast<int32_t*>(h->d.rlen), len.data(), (size_t)nt * 4, cudaMemcpyHostToDevice));
+  }
+  h->route_cap = (unsigned long long)total;
+  h->d.routes = h->routes;
+  if ((rc = reset_dynamic(h))) return rc;
+  std::vector<uint8_t> st(nt, SIM_PENDING);
+  if ((rc = build_queues(h, st))) return rc;
+  CK(cudaStreamSynchronize(h->stream));
+  h->routed = true;
+  h->graph_dirty = true;
+  return SIM_OK;
+}
+
+int sim_route_size(sim_handle* h, int64_t* n_hops) {
+  if (!h || !n_hops) return SIM_EINVAL;
+  if (!h->routed) return fail(h, SIM_ESTATE, "no routes");
+  std::vector<int32_t> len(h->nt);
+  if (h->nt) CK(cudaMemcpy(len.data(), h->d.rlen, (size_t)h->nt * 4, cudaMemcpyDeviceToHost));
+  int64_t s = 0;
+  for (int32_t l : len) s += l;
+  *n_hops = s;
+  return SIM_OK;
+}
+
+int sim_read_routes(sim_handle* h, int32_t* offsets, int32_t* links) {
+  if (!h || !offsets || !links) return SIM_EINVAL;
+  if (!h->routed) return fail(h, SIM_ESTATE, "no routes");
+  const int nt = h->nt;
+  std::vector<int32_t> off(nt), len(nt), all((size_t)std::max<unsigned long long>(1, h->route_cap));
+  if (nt) {
+    CK(cudaMemcpy(off.data(), h->d.roff, (size_t)nt * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(len.data(), h->d.rlen, (size_t)nt * 4, cudaMemcpyDeviceToHost));
+  }
+  if (h->route_cap) CK(cudaMemcpy(all.data(), h->routes, (size_t)h->route_cap * 4, cudaMemcpyDeviceToHost));
+  offsets[0] = 0;
+  for (int i = 0; i < nt; i++) {
+    memcpy(links + offsets[i], all.data() + off[i], (size_t)len[i] * 4);
+    offsets[i + 1] = offsets[i] + len[i];
+  }
+  return SIM_OK;
+}
+
+int sim_step(sim_handle* h, int32_t n_steps) {
+  if (!h || n_steps < 0) return SIM_EINVAL;
+  if (!h->routed) return fail(h, SIM_ESTATE, "sim_step before sim_route / sim_set_routes");
+  if (n_steps == 0) return SIM_OK;
+  if (h->graph_dirty) {
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->gexec = nullptr;
+    h->graph = nullptr;
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    launch_step(h->d, h->grid, h->has_stop, h->cap_stream);
+    CK(cudaStreamEndCapture(h->cap_stream, &h->graph));
+    CK(cudaGraphInstantiate(&h->gexec, h->graph, 0));
+    h->graph_dirty = false;
+  }
+  for (int s = 0; s < n_steps; s++) CK(cudaGraphLaunch(h->gexec, h->stream));
+  return check_device(h);
+}
+
+int sim_read_state(sim_handle* h, const sim_state_view* out, uint32_t fields, int on_device) {
+  if (!h || !out) return SIM_EINVAL;
+  const size_t nt = (size_t)h->nt;
+  void* ptr[9] = {out->status, out->link, out->lane, out->cursor, out->x, out->v,
+                  out->insert_step, out->arrive_step, out->lane_change};
+  const size_t esz[9] = {1, 4, 4, 4, 4, 4, 4, 4, 1};
+  void* dptr[9] = {nullptr};
+  std::vector<void*> tmp;
+  for (int f = 0; f < 9; f++) {
+    if (!(fields & (1u << f))) continue;
+    if (!ptr[f]) return fail(h, SIM_EINVAL, "requested field has a NULL pointer");
+    if (on_device) {
+      dptr[f] = ptr[f];
+    } else {
+      void* q;
+      cudaError_t e = cudaMalloc(&q, nt ? nt * esz[f] : 1);
+      if (e != cudaSuccess) {
+        for (void* p : tmp) cudaFree(p);
+        return cuda_fail(h, e, "read_state buffer");
+      }
+      tmp.push_back(q);
+      dptr[f] = q;
+    }
+  }
+  if (nt)
+    launch_state_out(h->d, h->grid, h->stream, (uint8_t*)dptr[0], (int32_t*)dptr[1], (int32_t*)dptr[2],
+                     (int32_t*)dptr[3], (float*)dptr[4], (float*)dptr[5], (int32_t*)dptr[6], (int32_t*)dptr[7],
+                     (int8_t*)dptr[8]);
+  cudaError_t e = cudaSuccess;
+  if (!on_device)
+    for (int f = 0; f < 9 && e == cudaSuccess; f++)
+      if (dptr[f] && nt) e = cudaMemcpyAsync(ptr[f], dptr[f], nt * esz[f], cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  for (void* p : tmp) cudaFree(p);
+  if (e != cudaSuccess) return cuda_fail(h, e, "read_state");
+  return SIM_OK;
+}
+
+int sim_write_state(sim_handle* h, const uint8_t* status, const int32_t* link, const int32_t* lane,
+                    const int32_t* cursor, const float* x, const float* v) {
+  if (!h || !status || !link || !lane || !cursor || !x || !v) return SIM_EINVAL;
+  if (!h->routed) return fail(h, SIM_ESTATE, "sim_write_state before routes exist");
+  const int nt = h->nt;
+  std::vector<int32_t> off(nt), len(nt), all((size_t)std::max<unsigned long long>(1, h->route_cap));
+  if (nt) {
+    CK(cudaMemcpy(off.data(), h->d.roff, (size_t)nt * 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(len.data(), h->d.rlen, (size_t)nt * 4, cudaMemcpyDeviceToHost));
+  }
+  if (h->route_cap) CK(cudaMemcpy(all.data(), h->routes, (size_t)h->route_cap * 4, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < nt; i++) {
+    if (status[i] > SIM_ARRIVED) return fail(h, SIM_EINVAL, "status must be 0, 1 or 2");
+    if (status[i] != SIM_ACTIVE) continue;
+    if (cursor[i] < 0 || cursor[i] >= len[i] || all[(size_t)off[i] + cursor[i]] != link[i])
+      return fail(h, SIM_EINVAL, "active trip not on route[cursor]");
+    if (lane[i] < 0 || lane[i] >= h->lanes[link[i]]) return fail(h, SIM_EINVAL, "lane out of range");
+    if (!(x[i] >= 0.0f) || !(x[i] <= h->len[link[i]]) || !(v[i] >= 0.0f))
+      return fail(h, SIM_EINVAL, "position must be in [0, length] and speed >= 0");
+  }
+  int rc = reset_dynamic(h);
+  if (rc) return rc;
+  std::vector<void*> tmp;
+  uint8_t* ds;
+  int32_t *dl, *dn, *dc;
+  float *dx, *dv;
+  const size_t n = (size_t)std::max(1, nt);
+  if ((rc = dalloc(h, &ds, n)) || (rc = dalloc(h, &dl, n)) || (rc = dalloc(h, &dn, n)) || (rc = dalloc(h, &dc, n)) ||
+      (rc = dalloc(h, &dx, n)) || (rc = dalloc(h, &dv, n)))
+    return rc;
+  void* tl[6] = {ds, dl, dn, dc, dx, dv};
+  if (nt) {
+    cudaMemcpy(ds, status, (size_t)nt, cudaMemcpyHostToDevice);
+    cudaMemcpy(dl, link, (size_t)nt * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(dn, lane, (size_t)nt * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(dc, cursor, (size_t)nt * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(dx, x, (size_t)nt * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(dv, v, (size_t)nt * 4, cudaMemcpyHostToDevice);
+    launch_state_in(h->d, h->grid, h->stream, ds, dl, dn, dc, dx, dv);
+  }
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  for (void* p : tl) dfree(h, p);
+  if (e != cudaSuccess) return cuda_fail(h, e, "write_state");
+  std::vector<uint8_t> st(status, status + nt);
+  if ((rc = build_queues(h, st))) return rc;
+  CK(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+
+int sim_occupancy(sim_handle* h, int32_t* lane_start, int32_t* sorted_vid) {
+  if (!h || !lane_start || !sorted_vid) return SIM_EINVAL;
+  if (!h->routed) return fail(h, SIM_ESTATE, "no routes");
+  launch_occupancy(h->d, h->grid, h->stream);
+  int32_t* dv;
+  int rc = dalloc(h, &dv, (size_t)std::max(1, h->nt));
+  if (rc) return rc;
+  launch_occ_out(h->d, h->grid, h->stream, dv);
+  cudaError_t e = cudaMemcpyAsync(lane_start, h->d.lane_start, ((size_t)h->n_lanes + 1) * 4,
+                                  cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess && lane_start[h->n_lanes] > 0)
+    e = cudaMemcpy(sorted_vid, dv, (size_t)lane_start[h->n_lanes] * 4, cudaMemcpyDeviceToHost);
+  dfree(h, dv);
+  if (e != cudaSuccess) return cuda_fail(h, e, "occupancy");
+  return check_device(h);
+}
+
+int sim_n_lanes(sim_handle* h, int64_t* n) {
+  if (!h || !n) return SIM_EINVAL;
+  *n = h->n_lanes;
+  return SIM_OK;
+}
+
+int sim_counters(sim_handle* h, sim_counters_t* out) {
+  if (!h || !out) return SIM_EINVAL;
+  Ctl c;
+  CK(cudaMemcpyAsync(&c, h->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
+  std::vector<uint8_t> st(h->nt);
+  if (h->nt) CK(cudaMemcpyAsync(st.data(), h->d.status, (size_t)h->nt, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  int64_t waiting = 0, pending = 0, active = 0;
+  for (int i = 0; i < h->nt; i++) {
+    if (st[i] == SIM_ACTIVE) active++;
+    else if (st[i] == SIM_PENDING) {
+      if ((long long)h->depart[i] < c.t) waiting++;
+      else pending++;
+    }
+  }
+  out->t = c.t;
+  out->departed = (int64_t)c.departed;
+  out->waiting = waiting;
+  out->active = active;
+  out->arrived = (int64_t)c.arrived;
+  out->veh_steps = (int64_t)c.veh_steps;
+  out->pending = pending;
+  out->active_last = c.active_last;
+  return SIM_OK;
+}
+
+const char* sim_last_error(const sim_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+void sim_destroy(sim_handle* h) {
+  if (!h) return;
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (void* p : h->allocs) cudaFree(p);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,259 @@
+// Internal device data layout and per-vehicle model functions of libgbtraffic.
+//
+// Model (Waddell et al., Sec. 6): Intelligent Driver Model car following (Eq. 7),
+// ballistic position update over dt (Sec. 6.3.2 gives dt = 0.5 s), mandatory /
+// discretionary lane changes with gap acceptance (Sec. 6.3.2), stop and signal
+// control (Sec. 6.3.2), per-lane ordered occupancy replacing the "traffic atlas"
+// (Sec. 6.3.3).  Every binary32 expression below is written in the one fixed
+// operation order of the model specification; the library is compiled with
+// -fmad=false so no multiply-add is ever fused, which keeps results bit-identical
+// to any IEEE implementation of the same order.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gbt {
+
+constexpr int kCtrlNone = 0, kCtrlStop = 1, kCtrlSignal = 2;
+constexpr int kPending = 0, kActive = 1, kArrived = 2;
+constexpr int kTurnThrough = 0, kTurnLeft = 1, kTurnRight = 2;
+
+// error word bits (device -> host)
+constexpr int kErrLane = 1, kErrLink = 2, kErrSlot = 4, kErrRoute = 8, kErrUnreach = 16,
+              kErrRouteCap = 32, kErrQueue = 64;
+
+// Per-link record, 32 bytes: everything a vehicle step needs about its link and
+// the node at its end, in one aligned load.
+struct __align__(16) LinkRec {
+  float len;           // link length, m
+  float v0;            // IDM desired speed on this link, m/s
+  int32_t lane_base;   // global id of lane 0
+  int32_t to;          // head node
+  uint8_t lanes, cls, ctrl, ew;   // lanes; parameter class; control of head node; approach is east-west
+  uint8_t in_index, n_in;         // rank among the head node's in-links (ascending id), in-degree
+  uint16_t sig_cyc;               // signal cycle, ds
+  int32_t sig_off;                // signal offset, ds
+  uint16_t sig_grn;               // north-south green, ds
+  uint16_t pad;
+};
+static_assert(sizeof(LinkRec) == 32, "LinkRec must be 32 bytes");
+
+struct ClassPar {      // IDM parameters of one link class
+  float a, sab2, T, s0;   // sab2 = 2 * sqrt(a * b)
+};
+
+// Structure-of-arrays vehicle state, one entry per slot.
+struct VehBuf {
+  float* x;
+  float* v;
+  int32_t* vid;
+  int32_t* link;   // -1: slot empty (vehicle arrived)
+  int32_t* nxt;    // next link of the route, -1 on the last link
+  int32_t* cur;    // index of the current link in the route
+  int32_t* lane;
+};
+
+struct Ctl {
+  long long t;
+  int nA;          // slots filled in the unsorted buffer A
+  int nB;          // vehicles in the sorted buffer B (active at step start)
+  int n_ins, n_arr;
+  int err, err_info;
+  int active_last;
+  int pad0;
+  unsigned long long veh_steps, departed, arrived;
+  unsigned long long route_cursor;  // bump allocator of the route store
+};
+
+struct Dev {
+  // network
+  const LinkRec* links;
+  const int32_t* lfrom;
+  const int32_t* node_x;
+  const int32_t* node_y;
+  const ClassPar* cls;
+  const float* tau;      // mandatory-switch table [256]
+  int n_links, n_nodes, n_lanes, n_trips;
+  // parameters
+  float dt, hdt2, vlen, s_min, zone, mp, mathr, mbsafe, mbias, lam, stop_acq;
+  int dt_ds, loop;
+  // trips
+  const int32_t* depart;
+  const int32_t* roff;
+  const int32_t* rlen;
+  const int32_t* routes;
+  const unsigned long long* hseed;
+  uint8_t* status;
+  int32_t* ins_step;
+  int32_t* arr_step;
+  int8_t* dec;
+  // vehicle state: A = unsorted next state, B = sorted current state
+  VehBuf A, B;
+  // per-slot / per-lane scratch
+  int32_t* aidx;
+  float* tx;
+  int32_t* tvid;
+  int32_t* tsrc;
+  int32_t* tg;
+  int32_t* cnt;
+  int32_t* lane_start;
+  int32_t* bsum;
+  unsigned long long* best;   // per lane: epoch-tagged admission key
+  float* a_own;
+  float* xo;
+  float* at;
+  int8_t* intent;
+  uint8_t* flags;
+  // per node
+  int32_t* holder;
+  unsigned long long* acq;
+  // departure queues
+  const int32_t* qlinks;
+  int n_qlinks;
+  const int32_t* q_end;
+  int32_t* q_head;
+  const int32_t* q_items;
+  Ctl* ctl;
+};
+
+// Trip-planning work description (one shortest-path tree per distinct origin).
+struct RouteDev {
+  int nn, nl;
+  const int32_t* out_start;
+  const int32_t* out_link;
+  const int32_t* in_start;
+  const int32_t* in_link;
+  const int32_t* lfrom;
+  const int32_t* lto;
+  const int32_t* cost;
+  const int32_t* origins;
+  int n_origins;
+  const int32_t* otrip_start;   // per node: trips with this origin
+  const int32_t* otrip_list;
+  const int32_t* dest;
+  unsigned long long* dist;     // [n_cta][nn]
+  int32_t* qflag;
+  int32_t* fflag;
+  int32_t* qa;
+  int32_t* qb;
+  int32_t* fa;
+  int32_t* fb;
+  unsigned* cta_epoch;
+  int32_t* cta_round;
+  int32_t* roff;
+  int32_t* rlen;
+  int32_t* routes;
+  unsigned long long cap;
+  int* work;
+  int delta;
+  Ctl* ctl;
+};
+
+void launch_route(const RouteDev& R, int n_cta, cudaStream_t s);
+
+constexpr uint8_t kFlagFront = 1, kFlagHolder = 2, kFlagCand = 4;
+
+// ---------------------------------------------------------------- model functions
+
+// Eq. 7 (IDM): a [1 - (v/v0)^4 - (s*/s)^2], s* = s0 + max(0, vT + v dv / (2 sqrt(ab))),
+// dv = v - v_lead, gap floored at s_min; without a leader the interaction term is 0.
+__host__ __device__ __forceinline__ float idm_acc(const ClassPar& P, float v0, float s_min, float s,
+                                                  float v, float vl, bool has_leader) {
+  float r = v / v0;
+  float r2 = r * r;
+  float r4 = r2 * r2;
+  float q2 = 0.0f;
+  if (has_leader) {
+    float dv = v - vl;
+    float t1 = v * P.T;
+    float t2 = (v * dv) / P.sab2;
+    float dyn = t1 + t2;
+    float ss = P.s0 + fmaxf(0.0f, dyn);
+    float se = fmaxf(s, s_min);
+    float q = ss / se;
+    q2 = q * q;
+  }
+  return P.a * ((1.0f - r4) - q2);
+}
+
+// Ballistic update: v' = v + a dt; x' = x + (v dt + a dt^2/2) unless the vehicle stops
+// within the step, then x' = x - v^2 / (2a), v' = 0.
+__host__ __device__ __forceinline__ void ballistic(float x, float v, float acc, float dt, float hdt2,
+                                                   float& xo, float& vo) {
+  float vn = v + acc * dt;
+  if (vn >= 0.0f) {
+    float d1 = v * dt;
+    float d2 = acc * hdt2;
+    xo = x + (d1 + d2);
+    vo = vn;
+  } else {
+    float den = 2.0f * acc;
+    float dx = -((v * v) / den);
+    xo = x + dx;
+    vo = 0.0f;
+  }
+}
+
+// Index into the mandatory-switch table: SplitMix64 finaliser (Steele, Lea & Flood
+// 2014) of (seed ^ vid << 32) ^ hop, top 8 bits.  hseed = seed ^ (vid << 32).
+__host__ __device__ __forceinline__ unsigned mand_index(unsigned long long hseed, int hop) {
+  unsigned long long z = hseed ^ (unsigned long long)(unsigned)hop;
+  z += 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  z = z ^ (z >> 31);
+  return (unsigned)(z >> 56);
+}
+
+// Movement class of a -> b -> c from integer node positions.
+__host__ __device__ __forceinline__ int turn_class(long long ax, long long ay, long long bx, long long by,
+                                                   long long cx, long long cy) {
+  long long ux = bx - ax, uy = by - ay, wx = cx - bx, wy = cy - by;
+  long long cr = ux * wy - uy * wx;
+  long long dot = ux * wx + uy * wy;
+  long long acr = cr < 0 ? -cr : cr;
+  if (dot > acr) return kTurnThrough;
+  return cr < 0 ? kTurnRight : kTurnLeft;
+}
+
+// Lanes allowed for the movement e -> e2: right turns from lane 0, left turns (and
+// U-turns) from the leftmost lane, through from any; all lanes at the route's end.
+__device__ __forceinline__ int move_mask(const Dev& d, int e, int lanes, int e2) {
+  int all = (1 << lanes) - 1;
+  if (e2 < 0) return all;
+  int a = d.lfrom[e], b = d.lfrom[e2];   // head of e == tail of e2
+  int c = d.links[e2].to;
+  int tc = turn_class(d.node_x[a], d.node_y[a], d.node_x[b], d.node_y[b], d.node_x[c], d.node_y[c]);
+  if (tc == kTurnRight) return 1;
+  if (tc == kTurnLeft) return 1 << (lanes - 1);
+  return all;
+}
+
+__device__ __forceinline__ int rr_rank(const LinkRec& L, long long t) {
+  int n = L.n_in;
+  return (int)((L.in_index + n - (int)(t % n)) % n);
+}
+
+__device__ __forceinline__ bool signal_green(const LinkRec& L, long long t, int dt_ds) {
+  long long p = (t * (long long)dt_ds - (long long)L.sig_off) % (long long)L.sig_cyc;
+  if (p < 0) p += L.sig_cyc;
+  bool ns = p < (long long)L.sig_grn;
+  return L.ew ? !ns : ns;
+}
+
+// Epoch-tagged 64-bit priority key: entries of step t compare below all entries of
+// earlier steps, so per-step minima need no reset.  Lower 32 bits: (rank, lane).
+__device__ __forceinline__ unsigned long long epoch_key(long long t, int rr, int lane) {
+  unsigned hi = 0xFFFFFFFEu - (unsigned)t;
+  return ((unsigned long long)hi << 32) | (unsigned long long)((rr << 8) | lane);
+}
+__device__ __forceinline__ bool epoch_current(unsigned long long k, long long t) {
+  return (unsigned)(k >> 32) == 0xFFFFFFFEu - (unsigned)t;
+}
+
+__device__ __forceinline__ void set_err(const Dev& d, int bit, int info) {
+  atomicOr(&d.ctl->err, bit);
+  atomicExch(&d.ctl->err_info, info);
+}
+
+}  // namespace gbt

@@ -1,0 +1,615 @@
+// One simulation step of the microsimulation hot path (Waddell et al., Sec. 6.3.2):
+//
+//   1. occupancy rebuild: counting pass by lane, exclusive scan, scatter, in-segment
+//      rank by (position, vid) -> vehicles of buffer A land sorted in buffer B
+//      (the per-lane order replaces the "traffic atlas" of Sec. 6.3.3);
+//   2. stop-sign acquisition (one vehicle at a time, Sec. 6.3.2);
+//   3. own-lane IDM acceleration (Eq. 7) with look-ahead over the link end and the
+//      stop line, tentative ballistic move, admission candidates;
+//   4. lane-change decisions (mandatory / discretionary + gap acceptance, Sec. 6.3.2);
+//   5. conflict resolution, final move, edge transition, arrival -> buffer A;
+//   6. departures from the per-link queues -> appended to buffer A.
+//
+// Every kernel reads the state at step t (buffer B and the per-step scratch written
+// by earlier kernels of the same step) and writes the state at t+1, so the result
+// does not depend on thread scheduling; ties are broken by vehicle id or by the
+// rotating round-robin rank.
+#include "gbt_internal.cuh"
+
+namespace gbt {
+
+#define GRID_STRIDE(i, n) for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
+
+// ------------------------------------------------------------------ occupancy
+__global__ void k_count(Dev d) {
+  const int nA = d.ctl->nA;
+  GRID_STRIDE(s, nA) {
+    int e = d.A.link[s];
+    if (e < 0) continue;
+    int lane = d.A.lane[s];
+    const LinkRec& L = d.links[e];
+    if ((unsigned)lane >= L.lanes) { set_err(d, kErrLane, s); continue; }
+    d.aidx[s] = atomicAdd(&d.cnt[L.lane_base + lane], 1);
+  }
+}
+
+constexpr int kScanThreads = 256, kScanItems = 8, kScanChunk = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int block_excl_scan(int val, int* smem_warp, int& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int inc = val;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) smem_warp[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    int w = (lane < (int)(blockDim.x >> 5)) ? smem_warp[lane] : 0;
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    smem_warp[lane] = wi - w;   // exclusive warp offsets
+    if (lane == 31) smem_warp[32] = wi;
+  }
+  __syncthreads();
+  int res = smem_warp[warp] + inc - val;
+  total = smem_warp[32];
+  __syncthreads();
+  return res;
+}
+
+__global__ void k_scan_sum(Dev d) {
+  __shared__ int sw[33];
+  int base = blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
+  int s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; k++) {
+    int i = base + k;
+    if (i < d.n_lanes) s += d.cnt[i];
+  }
+  int tot;
+  block_excl_scan(s, sw, tot);
+  if (threadIdx.x == 0) d.bsum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_top(Dev d, int nblocks) {
+  __shared__ int sw[33];
+  int carry = 0;
+  for (int b0 = 0; b0 < nblocks; b0 += blockDim.x) {
+    int i = b0 + threadIdx.x;
+    int v = i < nblocks ? d.bsum[i] : 0;
+    int tot;
+    int ex = block_excl_scan(v, sw, tot);
+    if (i < nblocks) d.bsum[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) {
+    d.ctl->nB = carry;
+    d.lane_start[d.n_lanes] = carry;
+  }
+}
+
+__global__ void k_scan_fin(Dev d) {
+  __shared__ int sw[33];
+  int base = blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
+  int v[kScanItems];
+  int s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; k++) {
+    int i = base + k;
+    v[k] = i < d.n_lanes ? d.cnt[i] : 0;
+    s += v[k];
+  }
+  int tot;
+  int ex = block_excl_scan(s, sw, tot) + d.bsum[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; k++) {
+    int i = base + k;
+    if (i < d.n_lanes) {
+      d.lane_start[i] = ex;
+      d.cnt[i] = 0;
+    }
+    ex += v[k];
+  }
+}
+
+__global__ void k_scatter(Dev d) {
+  const int nA = d.ctl->nA;
+  GRID_STRIDE(s, nA) {
+    int e = d.A.link[s];
+    if (e < 0) continue;
+    int g = d.links[e].lane_base + d.A.lane[s];
+    int p = d.lane_start[g] + d.aidx[s];
+    d.tx[p] = d.A.x[s];
+    d.tvid[p] = d.A.vid[s];
+    d.tsrc[p] = s;
+    d.tg[p] = g;
+  }
+}
+
+// Rank of each vehicle inside its lane segment by (x, vid); the vehicle's state
+// moves from its slot in A to position lane_start + rank in B.
+__global__ void k_rank(Dev d) {
+  const int nB = d.ctl->nB;
+  GRID_STRIDE(p, nB) {
+    int g = d.tg[p];
+    int s0 = d.lane_start[g], s1 = d.lane_start[g + 1];
+    float xp = d.tx[p];
+    int vp = d.tvid[p];
+    int rank = 0;
+    for (int q = s0; q < s1; q++) {
+      float xq = d.tx[q];
+      rank += (xq < xp || (xq == xp && d.tvid[q] < vp)) ? 1 : 0;
+    }
+    int dst = s0 + rank;
+    int src = d.tsrc[p];
+    d.B.x[dst] = d.A.x[src];
+    d.B.v[dst] = d.A.v[src];
+    d.B.vid[dst] = vp;
+    d.B.link[dst] = d.A.link[src];
+    d.B.nxt[dst] = d.A.nxt[src];
+    d.B.cur[dst] = d.A.cur[src];
+    d.B.lane[dst] = d.A.lane[src];
+  }
+}
+
+// ------------------------------------------------------------------ stop signs
+// A free stop-controlled node is acquired by the front vehicle (within
+// stop_acquire_m of the stop line, route continuing) of the incoming lane with the
+// smallest (round-robin rank of its link, lane).
+__global__ void k_acquire(Dev d) {
+  const int nB = d.ctl->nB;
+  const long long t = d.ctl->t;
+  GRID_STRIDE(p, nB) {
+    int e = d.B.link[p];
+    const LinkRec L = d.links[e];
+    if (L.ctrl != kCtrlStop) continue;
+    int lane = d.B.lane[p];
+    if (p + 1 != d.lane_start[L.lane_base + lane + 1]) continue;
+    if (d.holder[L.to] != -1 || d.B.nxt[p] < 0) continue;
+    if (!((L.len - d.B.x[p]) <= d.stop_acq)) continue;
+    atomicMin(&d.acq[L.to], epoch_key(t, rr_rank(L, t), lane));
+  }
+}
+
+// ------------------------------------------------------------------ neighbours / IDM
+struct Ctx {
+  const Dev& d;
+  long long t;
+};
+
+__device__ __forceinline__ bool is_holder(const Dev& d, const LinkRec& L, long long t, int vid, int lane,
+                                          bool front) {
+  if (L.ctrl != kCtrlStop) return false;
+  int h = d.holder[L.to];
+  if (h == vid) return true;
+  return h == -1 && front && d.acq[L.to] == epoch_key(t, rr_rank(L, t), lane);
+}
+
+__device__ __forceinline__ bool line_closed(const Dev& d, const LinkRec& L, long long t, bool holder) {
+  if (L.ctrl == kCtrlSignal) return !signal_green(L, t, d.dt_ds);
+  if (L.ctrl == kCtrlStop) return !holder;
+  return false;
+}
+
+// Acceleration of a vehicle with nothing ahead on its link e, considered in lane
+// `lane`: leader = rearmost vehicle of the mapped lane of its next link (gap across
+// the link end); a closed stop line is a standing obstacle (smaller acceleration).
+__device__ __forceinline__ float acc_front(const Dev& d, const LinkRec& L, const ClassPar& P, int vid, int nxt,
+                                           int lane, float x, float v, bool closed) {
+  if (nxt < 0) return idm_acc(P, L.v0, d.s_min, 0.0f, v, 0.0f, false);
+  const LinkRec Ln = d.links[nxt];
+  int m = lane < Ln.lanes - 1 ? lane : Ln.lanes - 1;
+  int g = Ln.lane_base + m;
+  int r = d.lane_start[g];
+  float a1;
+  if (r < d.lane_start[g + 1] && d.B.vid[r] != vid) {
+    float s = ((L.len - x) + d.B.x[r]) - d.vlen;
+    a1 = idm_acc(P, L.v0, d.s_min, s, v, d.B.v[r], true);
+  } else {
+    a1 = idm_acc(P, L.v0, d.s_min, 0.0f, v, 0.0f, false);
+  }
+  if (closed) {
+    float a2 = idm_acc(P, L.v0, d.s_min, L.len - x, v, 0.0f, true);
+    return fminf(a1, a2);
+  }
+  return a1;
+}
+
+__global__ void k_own(Dev d) {
+  const int nB = d.ctl->nB;
+  const long long t = d.ctl->t;
+  GRID_STRIDE(p, nB) {
+    const int e = d.B.link[p];
+    const LinkRec L = d.links[e];
+    const ClassPar P = d.cls[L.cls];
+    const float x = d.B.x[p], v = d.B.v[p];
+    const int vid = d.B.vid[p], lane = d.B.lane[p], nxt = d.B.nxt[p];
+    const int g = L.lane_base + lane;
+    const bool front = (p + 1 == d.lane_start[g + 1]);
+    const bool hold = is_holder(d, L, t, vid, lane, front);
+    float a;
+    if (!front) {
+      a = idm_acc(P, L.v0, d.s_min, (d.B.x[p + 1] - x) - d.vlen, v, d.B.v[p + 1], true);
+    } else {
+      bool closed = nxt >= 0 && line_closed(d, L, t, hold);
+      a = acc_front(d, L, P, vid, nxt, lane, x, v, closed);
+    }
+    float xo, vo;
+    ballistic(x, v, a, d.dt, d.hdt2, xo, vo);
+    d.a_own[p] = a;
+    d.xo[p] = xo;
+    uint8_t fl = (front ? kFlagFront : 0) | (hold ? kFlagHolder : 0);
+    // admission candidate: front, route continues, stop line open, move reaches the end
+    if (front && nxt >= 0 && !line_closed(d, L, t, hold) && xo >= L.len) {
+      const LinkRec Ln = d.links[nxt];
+      int m = lane < Ln.lanes - 1 ? lane : Ln.lanes - 1;
+      int gt = Ln.lane_base + m;
+      int r = d.lane_start[gt];
+      bool ok = true;
+      if (r < d.lane_start[gt + 1] && d.B.vid[r] != vid) {
+        float land = xo - L.len;
+        float room = d.B.x[r] - d.vlen;
+        ok = land <= room;
+      }
+      if (ok) {
+        fl |= kFlagCand;
+        atomicMin(&d.best[gt], epoch_key(t, rr_rank(L, t), lane));
+      }
+    }
+    d.flags[p] = fl;
+  }
+}
+
+// First position q in [s0, s1) whose (x, vid) exceeds (x, vid) of the probe.
+__device__ __forceinline__ int upper_pos(const Dev& d, int s0, int s1, float x, int vid) {
+  int lo = s0, hi = s1;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    float xm = d.B.x[mid];
+    bool greater = xm > x || (xm == x && d.B.vid[mid] > vid);
+    if (greater) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+// Lane-change decision from the state at t: MOBIL incentive (Kesting, Treiber &
+// Helbing 2007) for discretionary changes, mandatory changes toward the lanes of
+// the next movement once within the drawn switch distance, and gap acceptance =
+// no overlap and both the changer's and the new follower's accelerations >= -b_safe.
+__global__ void k_decide(Dev d) {
+  const int nB = d.ctl->nB;
+  const long long t = d.ctl->t;
+  GRID_STRIDE(p, nB) {
+    d.intent[p] = 0;
+    const int e = d.B.link[p];
+    const LinkRec L = d.links[e];
+    if (L.lanes < 2) continue;
+    const float x = d.B.x[p];
+    if (!(x >= d.zone && d.xo[p] < L.len - d.zone)) continue;
+    const ClassPar P = d.cls[L.cls];
+    const float v = d.B.v[p];
+    const int vid = d.B.vid[p], lane = d.B.lane[p], nxt = d.B.nxt[p], cur = d.B.cur[p];
+    const int M = move_mask(d, e, L.lanes, nxt);
+    int dirs[2];
+    int nd = 0;
+    bool mand = false;
+    if ((M >> lane) & 1) {
+      if (lane + 1 < L.lanes && ((M >> (lane + 1)) & 1)) dirs[nd++] = 1;
+      if (lane >= 1 && ((M >> (lane - 1)) & 1)) dirs[nd++] = -1;
+    } else {
+      int ms = __ffs(M) - 1;
+      int dd = ms > lane ? 1 : -1;
+      int ncross = ms > lane ? ms - lane : lane - ms;
+      float thr = (d.lam * (float)ncross) * d.tau[mand_index(d.hseed[vid], cur)];
+      float drem = L.len - x;
+      mand = drem <= thr;
+      dirs[nd++] = dd;
+    }
+    const int g = L.lane_base + lane;
+    const bool front = (p + 1 == d.lane_start[g + 1]);
+    const bool hold = (d.flags[p] & kFlagHolder) != 0;
+    const bool closed_self = nxt >= 0 && line_closed(d, L, t, hold);
+    int chosen = 0;
+    float chosen_inc = 0.0f, chosen_at = 0.0f;
+    for (int k = 0; k < nd; k++) {
+      const int dd = dirs[k];
+      const int l2 = lane + dd;
+      const int g2 = L.lane_base + l2;
+      const int s0 = d.lane_start[g2], s1 = d.lane_start[g2 + 1];
+      const int up = upper_pos(d, s0, s1, x, vid);
+      const int Ln = up < s1 ? up : -1;
+      const int Fn = up > s0 ? up - 1 : -1;
+      float ac;
+      if (Ln >= 0) {
+        float sl = (d.B.x[Ln] - x) - d.vlen;
+        if (!(sl > 0.0f)) continue;
+        ac = idm_acc(P, L.v0, d.s_min, sl, v, d.B.v[Ln], true);
+      } else {
+        ac = acc_front(d, L, P, vid, nxt, l2, x, v, closed_self);
+      }
+      if (!(ac >= -d.mbsafe)) continue;
+      float an = 0.0f;
+      if (Fn >= 0) {
+        float sg = (x - d.B.x[Fn]) - d.vlen;
+        if (!(sg > 0.0f)) continue;
+        an = idm_acc(P, L.v0, d.s_min, sg, d.B.v[Fn], v, true);
+        if (!(an >= -d.mbsafe)) continue;
+      }
+      if (mand) {
+        chosen = dd;
+        chosen_at = ac;
+        break;
+      }
+      float dc = ac - d.a_own[p];
+      float dn = Fn >= 0 ? an - d.a_own[Fn] : 0.0f;
+      float dno = 0.0f;
+      const int s_own = d.lane_start[g];
+      if (p > s_own) {   // old follower F = p - 1
+        const int F = p - 1;
+        float ao;
+        if (!front) {
+          ao = idm_acc(P, L.v0, d.s_min, (d.B.x[p + 1] - d.B.x[F]) - d.vlen, d.B.v[F], d.B.v[p + 1], true);
+        } else {
+          const int vF = d.B.vid[F];
+          const int nF = d.B.nxt[F];
+          bool holdF = is_holder(d, L, t, vF, lane, false);
+          bool closedF = nF >= 0 && line_closed(d, L, t, holdF);
+          ao = acc_front(d, L, P, vF, nF, lane, d.B.x[F], d.B.v[F], closedF);
+        }
+        dno = ao - d.a_own[F];
+      }
+      float inc = dc + d.mp * (dn + dno);
+      if (dd < 0) inc = inc + d.mbias;
+      if (!(inc > d.mathr)) continue;
+      if (chosen == 0 || inc > chosen_inc) {
+        chosen = dd;
+        chosen_inc = inc;
+        chosen_at = ac;
+      }
+    }
+    d.intent[p] = (int8_t)chosen;
+    d.at[p] = chosen_at;
+  }
+}
+
+// ------------------------------------------------------------------ move
+__global__ void k_move(Dev d) {
+  const int nB = d.ctl->nB;
+  const long long t = d.ctl->t;
+  GRID_STRIDE(p, nB) {
+    const int e = d.B.link[p];
+    const LinkRec L = d.links[e];
+    const ClassPar P = d.cls[L.cls];
+    const float x = d.B.x[p], v = d.B.v[p];
+    const int vid = d.B.vid[p], lane = d.B.lane[p], nxt = d.B.nxt[p], cur = d.B.cur[p];
+    const uint8_t fl = d.flags[p];
+    int change = d.intent[p];
+    if (change != 0) {
+      // cancelled by a lower-id vehicle changing into the same lane less than
+      // (vehicle length + s0) away; such vehicles sit in lanes tgt-1 and tgt+1
+      const int tgt = lane + change;
+      const float thr = d.vlen + P.s0;
+      bool cancel = false;
+      for (int src = tgt - 1; src <= tgt + 1 && !cancel; src += 2) {
+        if (src < 0 || src >= L.lanes) continue;
+        const int gs = L.lane_base + src;
+        const int q0 = d.lane_start[gs], q1 = d.lane_start[gs + 1];
+        for (int q = q0; q < q1 && !cancel; q++) {
+          int iq = d.intent[q];
+          if (iq == 0 || src + iq != tgt || d.B.vid[q] >= vid) continue;
+          if (fabsf(d.B.x[q] - x) < thr) cancel = true;
+        }
+      }
+      if (cancel) change = 0;
+    }
+    const float acc = change ? d.at[p] : d.a_own[p];
+    float x1, v1;
+    ballistic(x, v, acc, d.dt, d.hdt2, x1, v1);
+    d.dec[vid] = (int8_t)change;
+    const bool hold = (fl & kFlagHolder) != 0;
+    int nl = lane + change, nlink = e, ncur = cur, nnxt = nxt;
+    float nx = x1, nv = v1;
+    bool crossed = false;
+    if (x1 >= L.len) {
+      if (nxt < 0) {
+        d.A.link[p] = -1;
+        d.status[vid] = kArrived;
+        d.arr_step[vid] = (int32_t)t;
+        atomicAdd(&d.ctl->n_arr, 1);
+        continue;
+      }
+      const LinkRec Ln = d.links[nxt];
+      const int m = lane < Ln.lanes - 1 ? lane : Ln.lanes - 1;
+      const int gt = Ln.lane_base + m;
+      const bool won = (fl & kFlagCand) && d.best[gt] == epoch_key(t, rr_rank(L, t), lane);
+      if (won) {
+        const int off = d.roff[vid], len = d.rlen[vid];
+        ncur = d.loop ? (cur + 1) % len : cur + 1;
+        int k2 = ncur + 1;
+        nnxt = k2 < len ? d.routes[off + k2] : (d.loop ? d.routes[off + k2 % len] : -1);
+        nlink = nxt;
+        nl = m;
+        nx = x1 - L.len;
+        crossed = true;
+      } else {
+        nx = L.len;
+        nv = 0.0f;
+      }
+    }
+    if (hold) d.holder[L.to] = crossed ? -1 : vid;
+    d.A.x[p] = nx;
+    d.A.v[p] = nv;
+    d.A.vid[p] = vid;
+    d.A.link[p] = nlink;
+    d.A.nxt[p] = nnxt;
+    d.A.cur[p] = ncur;
+    d.A.lane[p] = nl;
+  }
+}
+
+// ------------------------------------------------------------------ departures
+// The head of each link's queue of due trips enters at x = 0, v = 0 in the allowed
+// lane with the largest rear space (ties to the lowest lane) that received no
+// vehicle from upstream in this step, if that space is at least s0 + vehicle length.
+__global__ void k_insert(Dev d) {
+  const int nq = d.n_qlinks;
+  const long long t = d.ctl->t;
+  const int nB = d.ctl->nB;
+  GRID_STRIDE(i, nq) {
+    const int e = d.qlinks[i];
+    const int hd = d.q_head[e];
+    if (hd >= d.q_end[e]) continue;
+    const int h = d.q_items[hd];
+    if ((long long)d.depart[h] > t) continue;
+    const LinkRec L = d.links[e];
+    const int off = d.roff[h], len = d.rlen[h];
+    const int e2 = len >= 2 ? d.routes[off + 1] : (d.loop ? d.routes[off] : -1);
+    const int M = move_mask(d, e, L.lanes, e2);
+    int bl = -1;
+    float brs = 0.0f;
+    for (int l = 0; l < L.lanes; l++) {
+      if (!((M >> l) & 1)) continue;
+      const int g = L.lane_base + l;
+      if (epoch_current(d.best[g], t)) continue;
+      const int r = d.lane_start[g];
+      const float rs = r < d.lane_start[g + 1] ? d.B.x[r] - d.vlen : INFINITY;
+      if (bl < 0 || rs > brs) {
+        bl = l;
+        brs = rs;
+      }
+    }
+    if (bl < 0) continue;
+    const float need = d.cls[L.cls].s0 + d.vlen;
+    if (!(brs >= need)) continue;
+    const int slot = nB + atomicAdd(&d.ctl->n_ins, 1);
+    if (slot >= d.n_trips) { set_err(d, kErrSlot, slot); continue; }
+    d.A.x[slot] = 0.0f;
+    d.A.v[slot] = 0.0f;
+    d.A.vid[slot] = h;
+    d.A.link[slot] = e;
+    d.A.nxt[slot] = e2;
+    d.A.cur[slot] = 0;
+    d.A.lane[slot] = bl;
+    d.status[h] = kActive;
+    d.ins_step[h] = (int32_t)t;
+    d.q_head[e] = hd + 1;
+  }
+}
+
+__global__ void k_finish(Dev d) {
+  Ctl* c = d.ctl;
+  c->veh_steps += (unsigned long long)c->nB;
+  c->departed += (unsigned long long)c->n_ins;
+  c->arrived += (unsigned long long)c->n_arr;
+  c->active_last = c->nB;
+  c->nA = c->nB + c->n_ins;
+  c->n_ins = 0;
+  c->n_arr = 0;
+  c->t += 1;
+}
+
+// ------------------------------------------------------------------ launch sequence
+int scan_blocks(int n_lanes) { return (n_lanes + kScanChunk - 1) / kScanChunk; }
+
+void launch_occupancy(const Dev& d, int grid, cudaStream_t s) {
+  const int nb = scan_blocks(d.n_lanes);
+  k_count<<<grid, 256, 0, s>>>(d);
+  k_scan_sum<<<nb, kScanThreads, 0, s>>>(d);
+  k_scan_top<<<1, 1024, 0, s>>>(d, nb);
+  k_scan_fin<<<nb, kScanThreads, 0, s>>>(d);
+  k_scatter<<<grid, 256, 0, s>>>(d);
+  k_rank<<<grid, 256, 0, s>>>(d);
+}
+
+void launch_step(const Dev& d, int grid, bool has_stop, cudaStream_t s) {
+  launch_occupancy(d, grid, s);
+  if (has_stop) k_acquire<<<grid, 256, 0, s>>>(d);
+  k_own<<<grid, 256, 0, s>>>(d);
+  k_decide<<<grid, 256, 0, s>>>(d);
+  k_move<<<grid, 256, 0, s>>>(d);
+  if (d.n_qlinks > 0) k_insert<<<(d.n_qlinks + 255) / 256 < grid ? (d.n_qlinks + 255) / 256 : grid, 256, 0, s>>>(d);
+  k_finish<<<1, 1, 0, s>>>(d);
+}
+
+// ------------------------------------------------------------------ state I/O kernels
+__global__ void k_state_out(Dev d, uint8_t* status, int32_t* link, int32_t* lane, int32_t* cursor, float* x,
+                            float* v, int32_t* ins, int32_t* arr, int8_t* dec) {
+  GRID_STRIDE(i, d.n_trips) {
+    if (status) status[i] = d.status[i];
+    if (link) link[i] = -1;
+    if (lane) lane[i] = 0;
+    if (cursor) cursor[i] = 0;
+    if (x) x[i] = 0.0f;
+    if (v) v[i] = 0.0f;
+    if (ins) ins[i] = d.ins_step[i];
+    if (arr) arr[i] = d.arr_step[i];
+    if (dec) dec[i] = d.status[i] == kActive ? d.dec[i] : 0;
+  }
+}
+
+__global__ void k_state_out_active(Dev d, int32_t* link, int32_t* lane, int32_t* cursor, float* x, float* v) {
+  const int nA = d.ctl->nA;
+  GRID_STRIDE(s, nA) {
+    int e = d.A.link[s];
+    if (e < 0) continue;
+    int i = d.A.vid[s];
+    if (link) link[i] = e;
+    if (lane) lane[i] = d.A.lane[s];
+    if (cursor) cursor[i] = d.A.cur[s];
+    if (x) x[i] = d.A.x[s];
+    if (v) v[i] = d.A.v[s];
+  }
+}
+
+void launch_state_out(const Dev& d, int grid, cudaStream_t s, uint8_t* status, int32_t* link, int32_t* lane,
+                      int32_t* cursor, float* x, float* v, int32_t* ins, int32_t* arr, int8_t* dec) {
+  k_state_out<<<grid, 256, 0, s>>>(d, status, link, lane, cursor, x, v, ins, arr, dec);
+  k_state_out_active<<<grid, 256, 0, s>>>(d, link, lane, cursor, x, v);
+}
+
+// Load a state (by vid) into buffer A: active trips are packed into slots by an
+// atomic counter (slot order is irrelevant: the next occupancy rebuild sorts).
+__global__ void k_state_in(Dev d, const uint8_t* status, const int32_t* link, const int32_t* lane,
+                           const int32_t* cursor, const float* x, const float* v) {
+  GRID_STRIDE(i, d.n_trips) {
+    d.status[i] = status[i];
+    d.ins_step[i] = status[i] == kActive ? 0 : -1;
+    d.arr_step[i] = -1;
+    d.dec[i] = 0;
+    if (status[i] != kActive) continue;
+    int slot = atomicAdd(&d.ctl->nA, 1);
+    int off = d.roff[i], len = d.rlen[i];
+    int k = cursor[i];
+    int k2 = k + 1;
+    d.A.x[slot] = x[i] + 0.0f;
+    d.A.v[slot] = v[i];
+    d.A.vid[slot] = i;
+    d.A.link[slot] = link[i];
+    d.A.lane[slot] = lane[i];
+    d.A.cur[slot] = k;
+    d.A.nxt[slot] = k2 < len ? d.routes[off + k2] : (d.loop ? d.routes[off + k2 % len] : -1);
+  }
+}
+
+void launch_state_in(const Dev& d, int grid, cudaStream_t s, const uint8_t* status, const int32_t* link,
+                     const int32_t* lane, const int32_t* cursor, const float* x, const float* v) {
+  k_state_in<<<grid, 256, 0, s>>>(d, status, link, lane, cursor, x, v);
+}
+
+__global__ void k_occ_out(Dev d, int32_t* sorted_vid) {
+  const int nB = d.ctl->nB;
+  GRID_STRIDE(p, nB) sorted_vid[p] = d.B.vid[p];
+}
+
+void launch_occ_out(const Dev& d, int grid, cudaStream_t s, int32_t* sorted_vid) {
+  k_occ_out<<<grid, 256, 0, s>>>(d, sorted_vid);
+}
+
+}  // namespace gbt

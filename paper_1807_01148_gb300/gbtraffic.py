@@ -1,0 +1,266 @@
+"""Python binding of libgbtraffic (argument marshalling only; every step runs in the
+CUDA library).  Names follow the C ABI in include/gbtraffic.h.
+
+The library is built in-tree by ``paper_1807_01148_gb300.build``; importing this module
+without it raises at first use, and there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SIM_OK, SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA, SIM_EUNREACHABLE, SIM_ETIMEOUT, SIM_ESTATE, SIM_EDEVICE = \
+    0, -1, -2, -3, -4, -5, -6, -7
+ERR_NAMES = {0: "SIM_OK", -1: "SIM_EINVAL", -2: "SIM_ENOMEM", -3: "SIM_ECUDA", -4: "SIM_EUNREACHABLE",
+             -5: "SIM_ETIMEOUT", -6: "SIM_ESTATE", -7: "SIM_EDEVICE"}
+F_STATUS, F_LINK, F_LANE, F_CURSOR, F_X, F_V, F_INSERT, F_ARRIVE, F_LANECHANGE = (1 << k for k in range(9))
+F_ALL = (1 << 9) - 1
+
+EXPORTS = ["sim_create", "sim_create_batch", "sim_set_stream", "sim_route", "sim_set_routes", "sim_route_size",
+           "sim_read_routes", "sim_step", "sim_read_state", "sim_write_state", "sim_occupancy", "sim_n_lanes",
+           "sim_counters", "sim_last_error", "sim_destroy"]
+
+
+class sim_network(C.Structure):
+    _fields_ = [("n_nodes", C.c_int32), ("n_links", C.c_int32),
+                ("node_x_dm", C.c_void_p), ("node_y_dm", C.c_void_p), ("node_control", C.c_void_p),
+                ("signal_offset_ds", C.c_void_p), ("signal_cycle_ds", C.c_void_p),
+                ("signal_green_ds", C.c_void_p), ("link_from", C.c_void_p), ("link_to", C.c_void_p),
+                ("link_length_m", C.c_void_p), ("link_speed_mps", C.c_void_p),
+                ("link_lanes", C.c_void_p), ("link_class", C.c_void_p)]
+
+
+class sim_demand(C.Structure):
+    _fields_ = [("n_trips", C.c_int32), ("origin", C.c_void_p), ("dest", C.c_void_p),
+                ("depart_step", C.c_void_p)]
+
+
+class sim_params(C.Structure):
+    _fields_ = [("dt", C.c_float), ("veh_len", C.c_float), ("s_min", C.c_float), ("n_class", C.c_int32),
+                ("v0", C.c_void_p), ("T", C.c_void_p), ("a", C.c_void_p), ("b", C.c_void_p), ("s0", C.c_void_p),
+                ("mobil_p", C.c_float), ("mobil_athr", C.c_float), ("mobil_bsafe", C.c_float),
+                ("mobil_bias_right", C.c_float), ("lambda_mand", C.c_float), ("stop_acquire_m", C.c_float),
+                ("seed", C.c_uint64), ("cost_mode", C.c_int32), ("loop_routes", C.c_int32)]
+
+
+class sim_counters_t(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in
+                ("t", "departed", "waiting", "active", "arrived", "veh_steps", "pending", "active_last")]
+
+
+class sim_state_view(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in
+                ("status", "link", "lane", "cursor", "x", "v", "insert_step", "arrive_step", "lane_change")]
+
+
+_lib = None
+
+
+def lib(path: str | None = None):
+    """Load libgbtraffic.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        so = path or _build.build()
+        if not os.path.exists(so):
+            raise RuntimeError(f"libgbtraffic not built: {so}")
+        L = C.CDLL(so)
+        vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        L.sim_create.argtypes = [C.POINTER(sim_network), C.POINTER(sim_demand), C.POINTER(sim_params),
+                                 C.POINTER(vp)]
+        L.sim_create_batch.argtypes = [i32, C.POINTER(C.POINTER(sim_network)), C.POINTER(C.POINTER(sim_demand)),
+                                       C.POINTER(C.POINTER(sim_params)), C.POINTER(vp)]
+        L.sim_set_stream.argtypes = [vp, vp]
+        L.sim_route.argtypes = [vp, vp]
+        L.sim_set_routes.argtypes = [vp, vp, vp]
+        L.sim_route_size.argtypes = [vp, C.POINTER(i64)]
+        L.sim_read_routes.argtypes = [vp, vp, vp]
+        L.sim_step.argtypes = [vp, i32]
+        L.sim_read_state.argtypes = [vp, C.POINTER(sim_state_view), C.c_uint32, C.c_int]
+        L.sim_write_state.argtypes = [vp] * 7
+        L.sim_occupancy.argtypes = [vp, vp, vp]
+        L.sim_n_lanes.argtypes = [vp, C.POINTER(i64)]
+        L.sim_counters.argtypes = [vp, C.POINTER(sim_counters_t)]
+        L.sim_last_error.argtypes = [vp]
+        L.sim_last_error.restype = C.c_char_p
+        L.sim_destroy.argtypes = [vp]
+        L.sim_destroy.restype = None
+        _lib = L
+    return _lib
+
+
+class SimError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _p(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+class _Keep:
+    """Holds the numpy arrays behind a ctypes struct until the call returns."""
+
+    def __init__(self):
+        self.arrs = []
+
+    def __call__(self, a, dt):
+        a = np.ascontiguousarray(a, dtype=dt)
+        self.arrs.append(a)
+        return a.ctypes.data
+
+
+def _structs(sc, keep):
+    net, dem, par = sc["network"], sc["demand"], sc["params"]
+    n = sim_network(net["n_nodes"], net["n_links"], keep(net["node_x_dm"], np.int32),
+                    keep(net["node_y_dm"], np.int32), keep(net["node_control"], np.uint8),
+                    keep(net["signal_offset_ds"], np.int32), keep(net["signal_cycle_ds"], np.int32),
+                    keep(net["signal_green_ds"], np.int32), keep(net["link_from"], np.int32),
+                    keep(net["link_to"], np.int32), keep(net["link_length_m"], np.float32),
+                    keep(net["link_speed_mps"], np.float32), keep(net["link_lanes"], np.uint8),
+                    keep(net["link_class"], np.uint8))
+    nt = dem["n_trips"]
+    d = sim_demand(nt, keep(dem["origin"], np.int32) if nt else None,
+                   keep(dem["dest"], np.int32) if nt else None,
+                   keep(dem["depart_step"], np.int32) if nt else None)
+    p = sim_params(par["dt"], par["veh_len"], par["s_min"], par["n_class"],
+                   keep(par["v0"], np.float32), keep(par["T"], np.float32), keep(par["a"], np.float32),
+                   keep(par["b"], np.float32), keep(par["s0"], np.float32),
+                   par["mobil_p"], par["mobil_athr"], par["mobil_bsafe"], par["mobil_bias_right"],
+                   par["lambda_mand"], par["stop_acquire_m"], par["seed"] & (2**64 - 1),
+                   par["cost_mode"], par["loop_routes"])
+    return n, d, p
+
+
+class Sim:
+    """One simulation handle of libgbtraffic.
+
+    ``Sim(scenario)`` wraps ``sim_create``; ``Sim.batch([scenarios])`` wraps
+    ``sim_create_batch``.  Scenarios are the dicts of ``paper_1807_01148_gb300.scenarios``.
+    """
+
+    def __init__(self, scenario=None, *, _handle=None, n_trips=None, n_nodes=None):
+        L = lib()
+        if _handle is not None:
+            self.h = _handle
+            self.n_trips = n_trips
+            self.n_nodes = n_nodes
+        else:
+            keep = _Keep()
+            n, d, p = _structs(scenario, keep)
+            h = C.c_void_p()
+            rc = L.sim_create(C.byref(n), C.byref(d), C.byref(p), C.byref(h))
+            if rc != SIM_OK:
+                raise SimError(rc, L.sim_last_error(None).decode())
+            self.h = h
+            self.n_trips = scenario["demand"]["n_trips"]
+            self.n_nodes = scenario["network"]["n_nodes"]
+        ln = C.c_int64()
+        L.sim_n_lanes(self.h, C.byref(ln))
+        self.n_lanes = ln.value
+
+    @classmethod
+    def batch(cls, scenarios):
+        L = lib()
+        keep = _Keep()
+        structs = [_structs(s, keep) for s in scenarios]
+        k = len(structs)
+        nets = (C.POINTER(sim_network) * k)(*[C.pointer(s[0]) for s in structs])
+        dems = (C.POINTER(sim_demand) * k)(*[C.pointer(s[1]) for s in structs])
+        pars = (C.POINTER(sim_params) * k)(*[C.pointer(s[2]) for s in structs])
+        h = C.c_void_p()
+        rc = L.sim_create_batch(k, nets, dems, pars, C.byref(h))
+        if rc != SIM_OK:
+            raise SimError(rc, L.sim_last_error(None).decode())
+        return cls(_handle=h, n_trips=sum(s["demand"]["n_trips"] for s in scenarios),
+                   n_nodes=sum(s["network"]["n_nodes"] for s in scenarios))
+
+    def _check(self, rc):
+        if rc != SIM_OK:
+            raise SimError(rc, lib().sim_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_handle):
+        """stream_handle: an integer cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream)."""
+        self._check(lib().sim_set_stream(self.h, C.c_void_p(stream_handle)))
+
+    def route(self, costs=None):
+        c = None if costs is None else np.ascontiguousarray(costs, np.int32)
+        self._check(lib().sim_route(self.h, _p(c)))
+
+    def set_routes(self, offsets, links):
+        o = np.ascontiguousarray(offsets, np.int32)
+        l_ = np.ascontiguousarray(links, np.int32)
+        self._check(lib().sim_set_routes(self.h, _p(o), _p(l_)))
+
+    def routes(self):
+        n = C.c_int64()
+        self._check(lib().sim_route_size(self.h, C.byref(n)))
+        off = np.zeros(self.n_trips + 1, np.int32)
+        links = np.zeros(max(1, n.value), np.int32)
+        self._check(lib().sim_read_routes(self.h, _p(off), _p(links)))
+        return off, links[: n.value]
+
+    def step(self, n=1):
+        self._check(lib().sim_step(self.h, int(n)))
+
+    def state(self, fields=F_ALL):
+        n = self.n_trips
+        out = dict(status=np.zeros(n, np.uint8), link=np.zeros(n, np.int32), lane=np.zeros(n, np.int32),
+                   cursor=np.zeros(n, np.int32), x=np.zeros(n, np.float32), v=np.zeros(n, np.float32),
+                   insert_step=np.zeros(n, np.int32), arrive_step=np.zeros(n, np.int32),
+                   lane_change=np.zeros(n, np.int8))
+        names = ("status", "link", "lane", "cursor", "x", "v", "insert_step", "arrive_step", "lane_change")
+        view = sim_state_view(*[out[k].ctypes.data if (fields >> i) & 1 else None for i, k in enumerate(names)])
+        self._check(lib().sim_read_state(self.h, C.byref(view), fields, 0))
+        return {k: out[k] for i, k in enumerate(names) if (fields >> i) & 1}
+
+    def state_device(self, tensors: dict, fields: int):
+        """Read fields into caller-owned device buffers (e.g. torch CUDA tensors)."""
+        names = ("status", "link", "lane", "cursor", "x", "v", "insert_step", "arrive_step", "lane_change")
+        view = sim_state_view(*[tensors[k].data_ptr() if (fields >> i) & 1 else None for i, k in enumerate(names)])
+        self._check(lib().sim_read_state(self.h, C.byref(view), fields, 1))
+
+    def write_state(self, st):
+        self._check(lib().sim_write_state(
+            self.h, _p(np.ascontiguousarray(st["status"], np.uint8)),
+            _p(np.ascontiguousarray(st["link"], np.int32)), _p(np.ascontiguousarray(st["lane"], np.int32)),
+            _p(np.ascontiguousarray(st["cursor"], np.int32)), _p(np.ascontiguousarray(st["x"], np.float32)),
+            _p(np.ascontiguousarray(st["v"], np.float32))))
+
+    def occupancy(self):
+        start = np.zeros(self.n_lanes + 1, np.int32)
+        vids = np.zeros(max(1, self.n_trips), np.int32)
+        self._check(lib().sim_occupancy(self.h, _p(start), _p(vids)))
+        return start, vids[: start[-1]]
+
+    def counters(self):
+        c = sim_counters_t()
+        self._check(lib().sim_counters(self.h, C.byref(c)))
+        return {k: getattr(c, k) for k, _ in sim_counters_t._fields_}
+
+
+def setup(scenario, sim=None):
+    """Create (or reuse) a handle and give it the scenario's routes and initial state."""
+    s = sim or Sim(scenario)
+    if "routes" in scenario:
+        s.set_routes(scenario["routes"]["offsets"], scenario["routes"]["links"])
+    else:
+        s.route()
+    if "init_state" in scenario:
+        s.write_state(scenario["init_state"])
+    return s
