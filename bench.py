@@ -1,0 +1,377 @@
+"""Benchmark: vehicle-steps/s of the traffic microsimulation hot path on one GB300.
+
+Workload (default): the metropolitan network (225,000 nodes, 550,000 links, 3,000,000
+gravity-OD trips; dt = 0.5 s) with every trip on its GPU-planned shortest-path route
+and all of them on the road at once (the saturated snapshot).  One
+bench step = one simulation step of the whole hot path (occupancy rebuild,
+neighbours, lane changes, IDM, admission and transitions, departures, counters).
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle instead (the
+reference arm of this build), on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "vehicle-steps/s"
+UNIT = "vehicle-steps/s"
+
+# Algorithmic bytes per active vehicle that each kernel must move (every array element
+# it has to read or write once; re-reads of neighbours and per-link records not counted).
+ALG_BYTES = {
+    "count": 8 + 8 + 4,          # link, lane; lane counter read+write; arrival index
+    "scatter": 20 + 4 + 16,      # link, lane, x, vid, arrival index; lane start; 4 scatter words
+    "rank": 16 + 4 + 28 + 28,    # scatter words; lane start; state gather from A; state write to B
+    "own": 24 + 4 + 9,           # x, v, vid, link, nxt, lane; lane end; a_own, xo, flags
+    "decide": 13,                # link, x, xo; intent (eligible vehicles read more, not counted)
+    "move": 28 + 9 + 28 + 1,     # sorted state; flags, intent, acceleration; next state; decision
+    "acquire": 12,               # link, lane, lane end
+}
+
+
+# DRAM bytes per active vehicle per launch from the ncu capture summarised in
+# profiles/step_kernels_metro_snapshot.md, valid only for the kernel source it was taken on.
+PROFILED_SRC_SHA = "e9ce4229aa9a6eda"
+PROFILED_TRAFFIC = {"decide": 61.9, "own": 49.0, "move": 65.7, "rank": 44.1}
+
+
+def kernel_source_sha():
+    import hashlib
+    p = os.path.join(ROOT, "paper_1807_01148_gb300", "csrc", "gbt_step.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="metro", choices=["metro", "metro-walk"],
+                    help="metro: GPU-planned shortest-path routes; metro-walk: the first --trips trips on "
+                         "random-walk routes (no trip planning; smaller cases for profiling)")
+    ap.add_argument("--trips", type=int, default=0, help="metro-walk: number of trips (0 = all)")
+    ap.add_argument("--sample-frac", type=float, default=0.1,
+                    help="fraction of trips in the CPU oracle's bounded sample")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------- helpers
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0, period_ms=50):
+        self.index = index
+        self.period = period_ms
+        self.proc = None
+        self.lines = []
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 f"-lms", str(self.period)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        rows = []
+        for ts, line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            rows.append((ts, f))
+        inside = [f for ts, f in rows if self.t0 and self.t1 and self.t0 - 0.05 <= ts <= self.t1 + 0.05]
+        use = inside if inside else [f for _, f in rows]
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(f[1]) for f in use if f[1].replace(".", "").isdigit()]
+        mx = [float(f[2]) for f in use if f[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for f in use for i in range(4) if f[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(use), "samples_in_timed_region": len(inside)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def lscpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if "Model name" in line:
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+# ---------------------------------------------------------------------------- oracle arm
+def oracle_sample(frac, seed=1807011499):
+    """Bounded sample of the workload for the CPU oracle: the same metro network and
+    snapshot recipe with a random ``frac`` of the trips, routed by the oracle itself is
+    too slow (one Dijkstra per origin over 225k nodes), so the sample's trips follow
+    random-walk routes of the same mean length (inputs, not derived from the GPU)."""
+    from paper_1807_01148_gb300 import scenarios as S
+    m = S.metro()
+    rng = np.random.default_rng(seed)
+    keep = np.sort(rng.choice(m["demand"]["n_trips"], int(m["demand"]["n_trips"] * frac), replace=False))
+    d = m["demand"]
+    m["demand"] = S._demand(d["origin"][keep], d["dest"][keep], d["depart_step"][keep])
+    off, links = S.random_walk_routes(m, min_hops=20, max_hops=90)
+    st = S.saturate(m, off, links)
+    return m, off, links, st
+
+
+def time_oracle(frac, steps, warmup, budget_s=None):
+    import oracle
+    m, off, links, st = oracle_sample(frac)
+    o = oracle.OracleSim(m)
+    o.set_routes(off, links)
+    o.write_state(st)
+    o.step(warmup)
+    c0 = o.counters()
+    t0 = time.perf_counter()
+    n = 0
+    while n < steps:
+        o.step(1)
+        n += 1
+        if budget_s and time.perf_counter() - t0 > budget_s and n >= 1:
+            break
+    dt = time.perf_counter() - t0
+    c1 = o.counters()
+    vs = c1["veh_steps"] - c0["veh_steps"]
+    return dict(value=vs / dt, steps=n, seconds=dt, veh_steps=vs, trips=m["demand"]["n_trips"])
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    r = time_oracle(args.sample_frac, args.steps, args.warmup)
+    cores = 1
+    sample = (f"{r['trips']} of 3,000,000 metro trips ({args.sample_frac:.0%}) in the saturated snapshot "
+              f"recipe on the full 225k-node network, random-walk routes; {r['steps']} steps")
+    line = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": r["steps"], "warmup": args.warmup, "ms_per_step": 1e3 * r["seconds"] / max(1, r["steps"]),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "metro saturated snapshot (bounded sample for the CPU oracle)",
+                       "network": "225000 nodes / 550000 links", "trips_in_sample": r["trips"]},
+            "cpu_baseline": {"value": r["value"], "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu": lscpu_model()},
+            "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------- cuda arm
+def run_cuda(args):
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1807_01148_gb300 import gbtraffic as G
+    from paper_1807_01148_gb300 import scenarios as S
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    m = S.metro()
+    if args.workload == "metro-walk" and args.trips:
+        d = m["demand"]
+        k = args.trips
+        m["demand"] = S._demand(d["origin"][:k], d["dest"][:k], d["depart_step"][:k])
+    stream = torch.cuda.current_stream()
+    g = G.Sim(m)
+    g.set_stream(stream.cuda_stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if args.workload == "metro":
+        g.route()
+        off, links = g.routes()
+    else:
+        off, links = S.random_walk_routes(m, min_hops=20, max_hops=90)
+        g.set_routes(off, links)
+    torch.cuda.synchronize()
+    route_s = time.perf_counter() - t0
+    snap = S.saturate(m, off, links)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local).start()
+
+    # -- main timed region: K graph-launched steps from the snapshot
+    g.write_state(snap)
+    g.step(args.warmup)
+    c0 = g.counters()
+    barrier()
+    clocks.mark("t0")
+    ev0.record(stream)
+    g.step(args.steps)
+    ev1.record(stream)
+    barrier()
+    clocks.mark("t1")
+    ms = ev0.elapsed_time(ev1)
+    c1 = g.counters()
+    veh_steps = c1["veh_steps"] - c0["veh_steps"]
+    kernels_per_step = 10 + (1 if int((m["network"]["node_control"] == 1).sum()) else 0) + \
+        (1 if int((snap["status"] == 0).sum()) else 0)
+    clk = clocks.stop()
+
+    # -- per-kernel device times over the same K steps (events after every kernel)
+    g.write_state(snap)
+    g.step(args.warmup)
+    c2 = g.counters()
+    kms = g.step_timed(args.steps)
+    c3 = g.counters()
+    avg_active = (c3["veh_steps"] - c2["veh_steps"]) / max(1, args.steps)
+    dom = max((k for k in kms if k in ALG_BYTES), key=lambda k: kms[k])
+    per_launch_ms = kms[dom] / args.steps
+    achieved = ALG_BYTES[dom] * avg_active / (per_launch_ms * 1e-3) / 1e9
+
+    # -- end to end through the C ABI with host buffers: load the snapshot from pinned host
+    #    memory, then every step read positions and speeds back to pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in snap.items()}
+        n = m["demand"]["n_trips"]
+        hx = torch.empty(n, dtype=torch.float32).pin_memory()
+        hv = torch.empty(n, dtype=torch.float32).pin_memory()
+        view = G.sim_state_view(None, None, None, None, hx.data_ptr(), hv.data_ptr(), None, None, None)
+        import ctypes
+        L = G.lib()
+        e_steps = min(args.steps, 100)
+        barrier()
+        t0 = time.perf_counter()
+        rc = L.sim_write_state(g.h, *[ctypes.c_void_p(pin[k].data_ptr()) for k in
+                                       ("status", "link", "lane", "cursor", "x", "v")])
+        assert rc == 0, L.sim_last_error(g.h)
+        ce0 = g.counters()
+        for _ in range(e_steps):
+            rc = L.sim_step(g.h, 1)
+            assert rc == 0
+            rc = L.sim_read_state(g.h, ctypes.byref(view), G.F_X | G.F_V, 0)
+            assert rc == 0
+        ce1 = g.counters()
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        h2d = sum(int(v.numel() * v.element_size()) for v in pin.values())
+        e2e = {"value": (ce1["veh_steps"] - ce0["veh_steps"]) / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / e_steps, "d2h_bytes_per_step": 8 * n + 64,
+               "steps": e_steps, "pattern": "sim_write_state(host snapshot) then per step sim_step(1) + "
+                                            "sim_read_state(x, v -> pinned host)"}
+
+    # -- aggregate over ranks (replicas only: each rank runs its own copy)
+    secs = ms / 1e3
+    tot_vs = veh_steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([secs], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        v = torch.tensor([float(veh_steps)], device="cuda")
+        dist.all_reduce(v, op=dist.ReduceOp.SUM)
+        secs, tot_vs = float(t.item()), float(v.item())
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        r = time_oracle(args.sample_frac, 50, 1, budget_s=20.0)
+        cpu = {"value": r["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{r['trips']} trips ({args.sample_frac:.0%} of the metro demand) in the saturated "
+                         f"snapshot recipe on the full network, random-walk routes; {r['steps']} steps, "
+                         f"{r['seconds']:.1f} s single-threaded",
+               "cpu": lscpu_model()}
+    line = {
+        "metric": METRIC, "value": tot_vs / secs, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": ("metro (225000 nodes, 550000 links, 3000000 trips) saturated snapshot: all trips "
+                                "on their GPU-planned shortest-path routes at once") if args.workload == "metro" else
+                               f"metro network, {m['demand']['n_trips']} trips on random-walk routes, saturated",
+                   "dt_s": 0.5, "avg_active_vehicles": tot_vs / world / args.steps,
+                   "l2": "working set > L2 (state, scratch and per-lane arrays ~0.5 GB; no flush)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                     "alg_bytes_per_vehicle": ALG_BYTES[dom],
+                     "traffic": (PROFILED_TRAFFIC[dom] * avg_active
+                                 if kernel_source_sha() == PROFILED_SRC_SHA and dom in PROFILED_TRAFFIC else None),
+                     "traffic_note": "ncu dram bytes per vehicle on a 1M-trip capture, scaled to this launch's "
+                                     "vehicles; null when the kernel source changed since"},
+        "per_kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+        "routing": {"seconds": route_s, "mode": "gpu sim_route" if args.workload == "metro" else "set_routes", "origins_trees": int(len(np.unique(m["demand"]["origin"]))),
+                    "trips": m["demand"]["n_trips"], "hops": int(off[-1])},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clk,
+        "gpu_launches": kernels_per_step * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_cuda(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -169,6 +169,18 @@ int sim_read_routes(sim_handle* h, int32_t* offsets, int32_t* links);
  * without a host round trip.  Errors: SIM_ESTATE (no routes), SIM_EDEVICE. */
 int sim_step(sim_handle* h, int32_t n_steps);
 
+/* Number of kernels in one step (see sim_kernel_name). */
+#define SIM_N_KERNELS 12
+
+/* Advance n_steps like sim_step, but launch every kernel directly with a CUDA event
+ * after each one, and add each kernel's device time (ms, including its launch gap)
+ * into kernel_ms[SIM_N_KERNELS] (host array, zeroed first).  Results are identical
+ * to sim_step.  For profiling; slower than sim_step's graph launch. */
+int sim_step_timed(sim_handle* h, int32_t n_steps, float* kernel_ms);
+
+/* Name of kernel k of a step (0 <= k < SIM_N_KERNELS), "" otherwise. */
+const char* sim_kernel_name(int32_t k);
+
 /* Read the per-trip state (fields = OR of SIM_F_*).  on_device = 1: the view's
  * pointers are device pointers (e.g. from torch tensors) of n_trips elements each;
  * on_device = 0: host pointers.  The call synchronises the stream. */

@@ -20,6 +20,9 @@ void launch_state_out(const Dev& d, int grid, cudaStream_t s, uint8_t* status, i
 void launch_state_in(const Dev& d, int grid, cudaStream_t s, const uint8_t* status, const int32_t* link,
                      const int32_t* lane, const int32_t* cursor, const float* x, const float* v);
 void launch_occ_out(const Dev& d, int grid, cudaStream_t s, int32_t* sorted_vid);
+void launch_state_check(const Dev& d, int grid, cudaStream_t s, const uint8_t* status, const int32_t* link,
+                        const int32_t* lane, const int32_t* cursor, const float* x, const float* v, int* bad);
+cudaError_t launch_steps_timed(const Dev& d, int grid, bool has_stop, cudaStream_t s, int n, float* kernel_ms);
 void launch_first_links(const int32_t* roff, const int32_t* routes, int n, int32_t* out, cudaStream_t s);
 }  // namespace gbt
 
@@ -616,7 +619,8 @@ int sim_route(sim_handle* h, const int32_t* link_cost_ds) {
   R.work = work;
   R.delta = delta;
   R.ctl = h->d.ctl;
-  unsigned long long cap = std::max<unsigned long long>(1024, (unsigned long long)std::max(1, nt) * 256ULL);
+  // initial reservation of the route store; a second pass with the exact size follows if it overflows
+  unsigned long long cap = std::max<unsigned long long>(1024, (unsigned long long)std::max(1, nt) * 96ULL);
   for (int attempt = 0; attempt < 2; attempt++) {
     dfree(h, h->routes);
     h->routes = nullptr;
@@ -753,6 +757,15 @@ int sim_step(sim_handle* h, int32_t n_steps) {
   return check_device(h);
 }
 
+int sim_step_timed(sim_handle* h, int32_t n_steps, float* kernel_ms) {
+  if (!h || n_steps < 0 || !kernel_ms) return SIM_EINVAL;
+  if (!h->routed) return fail(h, SIM_ESTATE, "sim_step_timed before sim_route / sim_set_routes");
+  CK(launch_steps_timed(h->d, h->grid, h->has_stop, h->stream, n_steps, kernel_ms));
+  return check_device(h);
+}
+
+const char* sim_kernel_name(int32_t k) { return (k >= 0 && k < kNumKernels) ? kKernelNames[k] : ""; }
+
 int sim_read_state(sim_handle* h, const sim_state_view* out, uint32_t fields, int on_device) {
   if (!h || !out) return SIM_EINVAL;
   const size_t nt = (size_t)h->nt;
@@ -796,43 +809,49 @@ int sim_write_state(sim_handle* h, const uint8_t* status, const int32_t* link, c
   if (!h || !status || !link || !lane || !cursor || !x || !v) return SIM_EINVAL;
   if (!h->routed) return fail(h, SIM_ESTATE, "sim_write_state before routes exist");
   const int nt = h->nt;
-  std::vector<int32_t> off(nt), len(nt), all((size_t)std::max<unsigned long long>(1, h->route_cap));
-  if (nt) {
-    CK(cudaMemcpy(off.data(), h->d.roff, (size_t)nt * 4, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(len.data(), h->d.rlen, (size_t)nt * 4, cudaMemcpyDeviceToHost));
-  }
-  if (h->route_cap) CK(cudaMemcpy(all.data(), h->routes, (size_t)h->route_cap * 4, cudaMemcpyDeviceToHost));
-  for (int i = 0; i < nt; i++) {
-    if (status[i] > SIM_ARRIVED) return fail(h, SIM_EINVAL, "status must be 0, 1 or 2");
-    if (status[i] != SIM_ACTIVE) continue;
-    if (cursor[i] < 0 || cursor[i] >= len[i] || all[(size_t)off[i] + cursor[i]] != link[i])
-      return fail(h, SIM_EINVAL, "active trip not on route[cursor]");
-    if (lane[i] < 0 || lane[i] >= h->lanes[link[i]]) return fail(h, SIM_EINVAL, "lane out of range");
-    if (!(x[i] >= 0.0f) || !(x[i] <= h->len[link[i]]) || !(v[i] >= 0.0f))
-      return fail(h, SIM_EINVAL, "position must be in [0, length] and speed >= 0");
-  }
-  int rc = reset_dynamic(h);
-  if (rc) return rc;
-  std::vector<void*> tmp;
   uint8_t* ds;
-  int32_t *dl, *dn, *dc;
+  int32_t *dl, *dn, *dc, *dbad;
   float *dx, *dv;
   const size_t n = (size_t)std::max(1, nt);
+  int rc;
   if ((rc = dalloc(h, &ds, n)) || (rc = dalloc(h, &dl, n)) || (rc = dalloc(h, &dn, n)) || (rc = dalloc(h, &dc, n)) ||
-      (rc = dalloc(h, &dx, n)) || (rc = dalloc(h, &dv, n)))
+      (rc = dalloc(h, &dx, n)) || (rc = dalloc(h, &dv, n)) || (rc = dalloc(h, &dbad, 1)))
     return rc;
-  void* tl[6] = {ds, dl, dn, dc, dx, dv};
-  if (nt) {
-    cudaMemcpy(ds, status, (size_t)nt, cudaMemcpyHostToDevice);
-    cudaMemcpy(dl, link, (size_t)nt * 4, cudaMemcpyHostToDevice);
-    cudaMemcpy(dn, lane, (size_t)nt * 4, cudaMemcpyHostToDevice);
-    cudaMemcpy(dc, cursor, (size_t)nt * 4, cudaMemcpyHostToDevice);
-    cudaMemcpy(dx, x, (size_t)nt * 4, cudaMemcpyHostToDevice);
-    cudaMemcpy(dv, v, (size_t)nt * 4, cudaMemcpyHostToDevice);
-    launch_state_in(h->d, h->grid, h->stream, ds, dl, dn, dc, dx, dv);
+  void* tl[7] = {ds, dl, dn, dc, dx, dv, dbad};
+  auto release = [&]() {
+    for (void* p : tl) dfree(h, p);
+  };
+  int bad = 0;
+  cudaError_t e = cudaMemsetAsync(dbad, 0, 4, h->stream);
+  if (nt && e == cudaSuccess) {
+    const cudaMemcpyKind k = cudaMemcpyHostToDevice;
+    e = cudaMemcpyAsync(ds, status, (size_t)nt, k, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dl, link, (size_t)nt * 4, k, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dn, lane, (size_t)nt * 4, k, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dc, cursor, (size_t)nt * 4, k, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dx, x, (size_t)nt * 4, k, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dv, v, (size_t)nt * 4, k, h->stream);
+    if (e == cudaSuccess) launch_state_check(h->d, h->grid, h->stream, ds, dl, dn, dc, dx, dv, dbad);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, dbad, 4, cudaMemcpyDeviceToHost, h->stream);
   }
-  cudaError_t e = cudaStreamSynchronize(h->stream);
-  for (void* p : tl) dfree(h, p);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(h, e, "write_state upload");
+  }
+  if (bad) {
+    release();
+    return fail(h, SIM_EINVAL, std::to_string(bad) +
+                                   " trips: status not 0..2, or active trip not on route[cursor] with a valid lane, "
+                                   "0 <= x <= length and v >= 0");
+  }
+  if ((rc = reset_dynamic(h))) {
+    release();
+    return rc;
+  }
+  if (nt) launch_state_in(h->d, h->grid, h->stream, ds, dl, dn, dc, dx, dv);
+  e = cudaStreamSynchronize(h->stream);
+  release();
   if (e != cudaSuccess) return cuda_fail(h, e, "write_state");
   std::vector<uint8_t> st(status, status + nt);
   if ((rc = build_queues(h, st))) return rc;

@@ -151,6 +151,11 @@ struct RouteDev {
 
 void launch_route(const RouteDev& R, int n_cta, cudaStream_t s);
 
+// kernels of one step, in launch order
+enum { kKCount, kKScanSum, kKScanTop, kKScanFin, kKScatter, kKRank, kKAcquire, kKOwn, kKDecide, kKMove, kKInsert,
+       kKFinish, kNumKernels };
+extern const char* const kKernelNames[kNumKernels];
+
 constexpr uint8_t kFlagFront = 1, kFlagHolder = 2, kFlagCand = 4;
 
 // ---------------------------------------------------------------- model functions

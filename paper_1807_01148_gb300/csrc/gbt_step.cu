@@ -178,11 +178,6 @@ __global__ void k_acquire(Dev d) {
 }
 
 // ------------------------------------------------------------------ neighbours / IDM
-struct Ctx {
-  const Dev& d;
-  long long t;
-};
-
 __device__ __forceinline__ bool is_holder(const Dev& d, const LinkRec& L, long long t, int vid, int lane,
                                           bool front) {
   if (L.ctrl != kCtrlStop) return false;
@@ -518,24 +513,75 @@ __global__ void k_finish(Dev d) {
 // ------------------------------------------------------------------ launch sequence
 int scan_blocks(int n_lanes) { return (n_lanes + kScanChunk - 1) / kScanChunk; }
 
+void launch_kernel(int k, const Dev& d, int grid, cudaStream_t s);
+
 void launch_occupancy(const Dev& d, int grid, cudaStream_t s) {
+  for (int k = kKCount; k <= kKRank; k++) launch_kernel(k, d, grid, s);
+}
+
+// Kernels of one step, in launch order (names reported by the timed step).
+const char* const kKernelNames[kNumKernels] = {"count", "scan_sum", "scan_top", "scan_fin", "scatter", "rank",
+                                               "acquire", "own", "decide", "move", "insert", "finish"};
+
+bool kernel_enabled(int k, const Dev& d, bool has_stop) {
+  if (k == kKAcquire) return has_stop;
+  if (k == kKInsert) return d.n_qlinks > 0;
+  return true;
+}
+
+void launch_kernel(int k, const Dev& d, int grid, cudaStream_t s) {
   const int nb = scan_blocks(d.n_lanes);
-  k_count<<<grid, 256, 0, s>>>(d);
-  k_scan_sum<<<nb, kScanThreads, 0, s>>>(d);
-  k_scan_top<<<1, 1024, 0, s>>>(d, nb);
-  k_scan_fin<<<nb, kScanThreads, 0, s>>>(d);
-  k_scatter<<<grid, 256, 0, s>>>(d);
-  k_rank<<<grid, 256, 0, s>>>(d);
+  switch (k) {
+    case kKCount: k_count<<<grid, 256, 0, s>>>(d); break;
+    case kKScanSum: k_scan_sum<<<nb, kScanThreads, 0, s>>>(d); break;
+    case kKScanTop: k_scan_top<<<1, 1024, 0, s>>>(d, nb); break;
+    case kKScanFin: k_scan_fin<<<nb, kScanThreads, 0, s>>>(d); break;
+    case kKScatter: k_scatter<<<grid, 256, 0, s>>>(d); break;
+    case kKRank: k_rank<<<grid, 256, 0, s>>>(d); break;
+    case kKAcquire: k_acquire<<<grid, 256, 0, s>>>(d); break;
+    case kKOwn: k_own<<<grid, 256, 0, s>>>(d); break;
+    case kKDecide: k_decide<<<grid, 256, 0, s>>>(d); break;
+    case kKMove: k_move<<<grid, 256, 0, s>>>(d); break;
+    case kKInsert: {
+      int g = (d.n_qlinks + 255) / 256;
+      k_insert<<<g < grid ? g : grid, 256, 0, s>>>(d);
+      break;
+    }
+    case kKFinish: k_finish<<<1, 1, 0, s>>>(d); break;
+    default: break;
+  }
 }
 
 void launch_step(const Dev& d, int grid, bool has_stop, cudaStream_t s) {
-  launch_occupancy(d, grid, s);
-  if (has_stop) k_acquire<<<grid, 256, 0, s>>>(d);
-  k_own<<<grid, 256, 0, s>>>(d);
-  k_decide<<<grid, 256, 0, s>>>(d);
-  k_move<<<grid, 256, 0, s>>>(d);
-  if (d.n_qlinks > 0) k_insert<<<(d.n_qlinks + 255) / 256 < grid ? (d.n_qlinks + 255) / 256 : grid, 256, 0, s>>>(d);
-  k_finish<<<1, 1, 0, s>>>(d);
+  for (int k = 0; k < kNumKernels; k++)
+    if (kernel_enabled(k, d, has_stop)) launch_kernel(k, d, grid, s);
+}
+
+// The same step with an event after every kernel: per-kernel device time (ms)
+// accumulated into kernel_ms over n steps.
+cudaError_t launch_steps_timed(const Dev& d, int grid, bool has_stop, cudaStream_t s, int n, float* kernel_ms) {
+  cudaEvent_t ev[kNumKernels + 1];
+  for (int k = 0; k <= kNumKernels; k++) {
+    cudaError_t e = cudaEventCreate(&ev[k]);
+    if (e != cudaSuccess) return e;
+  }
+  for (int k = 0; k < kNumKernels; k++) kernel_ms[k] = 0.0f;
+  cudaError_t err = cudaSuccess;
+  for (int it = 0; it < n && err == cudaSuccess; it++) {
+    cudaEventRecord(ev[0], s);
+    for (int k = 0; k < kNumKernels; k++) {
+      if (kernel_enabled(k, d, has_stop)) launch_kernel(k, d, grid, s);
+      cudaEventRecord(ev[k + 1], s);
+    }
+    err = cudaEventSynchronize(ev[kNumKernels]);
+    for (int k = 0; k < kNumKernels && err == cudaSuccess; k++) {
+      float ms = 0.0f;
+      err = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+      kernel_ms[k] += ms;
+    }
+  }
+  for (int k = 0; k <= kNumKernels; k++) cudaEventDestroy(ev[k]);
+  return err;
 }
 
 // ------------------------------------------------------------------ state I/O kernels
@@ -572,6 +618,26 @@ void launch_state_out(const Dev& d, int grid, cudaStream_t s, uint8_t* status, i
                       int32_t* cursor, float* x, float* v, int32_t* ins, int32_t* arr, int8_t* dec) {
   k_state_out<<<grid, 256, 0, s>>>(d, status, link, lane, cursor, x, v, ins, arr, dec);
   k_state_out_active<<<grid, 256, 0, s>>>(d, link, lane, cursor, x, v);
+}
+
+// Validate a state given by vid: every active trip sits on route[cursor], in a lane
+// of that link, with 0 <= x <= length and v >= 0.  Counts the violations.
+__global__ void k_state_check(Dev d, const uint8_t* status, const int32_t* link, const int32_t* lane,
+                              const int32_t* cursor, const float* x, const float* v, int* bad) {
+  GRID_STRIDE(i, d.n_trips) {
+    if (status[i] > kArrived) { atomicAdd(bad, 1); continue; }
+    if (status[i] != kActive) continue;
+    const int k = cursor[i], e = link[i];
+    bool ok = k >= 0 && k < d.rlen[i] && e >= 0 && e < d.n_links && d.routes[d.roff[i] + k] == e;
+    ok = ok && lane[i] >= 0 && lane[i] < d.links[e].lanes && x[i] >= 0.0f && x[i] <= d.links[e].len &&
+         v[i] >= 0.0f;
+    if (!ok) atomicAdd(bad, 1);
+  }
+}
+
+void launch_state_check(const Dev& d, int grid, cudaStream_t s, const uint8_t* status, const int32_t* link,
+                        const int32_t* lane, const int32_t* cursor, const float* x, const float* v, int* bad) {
+  k_state_check<<<grid, 256, 0, s>>>(d, status, link, lane, cursor, x, v, bad);
 }
 
 // Load a state (by vid) into buffer A: active trips are packed into slots by an

@@ -20,8 +20,9 @@ ERR_NAMES = {0: "SIM_OK", -1: "SIM_EINVAL", -2: "SIM_ENOMEM", -3: "SIM_ECUDA", -
 F_STATUS, F_LINK, F_LANE, F_CURSOR, F_X, F_V, F_INSERT, F_ARRIVE, F_LANECHANGE = (1 << k for k in range(9))
 F_ALL = (1 << 9) - 1
 
+N_KERNELS = 12
 EXPORTS = ["sim_create", "sim_create_batch", "sim_set_stream", "sim_route", "sim_set_routes", "sim_route_size",
-           "sim_read_routes", "sim_step", "sim_read_state", "sim_write_state", "sim_occupancy", "sim_n_lanes",
+           "sim_read_routes", "sim_step", "sim_step_timed", "sim_kernel_name", "sim_read_state", "sim_write_state", "sim_occupancy", "sim_n_lanes",
            "sim_counters", "sim_last_error", "sim_destroy"]
 
 
@@ -79,6 +80,9 @@ def lib(path: str | None = None):
         L.sim_route_size.argtypes = [vp, C.POINTER(i64)]
         L.sim_read_routes.argtypes = [vp, vp, vp]
         L.sim_step.argtypes = [vp, i32]
+        L.sim_step_timed.argtypes = [vp, i32, vp]
+        L.sim_kernel_name.argtypes = [i32]
+        L.sim_kernel_name.restype = C.c_char_p
         L.sim_read_state.argtypes = [vp, C.POINTER(sim_state_view), C.c_uint32, C.c_int]
         L.sim_write_state.argtypes = [vp] * 7
         L.sim_occupancy.argtypes = [vp, vp, vp]
@@ -217,6 +221,12 @@ class Sim:
 
     def step(self, n=1):
         self._check(lib().sim_step(self.h, int(n)))
+
+    def step_timed(self, n=1):
+        """Advance n steps with an event after every kernel; returns {kernel name: ms}."""
+        ms = np.zeros(N_KERNELS, np.float32)
+        self._check(lib().sim_step_timed(self.h, int(n), _p(ms)))
+        return {lib().sim_kernel_name(k).decode(): float(ms[k]) for k in range(N_KERNELS)}
 
     def state(self, fields=F_ALL):
         n = self.n_trips

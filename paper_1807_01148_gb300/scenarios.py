@@ -347,3 +347,101 @@ def small_metro(nx: int = 24, ny: int = 20, n_trips: int = 4000, steps: int = 12
     sc["demand"]["depart_step"] = np.ascontiguousarray(dep * (steps // 2) // 172_800, np.int32)
     sc["name"] = f"metro{nx}x{ny}"
     return sc
+
+
+# --------------------------------------------------------------------------- snapshots
+def random_walk_routes(sc: dict, min_hops: int = 20, max_hops: int = 120, seed: int = BASE_SEED + 20):
+    """Explicit routes for every trip: a random walk from the trip's origin that never
+    takes the link straight back (unless it is the only way on), of uniform length in
+    [min_hops, max_hops].  An input recipe for large stepping cases that need routes
+    without running trip planning; returns (offsets, links)."""
+    net = sc["network"]
+    nn, lf, lt = net["n_nodes"], net["link_from"].astype(np.int64), net["link_to"].astype(np.int64)
+    order = np.argsort(lf, kind="stable")
+    start = np.zeros(nn + 1, np.int64)
+    np.add.at(start, lf + 1, 1)
+    start = np.cumsum(start)
+    outl = order
+    deg = start[1:] - start[:-1]
+    rng = np.random.default_rng(seed)
+    nt = sc["demand"]["n_trips"]
+    hops = rng.integers(min_hops, max_hops + 1, nt)
+    node = sc["demand"]["origin"].astype(np.int64).copy()
+    prev_from = np.full(nt, -1, np.int64)
+    out = np.full((max_hops, nt), -1, np.int64)
+    for k in range(max_hops):
+        live = k < hops
+        d = deg[node]
+        pick = rng.integers(0, 1 << 30, nt) % np.maximum(d, 1)
+        e = outl[start[node] + pick]
+        back = (lt[e] == prev_from) & (d > 1)
+        pick2 = (pick + 1) % np.maximum(d, 1)
+        e = np.where(back, outl[start[node] + pick2], e)
+        out[k] = np.where(live, e, -1)
+        prev_from = np.where(live, node, prev_from)
+        node = np.where(live, lt[e], node)
+    links = out.T[out.T >= 0]
+    offsets = np.zeros(nt + 1, np.int64)
+    offsets[1:] = np.cumsum(hops)
+    return offsets.astype(np.int32), links.astype(np.int32)
+
+
+def saturate(sc: dict, offsets, links, spacing: float = 8.0, v_frac: float = 0.5,
+             seed: int = BASE_SEED + 21) -> dict:
+    """A saturated snapshot: every trip on the road at once.  Trip i sits on hop
+    k ~ U{0..len_i-1} of its route, in a uniformly drawn lane; vehicles of one lane are
+    spread evenly along it (at most one per ``spacing`` metres, excess trips are
+    re-drawn onto other hops, and after 30 rounds left pending), moving at ``v_frac``
+    of the link speed limit.  Returns a per-trip state dict (status, link, lane,
+    cursor, x, v)."""
+    net = sc["network"]
+    L = net["link_length_m"].astype(np.float64)
+    lanes = net["link_lanes"].astype(np.int64)
+    base = np.zeros(len(L) + 1, np.int64)
+    base[1:] = np.cumsum(lanes)
+    cap = np.maximum(1, np.floor(L / spacing)).astype(np.int64)
+    off = np.asarray(offsets, np.int64)
+    lk = np.asarray(links, np.int64)
+    nt = len(off) - 1
+    rlen = off[1:] - off[:-1]
+    rng = np.random.default_rng(seed)
+    cursor = np.zeros(nt, np.int64)
+    lane = np.zeros(nt, np.int64)
+    placed = np.zeros(nt, bool)
+    todo = np.arange(nt)
+    fill = np.zeros(base[-1], np.int64)
+    for _ in range(30):
+        if len(todo) == 0:
+            break
+        k = (rng.random(len(todo)) * rlen[todo]).astype(np.int64)
+        e = lk[off[todo] + k]
+        ln = (rng.random(len(todo)) * lanes[e]).astype(np.int64)
+        g = base[e] + ln
+        order = np.argsort(g, kind="stable")
+        gs = g[order]
+        first = np.r_[0, np.flatnonzero(gs[1:] != gs[:-1]) + 1]
+        run_start = np.repeat(first, np.diff(np.r_[first, len(gs)]))
+        rank = np.arange(len(gs)) - run_start + fill[gs]
+        ok_sorted = rank < cap[e[order]]
+        ok = np.zeros(len(todo), bool)
+        ok[order] = ok_sorted
+        np.add.at(fill, g[ok], 1)
+        idx = todo[ok]
+        cursor[idx], lane[idx], placed[idx] = k[ok], ln[ok], True
+        todo = todo[~ok]
+    link = np.where(placed, lk[off[:-1] + cursor], -1)
+    g = np.where(placed, base[np.maximum(link, 0)] + lane, -1)
+    key = rng.random(nt)
+    order = np.lexsort((key, g))
+    order = order[placed[order]]
+    gs = g[order]
+    first = np.r_[0, np.flatnonzero(gs[1:] != gs[:-1]) + 1]
+    counts = np.diff(np.r_[first, len(gs)])
+    rank = np.arange(len(gs)) - np.repeat(first, counts)
+    cnt = np.repeat(counts, counts)
+    x = np.zeros(nt, np.float64)
+    x[order] = (rank + 0.5) * L[link[order]] / cnt
+    v = np.where(placed, v_frac * net["link_speed_mps"].astype(np.float64)[np.maximum(link, 0)], 0.0)
+    return dict(status=np.where(placed, ST_ACTIVE, ST_PENDING).astype(np.uint8),
+                link=np.where(placed, link, 0).astype(np.int32), lane=lane.astype(np.int32),
+                cursor=cursor.astype(np.int32), x=x.astype(np.float32), v=v.astype(np.float32))
