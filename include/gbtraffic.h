@@ -201,6 +201,44 @@ int sim_n_lanes(sim_handle* h, int64_t* n_lanes);
 
 int sim_counters(sim_handle* h, sim_counters_t* out);
 
+/* Largest graph sim_sssp_static accepts (nodes). */
+#define SIM_SSSP_STATIC_MAX_NODES 262144
+
+/* One shortest-path tree without any device allocation.  The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc, such as code
+ * running while a framework owns the whole device memory pool, processes whose
+ * device memory is capped by a supervisor, or plug-ins that must not change the
+ * device's allocation state.
+ *
+ * It runs the same near-far search as sim_route's per-origin trees on a graph the
+ * caller already holds in device memory, and writes dist_out[v] = length of the
+ * shortest path origin -> v in the caller's integer costs (INT32_MAX when v is
+ * unreachable).  All pointers are DEVICE pointers owned by the caller:
+ *   out_start [n_nodes+1]  CSR offsets of the links leaving each node (out_start[0] = 0,
+ *                          out_start[n_nodes] = n_links, non-decreasing)
+ *   out_link  [n_links]    link ids grouped by tail node
+ *   link_to   [n_links]    head node of each link
+ *   link_cost [n_links]    cost of each link, 1..1e6
+ *   dist_out  [n_nodes]    output
+ * stream: cudaStream_t to run on (NULL = legacy default stream).  The call
+ * synchronises that stream before returning.
+ *
+ * Working memory is one fixed device array inside the library (about 9 MB, enough
+ * for SIM_SSSP_STATIC_MAX_NODES nodes) that every GPU loading the library keeps
+ * until the process exits.  n_nodes above SIM_SSSP_STATIC_MAX_NODES, an origin
+ * out of range, or a malformed graph (offsets, link ids, head nodes or costs out
+ * of range; costs whose path sums could overflow) return SIM_EINVAL without
+ * running the search.  The first call on each device looks up the array's device
+ * address (with that device current) and fills its distance words once (a device
+ * synchronisation); make that first call before any stream capture.  All calls share the array: calls that overlap on the GPU (different
+ * streams or host threads at the same time) race and give wrong results, so
+ * serialise them.  Only a small per-call control block is cleared on each call;
+ * the distance and queue words are tagged with a per-call epoch and need no
+ * clearing.  Returns SIM_OK, SIM_EINVAL or SIM_ECUDA; sim_last_error is not set. */
+int sim_sssp_static(int32_t n_nodes, int32_t n_links, const int32_t* out_start, const int32_t* out_link,
+                    const int32_t* link_to, const int32_t* link_cost, int32_t origin, int32_t* dist_out,
+                    void* stream);
+
 /* Message of the last failed call on this handle (or of the last failed
  * sim_create when h is NULL). */
 const char* sim_last_error(const sim_handle* h);
