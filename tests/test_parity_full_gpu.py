@@ -1,0 +1,182 @@
+"""GPU parity at the workloads' full sizes, batched ensembles and edge cases.
+
+- the 20x20 signalised grid, all 20,000 trips, all 9,000 steps, checked every 1,500;
+- the calibration grid (3 link classes with their own IDM parameters), 1,800 steps;
+- a batched ensemble (sim_create_batch) against each scenario run alone by the oracle
+  and by the library;
+- one full-size metro step: 3,000,000 vehicles on the 550,000-link network, every bit;
+- full-size metro trip planning (225k trees, 3M routes) on the GPU against oracle
+  routes of trips from sampled origins;
+- empty and one-trip demands, error codes."""
+import numpy as np
+import pytest
+
+from paper_1807_01148_gb300 import scenarios as S
+
+from .parity import compare, diff_state, run_lockstep, setup_pair
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_1807_01148_gb300 import gbtraffic
+    return gbtraffic
+
+
+@pytest.fixture(scope="module")
+def O():
+    import oracle
+    return oracle
+
+
+def test_grid20_full_run_bitexact(G, O):
+    sc = S.grid()
+    g, o = setup_pair(sc, G.Sim, O.OracleSim)
+    run_lockstep(g, o, 9000, 1500)
+    c = g.counters()
+    assert c["arrived"] == sc["demand"]["n_trips"]
+
+
+def test_calib_grid_three_classes_bitexact(G, O):
+    sc = S.calib()
+    g, o = setup_pair(sc, G.Sim, O.OracleSim)
+    run_lockstep(g, o, 1800, 300)
+    # the perturbed target parameters are a second, different run of the same model
+    tg = dict(sc, params=sc["target_params"])
+    g2, o2 = setup_pair(tg, G.Sim, O.OracleSim)
+    run_lockstep(g2, o2, 1800, 900)
+    assert not np.array_equal(g.state()["x"], g2.state()["x"])
+
+
+def _small_ensemble():
+    sides = [5, 8, 6, 10]
+    out = []
+    rng = np.random.default_rng(3)
+    for k, n in enumerate(sides):
+        sc = S.small_grid(n=n, n_trips=150 * n, steps=700, seed=1000 + k, window_steps=500)
+        sc["params"] = S.default_params(1, v0=[float(rng.uniform(25, 33))], T=[float(rng.uniform(1, 2))],
+                                        a=[float(rng.uniform(0.8, 1.5))], b=[float(rng.uniform(1.2, 2.5))],
+                                        seed=5000 + k)
+        out.append(sc)
+    return out
+
+
+def test_batched_ensemble_equals_each_scenario(G, O):
+    scs = _small_ensemble()
+    b = G.Sim.batch(scs)
+    b.route()
+    singles = [setup_pair(sc, G.Sim, O.OracleSim) for sc in scs]
+    for step in range(7):
+        b.step(100)
+        for g, o in singles:
+            g.step(100)
+            o.step(100)
+        sb = b.state()
+        base = 0
+        link_base = 0
+        for (g, o), sc in zip(singles, scs):
+            n = sc["demand"]["n_trips"]
+            sl = {k: v[base:base + n].copy() for k, v in sb.items()}
+            act = sl["status"] == 1
+            sl["link"][act] -= link_base
+            so = o.state()
+            d = diff_state(sl, so)
+            assert not d, f"batch slice differs from the oracle after {(step + 1) * 100} steps: {d}"
+            d2 = diff_state(sl, g.state())
+            assert not d2, f"batch slice differs from the plain run: {d2}"
+            base += n
+            link_base += sc["network"]["n_links"]
+    cb = b.counters()
+    assert cb["veh_steps"] == sum(g.counters()["veh_steps"] for g, _ in singles)
+
+
+def test_metro_full_size_one_step_bitexact(G, O):
+    sc = S.metro()
+    off, links = S.random_walk_routes(sc, min_hops=10, max_hops=40)
+    sc["routes"] = dict(offsets=off, links=links)
+    sc["init_state"] = S.saturate(sc, off, links)
+    g, o = setup_pair(sc, G.Sim, O.OracleSim)
+    assert g.counters()["active"] > 2_900_000
+    for k in range(2):
+        g.step(1)
+        o.step(1)
+        compare(g, o, f"metro step {k + 1}", check_occ=(k == 1))
+
+
+def test_metro_full_size_routes_sampled(G, O):
+    sc = S.metro()
+    g = G.Sim(sc)
+    g.route()
+    off, links = g.routes()
+    dem = sc["demand"]
+    assert off[-1] == len(links) and (np.diff(off) >= 1).all()
+    lf, lt = sc["network"]["link_from"], sc["network"]["link_to"]
+    # every route is a connected path from the origin to the destination
+    first = links[off[:-1]]
+    last = links[off[1:] - 1]
+    assert (lf[first] == dem["origin"]).all() and (lt[last] == dem["dest"]).all()
+    inner = np.ones(len(links), bool)
+    inner[off[:-1]] = False
+    idx = np.flatnonzero(inner)
+    assert (lf[links[idx]] == lt[links[idx - 1]]).all()
+    # exact equality with the oracle for all trips of 60 sampled origins
+    rng = np.random.default_rng(17)
+    origins = rng.choice(np.unique(dem["origin"]), 60, replace=False)
+    keep = np.flatnonzero(np.isin(dem["origin"], origins))
+    sub = dict(sc, demand=S._demand(dem["origin"][keep], dem["dest"][keep], dem["depart_step"][keep]))
+    o = O.OracleSim(sub)
+    o.route()
+    oo, ol = o.routes()
+    for j, i in enumerate(keep):
+        assert np.array_equal(links[off[i]:off[i + 1]], ol[oo[j]:oo[j + 1]]), f"trip {i}"
+
+
+def test_empty_and_single_trip_demands(G, O):
+    base = S.small_grid(n=4, n_trips=1, steps=200)
+    g, o = setup_pair(base, G.Sim, O.OracleSim)
+    run_lockstep(g, o, 400, 50)
+    empty = dict(base, demand=S._demand(np.zeros(0), np.zeros(0), np.zeros(0)))
+    g = G.Sim(empty)
+    g.route()
+    g.step(10)
+    c = g.counters()
+    assert c["t"] == 10 and c["veh_steps"] == 0 and c["active"] == 0
+
+
+def test_error_codes(G):
+    sc = S.small_grid(n=4, n_trips=20)
+    g = G.Sim(sc)
+    with pytest.raises(G.SimError) as e:
+        g.step(1)                                     # no routes yet
+    assert e.value.code == G.SIM_ESTATE
+    bad = dict(sc, network=dict(sc["network"], link_lanes=np.zeros(sc["network"]["n_links"], np.uint8)))
+    with pytest.raises(G.SimError) as e:
+        G.Sim(bad)
+    assert e.value.code == G.SIM_EINVAL
+    bad = dict(sc, network=dict(sc["network"], link_to=np.full(sc["network"]["n_links"], 99, np.int32)))
+    with pytest.raises(G.SimError) as e:
+        G.Sim(bad)
+    assert e.value.code == G.SIM_EINVAL
+    # a one-way pair of nodes: node 1 cannot reach node 0
+    from .nets import make_net
+    net = make_net([(0.0, 0.0), (100.0, 0.0)], [(0, 1)], lanes=1)
+    un = dict(network=net, demand=S._demand(np.array([1]), np.array([0]), np.array([0])),
+              params=S.default_params(1))
+    g2 = G.Sim(un)
+    with pytest.raises(G.SimError) as e:
+        g2.route()
+    assert e.value.code == G.SIM_EUNREACHABLE
+    # origin == destination
+    same = dict(un, demand=S._demand(np.array([0]), np.array([0]), np.array([0])))
+    with pytest.raises(G.SimError) as e:
+        G.Sim(same).route()
+    assert e.value.code == G.SIM_EINVAL
+    # a state that puts a vehicle off its route
+    g.route()
+    st = dict(status=np.ones(20, np.uint8), link=np.full(20, 7, np.int32), lane=np.zeros(20, np.int32),
+              cursor=np.zeros(20, np.int32), x=np.zeros(20, np.float32), v=np.zeros(20, np.float32))
+    with pytest.raises(G.SimError) as e:
+        g.write_state(st)
+    assert e.value.code == G.SIM_EINVAL
+    g.step(5)                                         # the handle stays usable
