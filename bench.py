@@ -31,13 +31,12 @@ UNIT = "vehicle-steps/s"
 # Algorithmic bytes per active vehicle that each kernel must move (every array element
 # it has to read or write once; re-reads of neighbours and per-link records not counted).
 ALG_BYTES = {
-    "count": 8 + 8 + 4,          # link, lane; lane counter read+write; arrival index
-    "scatter": 20 + 4 + 16,      # link, lane, x, vid, arrival index; lane start; 4 scatter words
-    "rank": 16 + 4 + 28 + 28,    # scatter words; lane start; state gather from A; state write to B
-    "own": 24 + 4 + 9,           # x, v, vid, link, nxt, lane; lane end; a_own, xo, flags
-    "decide": 13,                # link, x, xo; intent (eligible vehicles read more, not counted)
-    "move": 28 + 9 + 28 + 1,     # sorted state; flags, intent, acceleration; next state; decision
-    "acquire": 12,               # link, lane, lane end
+    "scatter": 20 + 4 + 16,          # link, lane, x, vid, arrival index; lane start; 4 scatter words
+    "rank": 16 + 4 + 28 + 28,        # scatter words; lane start; state gather from A; state write to B
+    "own": 24 + 4 + 10,              # x, v, vid, link, nxt, lane; lane end; a_own, xo, flags, intent
+    "decide": 13,                    # link, x, xo; intent (eligible vehicles read more, not counted)
+    "move": 28 + 9 + 28 + 1 + 12,    # sorted state; flags, intent, acceleration; next state; decision;
+                                     # next-lane count (read+write) and arrival index
 }
 
 
@@ -270,8 +269,7 @@ def run_cuda(args):
     ms = ev0.elapsed_time(ev1)
     c1 = g.counters()
     veh_steps = c1["veh_steps"] - c0["veh_steps"]
-    kernels_per_step = 10 + (1 if int((m["network"]["node_control"] == 1).sum()) else 0) + \
-        (1 if int((snap["status"] == 0).sum()) else 0)
+    kernels_per_step = G.N_KERNELS - (0 if int((snap["status"] == 0).sum()) else 1)
     clk = clocks.stop()
 
     # -- per-kernel device times over the same K steps (events after every kernel)

@@ -166,11 +166,12 @@ int sim_route_size(sim_handle* h, int64_t* n_hops);
 int sim_read_routes(sim_handle* h, int32_t* offsets, int32_t* links);
 
 /* Advance the simulation by n_steps steps of dt.  All steps run on the device
- * without a host round trip.  Errors: SIM_ESTATE (no routes), SIM_EDEVICE. */
+ * without a host round trip.  Errors: SIM_ESTATE (no routes), SIM_EDEVICE,
+ * SIM_EINVAL when the horizon would pass 2^31 deciseconds of simulated time. */
 int sim_step(sim_handle* h, int32_t n_steps);
 
 /* Number of kernels in one step (see sim_kernel_name). */
-#define SIM_N_KERNELS 12
+#define SIM_N_KERNELS 10
 
 /* Advance n_steps like sim_step, but launch every kernel directly with a CUDA event
  * after each one, and add each kernel's device time (ms, including its launch gap)

@@ -14,6 +14,7 @@
 namespace gbt {
 void launch_step(const Dev& d, int grid, bool has_stop, cudaStream_t s);
 void launch_occupancy(const Dev& d, int grid, cudaStream_t s);
+void launch_count(const Dev& d, int grid, cudaStream_t s);
 int scan_blocks(int n_lanes);
 void launch_state_out(const Dev& d, int grid, cudaStream_t s, uint8_t* status, int32_t* link, int32_t* lane,
                       int32_t* cursor, float* x, float* v, int32_t* ins, int32_t* arr, int8_t* dec);
@@ -350,6 +351,7 @@ int create_from_flat(Flat& F, sim_handle** out) {
     TRY(dalloc(h, &d.at, nt));
     TRY(dalloc(h, &d.intent, nt));
     TRY(dalloc(h, &d.flags, nt));
+    TRY(dalloc(h, &d.elig, nt));
     TRY(dalloc(h, &d.cnt, (size_t)nlan));
     TRY(dalloc(h, &d.lane_start, (size_t)nlan + 1));
     TRY(dalloc(h, &d.bsum, (size_t)scan_blocks(nlan) + 1));
@@ -449,6 +451,16 @@ int reset_dynamic(sim_handle* h) {
   CK(cudaMemsetAsync(d.best, 0xFF, (size_t)h->n_lanes * 8, h->stream));
   CK(cudaMemsetAsync(d.cnt, 0, (size_t)h->n_lanes * 4, h->stream));
   CK(cudaMemsetAsync(d.ctl, 0, sizeof(Ctl), h->stream));
+  return SIM_OK;
+}
+
+// Step times stay below 2^31 / dt_ds so that the device's 32-bit phase arithmetic is exact.
+int check_horizon(sim_handle* h, int n_steps) {
+  Ctl c;
+  CK(cudaMemcpyAsync(&c, h->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const long long limit = 2147483647LL / (h->d.dt_ds + 1);
+  if (c.t + (long long)n_steps > limit) return fail(h, SIM_EINVAL, "simulation horizon beyond 2^31 deciseconds");
   return SIM_OK;
 }
 
@@ -742,6 +754,7 @@ int sim_step(sim_handle* h, int32_t n_steps) {
   if (!h || n_steps < 0) return SIM_EINVAL;
   if (!h->routed) return fail(h, SIM_ESTATE, "sim_step before sim_route / sim_set_routes");
   if (n_steps == 0) return SIM_OK;
+  if (int rc = check_horizon(h, n_steps)) return rc;
   if (h->graph_dirty) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->graph) cudaGraphDestroy(h->graph);
@@ -760,6 +773,7 @@ int sim_step(sim_handle* h, int32_t n_steps) {
 int sim_step_timed(sim_handle* h, int32_t n_steps, float* kernel_ms) {
   if (!h || n_steps < 0 || !kernel_ms) return SIM_EINVAL;
   if (!h->routed) return fail(h, SIM_ESTATE, "sim_step_timed before sim_route / sim_set_routes");
+  if (int rc = check_horizon(h, n_steps)) return rc;
   CK(launch_steps_timed(h->d, h->grid, h->has_stop, h->stream, n_steps, kernel_ms));
   return check_device(h);
 }
@@ -849,7 +863,10 @@ int sim_write_state(sim_handle* h, const uint8_t* status, const int32_t* link, c
     release();
     return rc;
   }
-  if (nt) launch_state_in(h->d, h->grid, h->stream, ds, dl, dn, dc, dx, dv);
+  if (nt) {
+    launch_state_in(h->d, h->grid, h->stream, ds, dl, dn, dc, dx, dv);
+    launch_count(h->d, h->grid, h->stream);
+  }
   e = cudaStreamSynchronize(h->stream);
   release();
   if (e != cudaSuccess) return cuda_fail(h, e, "write_state");

@@ -60,7 +60,7 @@ struct Ctl {
   int n_ins, n_arr;
   int err, err_info;
   int active_last;
-  int pad0;
+  int n_elig;      // vehicles eligible for a lane change this step
   unsigned long long veh_steps, departed, arrived;
   unsigned long long route_cursor;  // bump allocator of the route store
 };
@@ -104,6 +104,7 @@ struct Dev {
   float* at;
   int8_t* intent;
   uint8_t* flags;
+  int32_t* elig;              // sorted positions of lane-change candidates
   // per node
   int32_t* holder;
   unsigned long long* acq;
@@ -152,8 +153,8 @@ struct RouteDev {
 void launch_route(const RouteDev& R, int n_cta, cudaStream_t s);
 
 // kernels of one step, in launch order
-enum { kKCount, kKScanSum, kKScanTop, kKScanFin, kKScatter, kKRank, kKAcquire, kKOwn, kKDecide, kKMove, kKInsert,
-       kKFinish, kNumKernels };
+enum { kKScanSum, kKScanTop, kKScanFin, kKScatter, kKRank, kKOwn, kKDecide, kKMove, kKInsert, kKFinish,
+       kNumKernels };
 extern const char* const kKernelNames[kNumKernels];
 
 constexpr uint8_t kFlagFront = 1, kFlagHolder = 2, kFlagCand = 4;
@@ -234,25 +235,27 @@ __device__ __forceinline__ int move_mask(const Dev& d, int e, int lanes, int e2)
   return all;
 }
 
-__device__ __forceinline__ int rr_rank(const LinkRec& L, long long t) {
-  int n = L.n_in;
-  return (int)((L.in_index + n - (int)(t % n)) % n);
+// Step time is kept below 2^31 / dt_ds (checked by sim_step), so the phase and
+// round-robin arithmetic is exact in 32 bits.
+__device__ __forceinline__ int rr_rank(const LinkRec& L, int t) {
+  const int n = L.n_in;
+  return (L.in_index + n - t % n) % n;
 }
 
-__device__ __forceinline__ bool signal_green(const LinkRec& L, long long t, int dt_ds) {
-  long long p = (t * (long long)dt_ds - (long long)L.sig_off) % (long long)L.sig_cyc;
+__device__ __forceinline__ bool signal_green(const LinkRec& L, int tds) {
+  int p = (tds - L.sig_off) % (int)L.sig_cyc;
   if (p < 0) p += L.sig_cyc;
-  bool ns = p < (long long)L.sig_grn;
+  const bool ns = p < (int)L.sig_grn;
   return L.ew ? !ns : ns;
 }
 
 // Epoch-tagged 64-bit priority key: entries of step t compare below all entries of
 // earlier steps, so per-step minima need no reset.  Lower 32 bits: (rank, lane).
-__device__ __forceinline__ unsigned long long epoch_key(long long t, int rr, int lane) {
+__device__ __forceinline__ unsigned long long epoch_key(int t, int rr, int lane) {
   unsigned hi = 0xFFFFFFFEu - (unsigned)t;
   return ((unsigned long long)hi << 32) | (unsigned long long)((rr << 8) | lane);
 }
-__device__ __forceinline__ bool epoch_current(unsigned long long k, long long t) {
+__device__ __forceinline__ bool epoch_current(unsigned long long k, int t) {
   return (unsigned)(k >> 32) == 0xFFFFFFFEu - (unsigned)t;
 }
 

@@ -133,52 +133,43 @@ __global__ void k_scatter(Dev d) {
 }
 
 // Rank of each vehicle inside its lane segment by (x, vid); the vehicle's state
-// moves from its slot in A to position lane_start + rank in B.
+// moves from its slot in A to position lane_start + rank in B.  The vehicle that
+// lands last in its segment is the lane's front: if its link ends at a free stop-
+// controlled node, it bids for the node here (Sec. 6.3.2 stop signs, one vehicle at
+// a time): the bid with the smallest (round-robin rank of its link, lane) acquires it.
 __global__ void k_rank(Dev d) {
   const int nB = d.ctl->nB;
+  const int t = (int)d.ctl->t;
   GRID_STRIDE(p, nB) {
-    int g = d.tg[p];
-    int s0 = d.lane_start[g], s1 = d.lane_start[g + 1];
-    float xp = d.tx[p];
-    int vp = d.tvid[p];
+    const int g = d.tg[p];
+    const int s0 = d.lane_start[g], s1 = d.lane_start[g + 1];
+    const float xp = d.tx[p];
+    const int vp = d.tvid[p];
     int rank = 0;
     for (int q = s0; q < s1; q++) {
-      float xq = d.tx[q];
+      const float xq = d.tx[q];
       rank += (xq < xp || (xq == xp && d.tvid[q] < vp)) ? 1 : 0;
     }
-    int dst = s0 + rank;
-    int src = d.tsrc[p];
-    d.B.x[dst] = d.A.x[src];
+    const int dst = s0 + rank;
+    const int src = d.tsrc[p];
+    const int e = d.A.link[src], nxt = d.A.nxt[src], lane = d.A.lane[src];
+    d.B.x[dst] = xp;
     d.B.v[dst] = d.A.v[src];
     d.B.vid[dst] = vp;
-    d.B.link[dst] = d.A.link[src];
-    d.B.nxt[dst] = d.A.nxt[src];
+    d.B.link[dst] = e;
+    d.B.nxt[dst] = nxt;
     d.B.cur[dst] = d.A.cur[src];
-    d.B.lane[dst] = d.A.lane[src];
-  }
-}
-
-// ------------------------------------------------------------------ stop signs
-// A free stop-controlled node is acquired by the front vehicle (within
-// stop_acquire_m of the stop line, route continuing) of the incoming lane with the
-// smallest (round-robin rank of its link, lane).
-__global__ void k_acquire(Dev d) {
-  const int nB = d.ctl->nB;
-  const long long t = d.ctl->t;
-  GRID_STRIDE(p, nB) {
-    int e = d.B.link[p];
-    const LinkRec L = d.links[e];
-    if (L.ctrl != kCtrlStop) continue;
-    int lane = d.B.lane[p];
-    if (p + 1 != d.lane_start[L.lane_base + lane + 1]) continue;
-    if (d.holder[L.to] != -1 || d.B.nxt[p] < 0) continue;
-    if (!((L.len - d.B.x[p]) <= d.stop_acq)) continue;
-    atomicMin(&d.acq[L.to], epoch_key(t, rr_rank(L, t), lane));
+    d.B.lane[dst] = lane;
+    if (dst + 1 == s1 && nxt >= 0) {
+      const LinkRec& L = d.links[e];
+      if (L.ctrl == kCtrlStop && d.holder[L.to] == -1 && (L.len - xp) <= d.stop_acq)
+        atomicMin(&d.acq[L.to], epoch_key(t, rr_rank(L, t), lane));
+    }
   }
 }
 
 // ------------------------------------------------------------------ neighbours / IDM
-__device__ __forceinline__ bool is_holder(const Dev& d, const LinkRec& L, long long t, int vid, int lane,
+__device__ __forceinline__ bool is_holder(const Dev& d, const LinkRec& L, int t, int vid, int lane,
                                           bool front) {
   if (L.ctrl != kCtrlStop) return false;
   int h = d.holder[L.to];
@@ -186,8 +177,8 @@ __device__ __forceinline__ bool is_holder(const Dev& d, const LinkRec& L, long l
   return h == -1 && front && d.acq[L.to] == epoch_key(t, rr_rank(L, t), lane);
 }
 
-__device__ __forceinline__ bool line_closed(const Dev& d, const LinkRec& L, long long t, bool holder) {
-  if (L.ctrl == kCtrlSignal) return !signal_green(L, t, d.dt_ds);
+__device__ __forceinline__ bool line_closed(const Dev& d, const LinkRec& L, int t, bool holder) {
+  if (L.ctrl == kCtrlSignal) return !signal_green(L, t * d.dt_ds);
   if (L.ctrl == kCtrlStop) return !holder;
   return false;
 }
@@ -218,7 +209,7 @@ __device__ __forceinline__ float acc_front(const Dev& d, const LinkRec& L, const
 
 __global__ void k_own(Dev d) {
   const int nB = d.ctl->nB;
-  const long long t = d.ctl->t;
+  const int t = (int)d.ctl->t;
   GRID_STRIDE(p, nB) {
     const int e = d.B.link[p];
     const LinkRec L = d.links[e];
@@ -239,6 +230,19 @@ __global__ void k_own(Dev d) {
     ballistic(x, v, a, d.dt, d.hdt2, xo, vo);
     d.a_own[p] = a;
     d.xo[p] = xo;
+    d.intent[p] = 0;
+    // lane-change candidates (multi-lane link, away from both link ends) go to a
+    // compact list so that the decision kernel runs full warps
+    const bool elig = L.lanes >= 2 && x >= d.zone && xo < L.len - d.zone;
+    const unsigned act = __activemask();
+    const unsigned em = __ballot_sync(act, elig);
+    if (em) {
+      const int ln = threadIdx.x & 31, lead = __ffs(em) - 1;
+      int base = 0;
+      if (ln == lead) base = atomicAdd(&d.ctl->n_elig, __popc(em));
+      base = __shfl_sync(act, base, lead);
+      if (elig) d.elig[base + __popc(em & ((1u << ln) - 1u))] = p;
+    }
     uint8_t fl = (front ? kFlagFront : 0) | (hold ? kFlagHolder : 0);
     // admission candidate: front, route continues, stop line open, move reaches the end
     if (front && nxt >= 0 && !line_closed(d, L, t, hold) && xo >= L.len) {
@@ -278,16 +282,14 @@ __device__ __forceinline__ int upper_pos(const Dev& d, int s0, int s1, float x, 
 // Helbing 2007) for discretionary changes, mandatory changes toward the lanes of
 // the next movement once within the drawn switch distance, and gap acceptance =
 // no overlap and both the changer's and the new follower's accelerations >= -b_safe.
-__global__ void k_decide(Dev d) {
-  const int nB = d.ctl->nB;
-  const long long t = d.ctl->t;
-  GRID_STRIDE(p, nB) {
-    d.intent[p] = 0;
+__global__ void __launch_bounds__(256, 4) k_decide(Dev d) {
+  const int ne = d.ctl->n_elig;
+  const int t = (int)d.ctl->t;
+  GRID_STRIDE(i, ne) {
+    const int p = d.elig[i];
     const int e = d.B.link[p];
     const LinkRec L = d.links[e];
-    if (L.lanes < 2) continue;
     const float x = d.B.x[p];
-    if (!(x >= d.zone && d.xo[p] < L.len - d.zone)) continue;
     const ClassPar P = d.cls[L.cls];
     const float v = d.B.v[p];
     const int vid = d.B.vid[p], lane = d.B.lane[p], nxt = d.B.nxt[p], cur = d.B.cur[p];
@@ -377,7 +379,7 @@ __global__ void k_decide(Dev d) {
 // ------------------------------------------------------------------ move
 __global__ void k_move(Dev d) {
   const int nB = d.ctl->nB;
-  const long long t = d.ctl->t;
+  const int t = (int)d.ctl->t;
   GRID_STRIDE(p, nB) {
     const int e = d.B.link[p];
     const LinkRec L = d.links[e];
@@ -439,6 +441,9 @@ __global__ void k_move(Dev d) {
       }
     }
     if (hold) d.holder[L.to] = crossed ? -1 : vid;
+    // lane count for the next occupancy rebuild
+    const int gb = crossed ? d.links[nlink].lane_base : L.lane_base;
+    d.aidx[p] = atomicAdd(&d.cnt[gb + nl], 1);
     d.A.x[p] = nx;
     d.A.v[p] = nv;
     d.A.vid[p] = vid;
@@ -455,7 +460,7 @@ __global__ void k_move(Dev d) {
 // vehicle from upstream in this step, if that space is at least s0 + vehicle length.
 __global__ void k_insert(Dev d) {
   const int nq = d.n_qlinks;
-  const long long t = d.ctl->t;
+  const int t = (int)d.ctl->t;
   const int nB = d.ctl->nB;
   GRID_STRIDE(i, nq) {
     const int e = d.qlinks[i];
@@ -492,6 +497,7 @@ __global__ void k_insert(Dev d) {
     d.A.nxt[slot] = e2;
     d.A.cur[slot] = 0;
     d.A.lane[slot] = bl;
+    d.aidx[slot] = atomicAdd(&d.cnt[L.lane_base + bl], 1);
     d.status[h] = kActive;
     d.ins_step[h] = (int32_t)t;
     d.q_head[e] = hd + 1;
@@ -507,6 +513,7 @@ __global__ void k_finish(Dev d) {
   c->nA = c->nB + c->n_ins;
   c->n_ins = 0;
   c->n_arr = 0;
+  c->n_elig = 0;
   c->t += 1;
 }
 
@@ -514,17 +521,23 @@ __global__ void k_finish(Dev d) {
 int scan_blocks(int n_lanes) { return (n_lanes + kScanChunk - 1) / kScanChunk; }
 
 void launch_kernel(int k, const Dev& d, int grid, cudaStream_t s);
+void launch_count(const Dev& d, int grid, cudaStream_t s);
 
+// Occupancy of the current state without stepping: rebuild B from the lane counts,
+// then count buffer A again so that the next step finds its counts.
 void launch_occupancy(const Dev& d, int grid, cudaStream_t s) {
-  for (int k = kKCount; k <= kKRank; k++) launch_kernel(k, d, grid, s);
+  for (int k = kKScanSum; k <= kKRank; k++) launch_kernel(k, d, grid, s);
+  launch_count(d, grid, s);
 }
 
-// Kernels of one step, in launch order (names reported by the timed step).
-const char* const kKernelNames[kNumKernels] = {"count", "scan_sum", "scan_top", "scan_fin", "scatter", "rank",
-                                               "acquire", "own", "decide", "move", "insert", "finish"};
+// Kernels of one step, in launch order (names reported by the timed step).  The
+// lane counts the scan starts from are made by the previous step's move and insert
+// kernels (or by k_count after a state is loaded).
+const char* const kKernelNames[kNumKernels] = {"scan_sum", "scan_top", "scan_fin", "scatter", "rank",
+                                               "own", "decide", "move", "insert", "finish"};
 
 bool kernel_enabled(int k, const Dev& d, bool has_stop) {
-  if (k == kKAcquire) return has_stop;
+  (void)has_stop;
   if (k == kKInsert) return d.n_qlinks > 0;
   return true;
 }
@@ -532,13 +545,11 @@ bool kernel_enabled(int k, const Dev& d, bool has_stop) {
 void launch_kernel(int k, const Dev& d, int grid, cudaStream_t s) {
   const int nb = scan_blocks(d.n_lanes);
   switch (k) {
-    case kKCount: k_count<<<grid, 256, 0, s>>>(d); break;
     case kKScanSum: k_scan_sum<<<nb, kScanThreads, 0, s>>>(d); break;
     case kKScanTop: k_scan_top<<<1, 1024, 0, s>>>(d, nb); break;
     case kKScanFin: k_scan_fin<<<nb, kScanThreads, 0, s>>>(d); break;
     case kKScatter: k_scatter<<<grid, 256, 0, s>>>(d); break;
     case kKRank: k_rank<<<grid, 256, 0, s>>>(d); break;
-    case kKAcquire: k_acquire<<<grid, 256, 0, s>>>(d); break;
     case kKOwn: k_own<<<grid, 256, 0, s>>>(d); break;
     case kKDecide: k_decide<<<grid, 256, 0, s>>>(d); break;
     case kKMove: k_move<<<grid, 256, 0, s>>>(d); break;
@@ -551,6 +562,9 @@ void launch_kernel(int k, const Dev& d, int grid, cudaStream_t s) {
     default: break;
   }
 }
+
+// lane counts of buffer A (after a state is loaded, or to restore them)
+void launch_count(const Dev& d, int grid, cudaStream_t s) { k_count<<<grid, 256, 0, s>>>(d); }
 
 void launch_step(const Dev& d, int grid, bool has_stop, cudaStream_t s) {
   for (int k = 0; k < kNumKernels; k++)

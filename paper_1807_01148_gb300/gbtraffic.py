@@ -20,7 +20,7 @@ ERR_NAMES = {0: "SIM_OK", -1: "SIM_EINVAL", -2: "SIM_ENOMEM", -3: "SIM_ECUDA", -
 F_STATUS, F_LINK, F_LANE, F_CURSOR, F_X, F_V, F_INSERT, F_ARRIVE, F_LANECHANGE = (1 << k for k in range(9))
 F_ALL = (1 << 9) - 1
 
-N_KERNELS = 12
+N_KERNELS = 10
 EXPORTS = ["sim_create", "sim_create_batch", "sim_set_stream", "sim_route", "sim_set_routes", "sim_route_size",
            "sim_read_routes", "sim_step", "sim_step_timed", "sim_kernel_name", "sim_read_state", "sim_write_state", "sim_occupancy", "sim_n_lanes",
            "sim_counters", "sim_last_error", "sim_destroy"]
