@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 64-scenario batched-ensemble comparison")
+    ap.add_argument("--batched-steps", type=int, default=7200)
     ap.add_argument("--workload", default="metro", choices=["metro", "metro-walk"],
                     help="metro: GPU-planned shortest-path routes; metro-walk: the first --trips trips on "
                          "random-walk routes (no trip planning; smaller cases for profiling)")
@@ -206,6 +209,47 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------- batched ensemble
+def measure_batched(G, S, torch, steps):
+    """64 grid scenarios of uneven size (side 10..40, 5k..80k trips, per-scenario IDM
+    parameters) advanced together by one handle (sim_create_batch) against the same 64
+    scenarios run one after another, each in its own handle; device time of the stepping
+    only (trip planning excluded on both sides)."""
+    scs = S.ensemble(steps=steps)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b = G.Sim.batch(scs)
+    b.set_stream(stream.cuda_stream)
+    b.route()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tb = e0.elapsed_time(e1) / 1e3
+    vb = b.counters()["veh_steps"]
+    b.close()
+    ts, vs = 0.0, 0
+    for sc in scs:
+        g = G.Sim(sc)
+        g.set_stream(stream.cuda_stream)
+        g.route()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        g.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts += e0.elapsed_time(e1) / 1e3
+        vs += g.counters()["veh_steps"]
+        g.close()
+    return {"scenarios": len(scs), "steps": steps, "trips": int(sum(s["demand"]["n_trips"] for s in scs)),
+            "batched": {"value": vb / tb, "seconds": tb, "veh_steps": vb},
+            "sequential": {"value": vs / ts, "seconds": ts, "veh_steps": vs},
+            "ratio": (vb / tb) / (vs / ts), "unit": UNIT,
+            "note": "one handle over the disjoint union (one launch sequence per step for all scenarios) vs "
+                    "64 handles stepped one after another; identical vehicle-steps"}
+
+
 # ---------------------------------------------------------------------------- cuda arm
 def run_cuda(args):
     import torch
@@ -325,6 +369,9 @@ def run_cuda(args):
         v = torch.tensor([float(veh_steps)], device="cuda")
         dist.all_reduce(v, op=dist.ReduceOp.SUM)
         secs, tot_vs = float(t.item()), float(v.item())
+    batched = None
+    if not args.no_batched:
+        batched = measure_batched(G, S, torch, args.batched_steps)
     if rank != 0:
         return
     cpu = None
@@ -355,6 +402,7 @@ def run_cuda(args):
         "per_kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
         "routing": {"seconds": route_s, "mode": "gpu sim_route" if args.workload == "metro" else "set_routes", "origins_trees": int(len(np.unique(m["demand"]["origin"]))),
                     "trips": m["demand"]["n_trips"], "hops": int(off[-1])},
+        "batched_ensemble": batched,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk,
