@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 64-scenario batched-ensemble comparison")
     ap.add_argument("--batched-steps", type=int, default=7200)
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward time ratio")
     ap.add_argument("--workload", default="metro", choices=["metro", "metro-walk"],
                     help="metro: GPU-planned shortest-path routes; metro-walk: the first --trips trips on "
                          "random-walk routes (no trip planning; smaller cases for profiling)")
@@ -250,6 +251,48 @@ def measure_batched(G, S, torch, steps):
                     "64 handles stepped one after another; identical vehicle-steps"}
 
 
+# ---------------------------------------------------------------------------- adjoint
+def measure_adjoint(G, S, torch, reps=3):
+    """Calibration workload: the 20x20 grid with 20,000 trips and three link classes,
+    1800 steps, loss = squared route-progress error every 20 steps against trajectories
+    of perturbed parameters.  Ratio = wall time of sim_adjoint (forward with checkpoints
+    every 64 steps, per-segment taped replay, binary64 reverse sweep) / wall time of the
+    plain forward sim_step(1800); best of `reps` each."""
+    sc = S.calib()
+    n = sc["demand"]["n_trips"]
+    steps, every = sc["steps"], sc["obs_every"]
+    keys = ("v0", "T", "a", "b", "s0")
+    g = G.Sim(sc)
+    g.route()
+    tp = sc["target_params"]
+    g.set_class_params(*[tp[k] for k in keys])
+    target = g.observe(steps, every)
+    p = sc["params"]
+    g.set_class_params(*[p[k] for k in keys])
+    start = dict(status=np.zeros(n, np.uint8), link=np.zeros(n, np.int32), lane=np.zeros(n, np.int32),
+                 cursor=np.zeros(n, np.int32), x=np.zeros(n, np.float32), v=np.zeros(n, np.float32))
+    tf, ta = [], []
+    grad = loss = None
+    for _ in range(reps):
+        g.write_state(start)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.step(steps)
+        torch.cuda.synchronize()
+        tf.append(time.perf_counter() - t0)
+        g.write_state(start)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        grad, loss = g.adjoint(steps, every, target, 3)
+        torch.cuda.synchronize()
+        ta.append(time.perf_counter() - t0)
+    g.close()
+    return {"workload": "20x20 grid, 20000 trips, 3 link classes x (v0, T, a, b, s0), 1800 steps, "
+                        "observations every 20 steps, checkpoints every 64",
+            "forward_s": min(tf), "adjoint_s": min(ta), "ratio": min(ta) / min(tf), "loss": loss,
+            "grad_norm": float(np.linalg.norm(grad))}
+
+
 # ---------------------------------------------------------------------------- cuda arm
 def run_cuda(args):
     import torch
@@ -369,6 +412,9 @@ def run_cuda(args):
         v = torch.tensor([float(veh_steps)], device="cuda")
         dist.all_reduce(v, op=dist.ReduceOp.SUM)
         secs, tot_vs = float(t.item()), float(v.item())
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = measure_adjoint(G, S, torch)
     batched = None
     if not args.no_batched:
         batched = measure_batched(G, S, torch, args.batched_steps)
@@ -403,6 +449,7 @@ def run_cuda(args):
         "routing": {"seconds": route_s, "mode": "gpu sim_route" if args.workload == "metro" else "set_routes", "origins_trees": int(len(np.unique(m["demand"]["origin"]))),
                     "trips": m["demand"]["n_trips"], "hops": int(off[-1])},
         "batched_ensemble": batched,
+        "adjoint_forward": adjoint,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk,

@@ -202,6 +202,38 @@ int sim_n_lanes(sim_handle* h, int64_t* n_lanes);
 
 int sim_counters(sim_handle* h, sim_counters_t* out);
 
+/* Replace the IDM parameters of every class (arrays [n_class], host): the next steps
+ * use them.  Classes created with v0 <= 0 (desired speed = link speed limit) must
+ * keep v0 <= 0 and the others v0 > 0.  Errors: SIM_EINVAL. */
+int sim_set_class_params(sim_handle* h, const float* v0, const float* T, const float* a, const float* b,
+                         const float* s0);
+
+/* Advance n_steps and record the route progress of every trip after every obs_every
+ * steps: progress[k * n_trips + v] (host, double, metres) = length of the completed
+ * links of trip v's route plus its position, 0 before departure, the whole route
+ * after arrival; k = 0 .. n_steps / obs_every - 1. */
+int sim_observe(sim_handle* h, int32_t n_steps, int32_t obs_every, double* progress);
+
+/* Calibration loss of a trajectory (not in the paper). */
+typedef struct {
+  int32_t n_steps;            /* horizon, a multiple of obs_every */
+  int32_t obs_every;          /* observation period, steps */
+  int32_t checkpoint_every;   /* steps between stored states (<= 0: 64) */
+  const double* target;       /* host [n_steps / obs_every][n_trips] target progress, m */
+} sim_loss_spec;
+
+/* Loss L = sum_k sum_v (p_v(t_k) - target[k][v])^2 over the n_steps from the current
+ * state (t_k = (k+1) * obs_every steps later; p as in sim_observe) and its gradient
+ * with respect to the IDM parameters of every class, grad_out[5 * c + {0..4}] =
+ * dL/d{v0, T, a, b, s0} of class c (host, double; the v0 entry is 0 for classes that
+ * use the link speed limit).  The discrete decisions of the run (leaders, lane
+ * changes, admissions, clamps at the stop line, stops within a step, departures,
+ * arrivals) are held fixed.  The forward pass stores the state every
+ * checkpoint_every steps; the reverse pass replays each segment with a tape of the
+ * vehicle-steps and sweeps it backwards in binary64.  On return the state is the one
+ * after the n_steps.  Errors: SIM_EINVAL, SIM_ESTATE, SIM_ENOMEM. */
+int sim_adjoint(sim_handle* h, const sim_loss_spec* spec, double* grad_out, double* loss_out);
+
 /* Largest graph sim_sssp_static accepts (nodes). */
 #define SIM_SSSP_STATIC_MAX_NODES 262144
 

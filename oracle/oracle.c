@@ -81,7 +81,31 @@ struct orc_sim {
   /* departure queues: trips by first link, ordered (depart_step, trip id) */
   int32_t *q_start, *q_items, *q_head;
   int64_t t, departed, arrived, veh_steps, active_last;
+  /* adjoint tape: per step, one record per vehicle advanced (see orc_adjoint) */
+  int recording;
+  struct orc_rec* rec;
+  int64_t rec_n, rec_cap;
+  int64_t* rec_step;        /* [steps + 1] start of each step's records */
+  int rec_steps, rec_step_cap;
+  /* start state of the taped run (for the replay) */
+  uint8_t* st0;
+  int32_t* cur0;
+  float *x0, *v0s;
+  double* tgt;              /* targets of the taped run */
+  int tgt_nobs, tgt_every;
 };
+
+/* One taped vehicle-step: the form of Eq. 7 used (kind/lead/s/vl, see acc_form
+ * below), the speed and acceleration, the link, and how the move ended. */
+#define BR_NORMAL 0
+#define BR_STOP 1
+#define BR_CLAMP 2
+#define BR_ARRIVE 3
+typedef struct orc_rec {
+  int32_t vid, lead, link;
+  float s, v, vl, a;
+  uint8_t kind, branch, crossed;
+} orc_rec;
 
 /* ------------------------------------------------------------------ helpers */
 static void* xcalloc(size_t n, size_t sz) { return calloc(n ? n : 1, sz ? sz : 1); }
@@ -351,7 +375,7 @@ void orc_destroy(orc_sim* S) {
                   S->v0l, S->lane_base, S->in_start, S->in_list, S->in_index, S->n_in, S->pv0, S->pT, S->pa,
                   S->pb, S->ps0, S->psab, S->orig, S->dest, S->dep, S->roff, S->rl, S->st, S->link, S->lane,
                   S->cur, S->x, S->v, S->ins_step, S->arr_step, S->dec, S->holder, S->q_start, S->q_items,
-                  S->q_head};
+                  S->q_head, S->rec, S->rec_step, S->st0, S->cur0, S->x0, S->v0s, S->tgt};
   for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); i++) free(ptrs[i]);
   free(S);
 }
@@ -615,28 +639,48 @@ static float acc_gap(const orc_sim* S, int e, float s, float v, float vl) {
   return idm_acc(S->pa[c], S->psab[c], S->pT[c], S->ps0[c], S->v0l[e], S->s_min, s, v, vl, 1);
 }
 
+/* Which form of Eq. 7 produced an acceleration (for the adjoint's tape): kind
+ * 1 = leader on the same link, 4 = leader across the link end, 2 = free road,
+ * 3 = closed stop line; lead = leader trip id, s and vl = the gap and leader speed
+ * that entered Eq. 7. */
+#define FORM_NONE 0
+#define FORM_LEAD 1
+#define FORM_FREE 2
+#define FORM_STOP 3
+#define FORM_NEXT 4
+typedef struct { int kind, lead; float s, vl; } accform;
+
+static void set_form(accform* f, int kind, int lead, float s, float vl) {
+  if (f) { f->kind = kind; f->lead = lead; f->s = s; f->vl = vl; }
+}
+
 /* Acceleration of vehicle j at (x, v) on link e, lane l when nothing is ahead of it
  * on e: the leader is the rearmost vehicle of the mapped lane of j's next link
  * (gap counted across the link end), and a closed stop line acts as a standing
  * obstacle; the smaller acceleration applies.  On the last link of a route the
  * road ahead is free. */
-static float acc_front(const orc_sim* S, const occ_t* O, int j, int e, int l, float x, float v) {
+static float acc_front(const orc_sim* S, const occ_t* O, int j, int e, int l, float x, float v, accform* f) {
   int nx = next_link(S, j, S->cur[j]);
-  if (nx < 0) return acc_free(S, e, v);
+  if (nx < 0) { set_form(f, FORM_FREE, -1, 0.0f, 0.0f); return acc_free(S, e, v); }
   int m = l < S->lanes[nx] - 1 ? l : S->lanes[nx] - 1;
   int g = lane_id(S, nx, m);
   float a1;
+  accform f1;
   if (O->start[g] < O->start[g + 1] && O->vids[O->start[g]] != j) {
     int r = O->vids[O->start[g]];
     float s = ((S->len[e] - x) + S->x[r]) - S->len_v;
     a1 = acc_gap(S, e, s, v, S->v[r]);
+    f1 = (accform){FORM_NEXT, r, s, S->v[r]};
   } else {
     a1 = acc_free(S, e, v);
+    f1 = (accform){FORM_FREE, -1, 0.0f, 0.0f};
   }
   if (stopline_closed(S, j, e)) {
-    float a2 = acc_gap(S, e, S->len[e] - x, v, 0.0f);
-    return fminf(a1, a2);
+    float s2 = S->len[e] - x;
+    float a2 = acc_gap(S, e, s2, v, 0.0f);
+    if (a2 < a1) { set_form(f, FORM_STOP, -1, s2, 0.0f); return a2; }
   }
+  if (f) *f = f1;
   return a1;
 }
 
@@ -657,11 +701,34 @@ static int key_less(const orc_sim* S, int a, int b) {   /* (x, vid) order */
 }
 
 /* Own-lane acceleration (Eq. 7 with the own-lane leader, else acc_front). */
-static float acc_own(const orc_sim* S, const occ_t* O, int i) {
+static float acc_own(const orc_sim* S, const occ_t* O, int i, accform* f) {
   int L = leader_of(S, O, i);
   int e = S->link[i];
-  if (L >= 0) return acc_gap(S, e, (S->x[L] - S->x[i]) - S->len_v, S->v[i], S->v[L]);
-  return acc_front(S, O, i, e, S->lane[i], S->x[i], S->v[i]);
+  if (L >= 0) {
+    float s = (S->x[L] - S->x[i]) - S->len_v;
+    set_form(f, FORM_LEAD, L, s, S->v[L]);
+    return acc_gap(S, e, s, S->v[i], S->v[L]);
+  }
+  return acc_front(S, O, i, e, S->lane[i], S->x[i], S->v[i], f);
+}
+
+static orc_rec* rec_push(orc_sim* S) {
+  if (S->rec_n == S->rec_cap) {
+    S->rec_cap = S->rec_cap ? 2 * S->rec_cap : 65536;
+    S->rec = (orc_rec*)realloc(S->rec, (size_t)S->rec_cap * sizeof(orc_rec));
+  }
+  orc_rec* r = &S->rec[S->rec_n++];
+  memset(r, 0, sizeof(*r));
+  return r;
+}
+
+static void rec_begin_step(orc_sim* S) {
+  if (S->rec_steps + 2 > S->rec_step_cap) {
+    S->rec_step_cap = S->rec_step_cap ? 2 * S->rec_step_cap : 1024;
+    S->rec_step = (int64_t*)realloc(S->rec_step, (size_t)S->rec_step_cap * sizeof(int64_t));
+  }
+  S->rec_step[S->rec_steps++] = S->rec_n;
+  S->rec_step[S->rec_steps] = S->rec_n;
 }
 
 int orc_step(orc_sim* S, int32_t n_steps) {
@@ -678,9 +745,12 @@ int orc_step(orc_sim* S, int32_t n_steps) {
   uint8_t* nst = (uint8_t*)xcalloc(nt, 1);
   int32_t *nlink = (int32_t*)xcalloc(nt, 4), *nlane = (int32_t*)xcalloc(nt, 4), *ncur = (int32_t*)xcalloc(nt, 4);
   float *nx_ = (float*)xcalloc(nt, 4), *nv = (float*)xcalloc(nt, 4);
+  accform* own_f = (accform*)xcalloc(nt, sizeof(accform));
+  accform* tgt_f = (accform*)xcalloc(nt, sizeof(accform));
 
   for (int step = 0; step < n_steps; step++) {
     int64_t t = S->t;
+    if (S->recording) rec_begin_step(S);
     occ_t O;
     build_occ(S, &O);
     S->veh_steps += O.n;
@@ -710,7 +780,7 @@ int orc_step(orc_sim* S, int32_t n_steps) {
     /* own-lane acceleration and tentative move of every vehicle */
     for (int i = 0; i < nt; i++) {
       if (S->st[i] != ST_ACTIVE) continue;
-      a_own[i] = acc_own(S, &O, i);
+      a_own[i] = acc_own(S, &O, i, S->recording ? &own_f[i] : NULL);
       ballistic(S->x[i], S->v[i], a_own[i], S->dt, S->hdt2, &xo[i], &vo[i]);
     }
 
@@ -783,12 +853,14 @@ int orc_step(orc_sim* S, int32_t n_steps) {
           else if (Ln < 0) Ln = j;
         }
         float ac;
+        accform cf;
         if (Ln >= 0) {
           float sl = (S->x[Ln] - S->x[i]) - S->len_v;
           if (!(sl > 0.0f)) continue;
           ac = acc_gap(S, e, sl, S->v[i], S->v[Ln]);
+          cf = (accform){FORM_LEAD, Ln, sl, S->v[Ln]};
         } else {
-          ac = acc_front(S, &O, i, e, l2, S->x[i], S->v[i]);
+          ac = acc_front(S, &O, i, e, l2, S->x[i], S->v[i], &cf);
         }
         if (!(ac >= -S->mbsafe)) continue;
         float an = 0.0f;
@@ -798,7 +870,7 @@ int orc_step(orc_sim* S, int32_t n_steps) {
           an = acc_gap(S, e, sg, S->v[Fn], S->v[i]);
           if (!(an >= -S->mbsafe)) continue;
         }
-        if (mand) { chosen = d; chosen_at = ac; break; }
+        if (mand) { chosen = d; chosen_at = ac; tgt_f[i] = cf; break; }
         float dc = ac - a_own[i];
         float dn = Fn >= 0 ? an - a_own[Fn] : 0.0f;
         float dn_o = 0.0f;
@@ -806,13 +878,13 @@ int orc_step(orc_sim* S, int32_t n_steps) {
         if (F >= 0) {
           int L = leader_of(S, &O, i);
           float ao = (L >= 0) ? acc_gap(S, e, (S->x[L] - S->x[F]) - S->len_v, S->v[F], S->v[L])
-                              : acc_front(S, &O, F, e, l, S->x[F], S->v[F]);
+                              : acc_front(S, &O, F, e, l, S->x[F], S->v[F], NULL);
           dn_o = ao - a_own[F];
         }
         float inc = dc + S->mp * (dn + dn_o);
         if (d < 0) inc = inc + S->mbias;
         if (!(inc > S->mathr)) continue;
-        if (chosen == 0 || inc > chosen_inc) { chosen = d; chosen_inc = inc; chosen_at = ac; }
+        if (chosen == 0 || inc > chosen_inc) { chosen = d; chosen_inc = inc; chosen_at = ac; tgt_f[i] = cf; }
       }
       intent[i] = (int8_t)chosen;
       at[i] = chosen_at;
@@ -852,6 +924,15 @@ int orc_step(orc_sim* S, int32_t n_steps) {
       float acc = change[i] ? at[i] : a_own[i];
       float x1, v1;
       ballistic(S->x[i], S->v[i], acc, S->dt, S->hdt2, &x1, &v1);
+      orc_rec* rr = NULL;
+      if (S->recording) {
+        rr = rec_push(S);
+        accform fu = change[i] ? tgt_f[i] : own_f[i];
+        rr->vid = i; rr->lead = fu.lead; rr->link = e; rr->kind = (uint8_t)fu.kind;
+        rr->s = fu.s; rr->v = S->v[i]; rr->vl = fu.vl; rr->a = acc;
+        rr->branch = (S->v[i] + acc * S->dt >= 0.0f) ? BR_NORMAL : BR_STOP;
+        rr->crossed = 0;
+      }
       int l1 = S->lane[i] + change[i];
       S->dec[i] = change[i];
       int node = S->lt[e];
@@ -860,6 +941,7 @@ int orc_step(orc_sim* S, int32_t n_steps) {
         int nx = next_link(S, i, S->cur[i]);
         if (nx < 0) {
           nst[i] = ST_ARRIVED; nlink[i] = -1; nx_[i] = 0.0f; nv[i] = 0.0f;
+          if (rr) rr->branch = BR_ARRIVE;
           S->arr_step[i] = (int32_t)t;
           arrivals++;
           continue;
@@ -873,8 +955,10 @@ int orc_step(orc_sim* S, int32_t n_steps) {
           ncur[i] = S->loop ? (S->cur[i] + 1) % rlen : S->cur[i] + 1;
           nx_[i] = x1 - S->len[e]; nv[i] = v1;
           if (was_holder) S->holder[node] = -1;
+          if (rr) rr->crossed = 1;
         } else {
           nlane[i] = l1; nx_[i] = S->len[e]; nv[i] = 0.0f;
+          if (rr) rr->branch = BR_CLAMP;
         }
       } else {
         nlane[i] = l1; nx_[i] = x1; nv[i] = v1;
@@ -921,7 +1005,7 @@ int orc_step(orc_sim* S, int32_t n_steps) {
     free_occ(&O);
   }
   free(a_own); free(xo); free(vo); free(at); free(intent); free(change); free(cand); free(best);
-  free(nst); free(nlink); free(nlane); free(ncur); free(nx_); free(nv);
+  free(nst); free(nlink); free(nlane); free(ncur); free(nx_); free(nv); free(own_f); free(tgt_f);
   return OK;
 }
 
@@ -972,5 +1056,239 @@ int orc_counters(const orc_sim* S, int64_t out[8]) {
   }
   out[0] = S->t; out[1] = S->departed; out[2] = waiting; out[3] = active;
   out[4] = S->arrived; out[5] = S->veh_steps; out[6] = pending; out[7] = S->active_last;
+  return OK;
+}
+
+/* ------------------------------------------------------------------ calibration adjoint
+ * Not in the paper (the calibration workload of this build): loss
+ *   L = sum over observations k and trips v of (p_v(t_k) - target_{k,v})^2,
+ * t_k = k * obs_every steps after the start, p_v = route progress (length of the
+ * completed links of the route plus x; 0 before departure; the whole route length
+ * after arrival).  Its gradient with respect to the IDM parameters of every link
+ * class (v0, T, a, b, s0) holds every discrete decision of the run fixed: leaders,
+ * lane changes, admissions, the stop-within-the-step branch, the clamp at a closed
+ * stop line, floors of Eq. 7, departures and arrivals (the "tape").
+ */
+static double route_prefix(const orc_sim* S, int i, int upto) {
+  double p = 0.0;
+  for (int k = 0; k < upto; k++) p += (double)S->len[S->rl[S->roff[i] + k]];
+  return p;
+}
+
+static double progress_of(const orc_sim* S, int i) {
+  if (S->st[i] == ST_ACTIVE) return route_prefix(S, i, S->cur[i]) + (double)S->x[i];
+  if (S->st[i] == ST_ARRIVED) return route_prefix(S, i, route_len(S, i));
+  return 0.0;
+}
+
+int orc_observe(orc_sim* S, int32_t n_steps, int32_t obs_every, double* progress) {
+  if (!S->routed) return ESTATE;
+  if (obs_every <= 0 || n_steps < 0) return EINV;
+  int nobs = n_steps / obs_every;
+  for (int k = 0; k < nobs; k++) {
+    orc_step(S, obs_every);
+    for (int i = 0; i < S->nt; i++) progress[(int64_t)k * S->nt + i] = progress_of(S, i);
+  }
+  return OK;
+}
+
+int orc_set_class_params(orc_sim* S, const float* v0, const float* T, const float* a, const float* b,
+                         const float* s0) {
+  for (int c = 0; c < S->ncls; c++)
+    if (!(a[c] > 0.0f) || !(b[c] > 0.0f) || !(T[c] >= 0.0f) || !(s0[c] >= 0.0f)) return EINV;
+  for (int c = 0; c < S->ncls; c++) {
+    S->pv0[c] = v0[c]; S->pT[c] = T[c]; S->pa[c] = a[c]; S->pb[c] = b[c]; S->ps0[c] = s0[c];
+    S->psab[c] = sqrtf(S->pa[c] * S->pb[c]);
+  }
+  for (int e = 0; e < S->nl; e++) S->v0l[e] = S->pv0[S->cls[e]] > 0.0f ? S->pv0[S->cls[e]] : S->spd[e];
+  return OK;
+}
+
+/* Partial derivatives of Eq. 7 (binary64) at the taped point: acceleration a with
+ * respect to the gap s, own speed v, leader speed vl and the class parameters
+ * (A, B, T, s0, v0).  The floors (gap at s_min, dynamic term at 0) are decided as in
+ * the binary32 forward pass and held fixed. */
+typedef struct { double ds, dv, dvl, dA, dB, dT, ds0, dv0; } idm_grad;
+
+static idm_grad idm_partials(const orc_sim* S, int c, double v0, int kind, float s32, float v32, float vl32) {
+  idm_grad g;
+  memset(&g, 0, sizeof g);
+  double A = S->pa[c], Bb = S->pb[c], T = S->pT[c], s0 = S->ps0[c];
+  double v = v32;
+  double r = v / v0;
+  double r3 = r * r * r, r4 = r3 * r;
+  g.dA = 1.0 - r4;
+  g.dv0 = 4.0 * A * r4 / v0;
+  g.dv = -4.0 * A * r3 / v0;
+  if (kind == FORM_FREE || kind == FORM_NONE) return g;
+  /* decisions taken in binary32, exactly as the forward pass took them */
+  float dv32 = v32 - vl32;
+  float t1 = v32 * S->pT[c];
+  float t2 = (v32 * dv32) / (2.0f * S->psab[c]);
+  int dyn_on = (t1 + t2) > 0.0f;
+  int floored = !(s32 >= S->s_min) || s32 == S->s_min;
+  double vl = vl32, s = s32;
+  double cc = 1.0 / (2.0 * sqrt(A * Bb));
+  double dvv = v - vl;
+  double ss = s0 + (dyn_on ? v * T + v * dvv * cc : 0.0);
+  double se = floored ? (double)S->s_min : s;
+  double q = ss / se;
+  double k2 = -2.0 * A * q / se;      /* d a / d ss */
+  g.dA += -q * q;
+  g.ds0 = k2;
+  if (dyn_on) {
+    g.dT = k2 * v;
+    g.dA += k2 * v * dvv * (-cc / (2.0 * A));
+    g.dB = k2 * v * dvv * (-cc / (2.0 * Bb));
+    g.dv += k2 * (T + (dvv + v) * cc);
+    g.dvl = k2 * (-v * cc);
+  }
+  g.ds = floored ? 0.0 : 2.0 * A * q * q / se;
+  return g;
+}
+
+int orc_adjoint(orc_sim* S, int32_t n_steps, int32_t obs_every, const double* target, double* grad, double* loss) {
+  if (!S->routed) return ESTATE;
+  if (obs_every <= 0 || n_steps <= 0 || n_steps % obs_every) return EINV;
+  int nt = S->nt, nobs = n_steps / obs_every;
+  /* start state, kept for the taped replay */
+  free(S->st0); free(S->cur0); free(S->x0); free(S->v0s); free(S->tgt);
+  S->st0 = (uint8_t*)xcalloc(nt, 1); S->cur0 = (int32_t*)xcalloc(nt, 4);
+  S->x0 = (float*)xcalloc(nt, 4); S->v0s = (float*)xcalloc(nt, 4);
+  memcpy(S->st0, S->st, (size_t)nt); memcpy(S->cur0, S->cur, (size_t)nt * 4);
+  memcpy(S->x0, S->x, (size_t)nt * 4); memcpy(S->v0s, S->v, (size_t)nt * 4);
+  S->tgt = (double*)xcalloc((size_t)nobs * nt, 8);
+  memcpy(S->tgt, target, (size_t)nobs * nt * 8);
+  S->tgt_nobs = nobs; S->tgt_every = obs_every;
+  /* forward with the tape; residuals of the observations */
+  double* res = (double*)xcalloc((size_t)nobs * nt, 8);
+  double L = 0.0;
+  S->rec_n = 0; S->rec_steps = 0; S->recording = 1;
+  for (int k = 0; k < nobs; k++) {
+    orc_step(S, obs_every);
+    for (int i = 0; i < nt; i++) {
+      double r = progress_of(S, i) - target[(int64_t)k * nt + i];
+      L += r * r;
+      res[(int64_t)k * nt + i] = S->st[i] == ST_ACTIVE ? r : 0.0;   /* only positions depend on the parameters */
+    }
+  }
+  S->recording = 0;
+  S->rec_step[S->rec_steps] = S->rec_n;
+  /* reverse sweep in binary64 */
+  double* lx = (double*)xcalloc(nt, 8); double* lv = (double*)xcalloc(nt, 8);
+  double* nx = (double*)xcalloc(nt, 8); double* nv = (double*)xcalloc(nt, 8);
+  for (int q = 0; q < S->ncls * 5; q++) grad[q] = 0.0;
+  double dt = S->dt, h = 0.5 * dt * dt;
+  for (int j = n_steps - 1; j >= 0; j--) {
+    if ((j + 1) % obs_every == 0) {
+      int k = (j + 1) / obs_every - 1;
+      for (int i = 0; i < nt; i++) lx[i] += 2.0 * res[(int64_t)k * nt + i];
+    }
+    memset(nx, 0, (size_t)nt * 8); memset(nv, 0, (size_t)nt * 8);
+    for (int64_t q = S->rec_step[j]; q < S->rec_step[j + 1]; q++) {
+      const orc_rec* r = &S->rec[q];
+      int i = r->vid;
+      double mu = 0.0;
+      if (r->branch == BR_NORMAL) {
+        mu = lx[i] * h + lv[i] * dt;
+        nx[i] += lx[i];
+        nv[i] += lx[i] * dt + lv[i];
+      } else if (r->branch == BR_STOP) {
+        double a = r->a, v = r->v;
+        mu = lx[i] * v * v / (2.0 * a * a);
+        nx[i] += lx[i];
+        nv[i] += lx[i] * (-v / a);
+      }
+      if (mu == 0.0 || r->kind == FORM_NONE) continue;
+      int c = S->cls[r->link];
+      double v0 = S->v0l[r->link];
+      idm_grad g = idm_partials(S, c, v0, r->kind, r->s, r->v, r->vl);
+      nv[i] += mu * g.dv;
+      if (r->kind != FORM_FREE) nx[i] -= mu * g.ds;
+      if (r->kind == FORM_LEAD || r->kind == FORM_NEXT) {
+        nx[r->lead] += mu * g.ds;
+        nv[r->lead] += mu * g.dvl;
+      }
+      if (S->pv0[c] > 0.0f) grad[c * 5 + 0] += mu * g.dv0;
+      grad[c * 5 + 1] += mu * g.dT;
+      grad[c * 5 + 2] += mu * g.dA;
+      grad[c * 5 + 3] += mu * g.dB;
+      grad[c * 5 + 4] += mu * g.ds0;
+    }
+    double* tx = lx; lx = nx; nx = tx;
+    double* tv = lv; lv = nv; nv = tv;
+  }
+  *loss = L;
+  free(lx); free(lv); free(nx); free(nv); free(res);
+  return OK;
+}
+
+/* Loss of the last taped run replayed in binary64 with other class parameters
+ * (v0, T, a, b, s0 per class), every discrete decision taken from the tape. */
+int orc_replay_loss(const orc_sim* S, const double* pv0, const double* pT, const double* pa, const double* pb,
+                    const double* ps0, double* loss) {
+  if (!S->st0 || S->rec_steps <= 0) return ESTATE;
+  int nt = S->nt;
+  double* x = (double*)xcalloc(nt, 8); double* v = (double*)xcalloc(nt, 8);
+  double* off = (double*)xcalloc(nt, 8); double* acc = (double*)xcalloc(nt, 8);
+  uint8_t* st = (uint8_t*)xcalloc(nt, 1);
+  for (int i = 0; i < nt; i++) {
+    st[i] = S->st0[i];
+    if (st[i] == ST_ACTIVE) { x[i] = S->x0[i]; v[i] = S->v0s[i]; off[i] = route_prefix(S, i, S->cur0[i]); }
+  }
+  double dt = S->dt, h = 0.5 * dt * dt, L = 0.0;
+  for (int j = 0; j < S->rec_steps; j++) {
+    /* vehicles that entered at the end of the previous step */
+    for (int64_t q = S->rec_step[j]; q < S->rec_step[j + 1]; q++) {
+      int i = S->rec[q].vid;
+      if (st[i] != ST_ACTIVE) { st[i] = ST_ACTIVE; x[i] = 0.0; v[i] = 0.0; off[i] = 0.0; }
+    }
+    for (int64_t q = S->rec_step[j]; q < S->rec_step[j + 1]; q++) {
+      const orc_rec* r = &S->rec[q];
+      int i = r->vid, c = S->cls[r->link];
+      double A = pa[c], Bb = pb[c], T = pT[c], s0 = ps0[c];
+      double v0 = S->pv0[c] > 0.0f ? pv0[c] : (double)S->spd[r->link];
+      double rr = v[i] / v0, r4 = rr * rr * rr * rr;
+      double a = A * (1.0 - r4);
+      if (r->kind != FORM_FREE && r->kind != FORM_NONE) {
+        double s, vl;
+        double Lk = S->len[r->link];
+        if (r->kind == FORM_LEAD) { s = (x[r->lead] - x[i]) - S->len_v; vl = v[r->lead]; }
+        else if (r->kind == FORM_NEXT) { s = ((Lk - x[i]) + x[r->lead]) - S->len_v; vl = v[r->lead]; }
+        else { s = Lk - x[i]; vl = 0.0; }
+        float dv32 = r->v - r->vl;
+        int c32 = c;
+        float t1 = r->v * S->pT[c32];
+        float t2 = (r->v * dv32) / (2.0f * S->psab[c32]);
+        int dyn_on = (t1 + t2) > 0.0f;
+        int floored = !(r->s >= S->s_min) || r->s == S->s_min;
+        double ss = s0 + (dyn_on ? v[i] * T + v[i] * (v[i] - vl) / (2.0 * sqrt(A * Bb)) : 0.0);
+        double se = floored ? (double)S->s_min : s;
+        double qq = ss / se;
+        a -= A * qq * qq;
+      }
+      acc[i] = a;
+    }
+    for (int64_t q = S->rec_step[j]; q < S->rec_step[j + 1]; q++) {
+      const orc_rec* r = &S->rec[q];
+      int i = r->vid;
+      double Lk = S->len[r->link];
+      if (r->branch == BR_ARRIVE) { st[i] = ST_ARRIVED; continue; }
+      if (r->branch == BR_CLAMP) { x[i] = Lk; v[i] = 0.0; continue; }
+      if (r->branch == BR_NORMAL) { x[i] = x[i] + (v[i] * dt + acc[i] * h); v[i] = v[i] + acc[i] * dt; }
+      else { x[i] = x[i] - v[i] * v[i] / (2.0 * acc[i]); v[i] = 0.0; }
+      if (r->crossed) { x[i] -= Lk; off[i] += Lk; }
+    }
+    if ((j + 1) % S->tgt_every == 0) {
+      int k = (j + 1) / S->tgt_every - 1;
+      for (int i = 0; i < nt; i++) {
+        double p = st[i] == ST_ACTIVE ? off[i] + x[i] : (st[i] == ST_ARRIVED ? route_prefix(S, i, route_len(S, i)) : 0.0);
+        double d = p - S->tgt[(int64_t)k * nt + i];
+        L += d * d;
+      }
+    }
+  }
+  *loss = L;
+  free(x); free(v); free(off); free(acc); free(st);
   return OK;
 }

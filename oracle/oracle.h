@@ -55,6 +55,15 @@ int  orc_n_lanes(const orc_sim*);
 int  orc_counters(const orc_sim*, int64_t out[8]);
 int  orc_node_holder(const orc_sim*, int32_t* holder);
 
+/* calibration (not in the paper): route progress every obs_every steps, and the
+ * gradient of the squared progress error with respect to the IDM parameters of every
+ * class (v0, T, a, b, s0), discrete decisions held fixed; binary64 reverse sweep */
+int  orc_observe(orc_sim*, int32_t n_steps, int32_t obs_every, double* progress);
+int  orc_adjoint(orc_sim*, int32_t n_steps, int32_t obs_every, const double* target, double* grad, double* loss);
+int  orc_replay_loss(const orc_sim*, const double* v0, const double* T, const double* a, const double* b,
+                     const double* s0, double* loss);
+int  orc_set_class_params(orc_sim*, const float* v0, const float* T, const float* a, const float* b, const float* s0);
+
 /* building blocks exposed for the pin tests */
 float orc_idm(float a, float b, float T, float s0, float v0, float s_min,
               float s, float v, float v_lead, int has_leader);

@@ -71,6 +71,10 @@ def lib():
         L.orc_n_lanes.argtypes = [vp]
         L.orc_counters.argtypes = [vp, vp]
         L.orc_node_holder.argtypes = [vp, vp]
+        L.orc_observe.argtypes = [vp, i32, i32, vp]
+        L.orc_adjoint.argtypes = [vp, i32, i32, vp, vp, vp]
+        L.orc_replay_loss.argtypes = [vp] + [vp] * 6
+        L.orc_set_class_params.argtypes = [vp] * 6
         L.orc_idm.argtypes = [f32] * 9 + [C.c_int]
         L.orc_idm.restype = f32
         L.orc_ballistic.argtypes = [f32, f32, f32, f32, C.POINTER(f32), C.POINTER(f32)]
@@ -198,6 +202,28 @@ class OracleSim:
         _check(lib().orc_counters(self.h, _p(c)), "orc_counters")
         keys = ("t", "departed", "waiting", "active", "arrived", "veh_steps", "pending", "active_last")
         return {k: int(v) for k, v in zip(keys, c)}
+
+    def set_class_params(self, v0, T, a, b, s0):
+        arrs = [np.ascontiguousarray(q, np.float32) for q in (v0, T, a, b, s0)]
+        _check(lib().orc_set_class_params(self.h, *[_p(q) for q in arrs]), "orc_set_class_params")
+
+    def observe(self, n_steps, obs_every):
+        out = np.zeros((n_steps // obs_every, self.n_trips), np.float64)
+        _check(lib().orc_observe(self.h, int(n_steps), int(obs_every), _p(out)), "orc_observe")
+        return out
+
+    def adjoint(self, n_steps, obs_every, target, n_class):
+        t = np.ascontiguousarray(target, np.float64)
+        g = np.zeros(n_class * 5, np.float64)
+        loss = np.zeros(1, np.float64)
+        _check(lib().orc_adjoint(self.h, int(n_steps), int(obs_every), _p(t), _p(g), _p(loss)), "orc_adjoint")
+        return g, float(loss[0])
+
+    def replay_loss(self, v0, T, a, b, s0):
+        arrs = [np.ascontiguousarray(q, np.float64) for q in (v0, T, a, b, s0)]
+        loss = np.zeros(1, np.float64)
+        _check(lib().orc_replay_loss(self.h, *[_p(q) for q in arrs], _p(loss)), "orc_replay_loss")
+        return float(loss[0])
 
     def node_holder(self):
         h = np.zeros(self.n_nodes, np.int32)

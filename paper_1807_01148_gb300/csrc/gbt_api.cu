@@ -24,6 +24,10 @@ void launch_occ_out(const Dev& d, int grid, cudaStream_t s, int32_t* sorted_vid)
 void launch_state_check(const Dev& d, int grid, cudaStream_t s, const uint8_t* status, const int32_t* link,
                         const int32_t* lane, const int32_t* cursor, const float* x, const float* v, int* bad);
 cudaError_t launch_steps_timed(const Dev& d, int grid, bool has_stop, cudaStream_t s, int n, float* kernel_ms);
+void launch_observe(const Dev& d, int grid, cudaStream_t s, const double* target, double* res, double* p_out);
+void launch_tape_begin(const Dev& d, cudaStream_t s);
+void launch_adj_step(const Dev& d, int grid, cudaStream_t s, const TapeRec* slab, const double* lx,
+                     const double* lv, const double* res, double* nx, double* nv, double* grad, int n_class);
 void launch_first_links(const int32_t* roff, const int32_t* routes, int n, int32_t* out, cudaStream_t s);
 }  // namespace gbt
 
@@ -58,6 +62,16 @@ struct sim_handle {
   cudaGraphExec_t gexec = nullptr;
   cudaGraph_t graph = nullptr;
   bool graph_dirty = true;
+  // class parameters (host copies) and the adjoint's tape
+  std::vector<float> v0c, Tc, ac, bc, s0c, spd_link;
+  std::vector<uint8_t> cls_link;
+  std::vector<LinkRec> recs;
+  TapeRec* tape = nullptr;
+  TapeForm* tform = nullptr;
+  int tape_steps = 0;
+  cudaGraphExec_t gexec_tape = nullptr;
+  cudaGraph_t graph_tape = nullptr;
+  bool tape_graph_dirty = true;
 };
 
 namespace {
@@ -267,10 +281,16 @@ int create_from_flat(Flat& F, sim_handle** out) {
   h->lane_base[F.nl] = nlan;
   h->n_lanes = nlan;
   std::vector<ClassPar> cp(F.ncls);
+  std::vector<uint8_t> v0p(F.ncls);
   for (int c = 0; c < F.ncls; c++) {
     float sab = sqrtf(F.a[c] * F.b[c]);
     cp[c] = ClassPar{F.a[c], 2.0f * sab, F.T[c], F.s0[c]};
+    v0p[c] = F.v0[c] > 0.0f ? 1 : 0;
   }
+  h->v0c = F.v0; h->Tc = F.T; h->ac = F.a; h->bc = F.b; h->s0c = F.s0;
+  h->spd_link = F.spd;
+  h->cls_link = F.cls;
+  h->recs = recs;
   // mandatory-switch table: tau[k] = sqrt(-ln((k + 0.5) / 256)) in binary64, rounded once
   std::vector<float> tau(256);
   for (int k = 0; k < 256; k++) tau[k] = (float)std::sqrt(-std::log(((double)k + 0.5) / 256.0));
@@ -289,6 +309,12 @@ int create_from_flat(Flat& F, sim_handle** out) {
     TRY(upload(h, &links, recs.data(), recs.size()));
     TRY(upload(h, &cls, cp.data(), cp.size()));
     TRY(upload(h, &taud, tau.data(), tau.size()));
+    float* clsb;
+    uint8_t* clsv0;
+    TRY(upload(h, &clsb, F.b.data(), F.b.size()));
+    TRY(upload(h, &clsv0, v0p.data(), v0p.size()));
+    d.cls_b = clsb;
+    d.cls_v0_param = clsv0;
     d.links = links;
     d.cls = cls;
     d.tau = taud;
@@ -435,6 +461,7 @@ int build_queues(sim_handle* h, const std::vector<uint8_t>& status) {
   h->d.qlinks = h->qlinks;
   h->d.n_qlinks = (int)ql.size();
   h->graph_dirty = true;
+  h->tape_graph_dirty = true;
   return SIM_OK;
 }
 
@@ -926,12 +953,218 @@ int sim_counters(sim_handle* h, sim_counters_t* out) {
   return SIM_OK;
 }
 
+int sim_set_class_params(sim_handle* h, const float* v0, const float* T, const float* a, const float* b,
+                         const float* s0) {
+  if (!h || !v0 || !T || !a || !b || !s0) return SIM_EINVAL;
+  for (int c = 0; c < h->ncls; c++)
+    if (!(a[c] > 0.0f) || !(b[c] > 0.0f) || !(T[c] >= 0.0f) || !(s0[c] >= 0.0f) ||
+        ((h->v0c[c] > 0.0f) != (v0[c] > 0.0f)))
+      return fail(h, SIM_EINVAL, "class parameters need a > 0, b > 0, T >= 0, s0 >= 0, and v0 > 0 exactly for "
+                                 "the classes created with v0 > 0");
+  std::vector<ClassPar> cp(h->ncls);
+  for (int c = 0; c < h->ncls; c++) {
+    h->v0c[c] = v0[c]; h->Tc[c] = T[c]; h->ac[c] = a[c]; h->bc[c] = b[c]; h->s0c[c] = s0[c];
+    float sab = sqrtf(a[c] * b[c]);
+    cp[c] = ClassPar{a[c], 2.0f * sab, T[c], s0[c]};
+  }
+  for (int e = 0; e < h->nl; e++) {
+    const int c = h->cls_link[e];
+    h->recs[e].v0 = h->v0c[c] > 0.0f ? h->v0c[c] : h->spd_link[e];
+  }
+  CK(cudaMemcpyAsync(const_cast<ClassPar*>(h->d.cls), cp.data(), cp.size() * sizeof(ClassPar),
+                     cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(const_cast<float*>(h->d.cls_b), h->bc.data(), h->bc.size() * 4, cudaMemcpyHostToDevice,
+                     h->stream));
+  CK(cudaMemcpyAsync(const_cast<LinkRec*>(h->d.links), h->recs.data(), h->recs.size() * sizeof(LinkRec),
+                     cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+
+int sim_observe(sim_handle* h, int32_t n_steps, int32_t obs_every, double* progress) {
+  if (!h || !progress || obs_every <= 0 || n_steps < 0) return SIM_EINVAL;
+  if (!h->routed) return fail(h, SIM_ESTATE, "sim_observe before routes exist");
+  const int nobs = n_steps / obs_every;
+  const size_t nt = (size_t)h->nt;
+  double* dp;
+  int rc = dalloc(h, &dp, std::max<size_t>(1, nt));
+  if (rc) return rc;
+  for (int k = 0; k < nobs; k++) {
+    if ((rc = sim_step(h, obs_every))) break;
+    launch_observe(h->d, h->grid, h->stream, nullptr, nullptr, dp);
+    cudaError_t e = cudaMemcpyAsync(progress + (size_t)k * nt, dp, nt * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(h, e, "observe");
+      break;
+    }
+  }
+  dfree(h, dp);
+  return rc;
+}
+
+namespace {
+
+// Everything a step changes, for the adjoint's checkpoints.
+struct CkptLayout {
+  size_t nt, nn, nl, nlan, bytes;
+};
+
+CkptLayout ckpt_layout(const sim_handle* h) {
+  CkptLayout L;
+  L.nt = (size_t)std::max(1, h->nt);
+  L.nn = (size_t)h->nn;
+  L.nl = (size_t)h->nl;
+  L.nlan = (size_t)h->n_lanes;
+  L.bytes = L.nt * (7 * 4 + 1 + 4 + 4 + 1 + 4) + L.nn * 4 + L.nl * 4 + L.nlan * 4 + sizeof(Ctl) + 64;
+  return L;
+}
+
+cudaError_t ckpt_copy(sim_handle* h, unsigned char* buf, bool save) {
+  const CkptLayout L = ckpt_layout(h);
+  Dev& d = h->d;
+  struct Item { void* p; size_t n; } items[] = {
+      {d.A.x, L.nt * 4}, {d.A.v, L.nt * 4}, {d.A.vid, L.nt * 4}, {d.A.link, L.nt * 4}, {d.A.nxt, L.nt * 4},
+      {d.A.cur, L.nt * 4}, {d.A.lane, L.nt * 4}, {d.status, L.nt}, {d.ins_step, L.nt * 4}, {d.arr_step, L.nt * 4},
+      {d.dec, L.nt}, {d.aidx, L.nt * 4}, {d.holder, L.nn * 4}, {h->q_head, L.nl * 4}, {d.cnt, L.nlan * 4},
+      {d.ctl, sizeof(Ctl)}};
+  size_t off = 0;
+  for (const Item& it : items) {
+    if (!it.p || !it.n) continue;
+    cudaError_t e = save ? cudaMemcpyAsync(buf + off, it.p, it.n, cudaMemcpyDeviceToDevice, h->stream)
+                         : cudaMemcpyAsync(it.p, buf + off, it.n, cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return e;
+    off += it.n;
+  }
+  if (!save) {
+    // epoch-tagged keys written after the checkpoint would outrank the replayed steps' keys
+    cudaError_t e = cudaMemsetAsync(d.best, 0xFF, L.nlan * 8, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.acq, 0xFF, L.nn * 8, h->stream);
+    return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+int sim_adjoint(sim_handle* h, const sim_loss_spec* spec, double* grad_out, double* loss_out) {
+  if (!h || !spec || !grad_out || !loss_out || !spec->target) return SIM_EINVAL;
+  if (!h->routed) return fail(h, SIM_ESTATE, "sim_adjoint before routes exist");
+  const int n_steps = spec->n_steps, every = spec->obs_every;
+  const int seg = spec->checkpoint_every > 0 ? spec->checkpoint_every : 64;
+  if (n_steps <= 0 || every <= 0 || n_steps % every) return fail(h, SIM_EINVAL, "n_steps must be a multiple of obs_every");
+  if (int rc = check_horizon(h, n_steps)) return rc;
+  const int nobs = n_steps / every, nseg = (n_steps + seg - 1) / seg;
+  const size_t nt = (size_t)std::max(1, h->nt);
+  // sim_step's graph
+  int rc = sim_step(h, 0);
+  if (rc) return rc;
+  if (h->graph_dirty) {
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->gexec = nullptr;
+    h->graph = nullptr;
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    launch_step(h->d, h->grid, h->has_stop, h->cap_stream);
+    CK(cudaStreamEndCapture(h->cap_stream, &h->graph));
+    CK(cudaGraphInstantiate(&h->gexec, h->graph, 0));
+    h->graph_dirty = false;
+  }
+  // tape of one segment and its graph
+  if (h->tape_steps != seg || !h->tape) {
+    dfree(h, h->tape);
+    dfree(h, h->tform);
+    h->tape = nullptr;
+    h->tform = nullptr;
+    if ((rc = dalloc(h, &h->tape, (size_t)seg * nt))) return rc;
+    if ((rc = dalloc(h, &h->tform, nt))) return rc;
+    h->tape_steps = seg;
+    h->tape_graph_dirty = true;
+  }
+  if (h->tape_graph_dirty) {
+    if (h->gexec_tape) cudaGraphExecDestroy(h->gexec_tape);
+    if (h->graph_tape) cudaGraphDestroy(h->graph_tape);
+    h->gexec_tape = nullptr;
+    h->graph_tape = nullptr;
+    Dev dt = h->d;
+    dt.tape = h->tape;
+    dt.tform = h->tform;
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    launch_step(dt, h->grid, h->has_stop, h->cap_stream);
+    CK(cudaStreamEndCapture(h->cap_stream, &h->graph_tape));
+    CK(cudaGraphInstantiate(&h->gexec_tape, h->graph_tape, 0));
+    h->tape_graph_dirty = false;
+  }
+  Dev dtape = h->d;
+  dtape.tape = h->tape;
+  dtape.tform = h->tform;
+  // working memory of this call
+  const CkptLayout CL = ckpt_layout(h);
+  unsigned char* ck;
+  double *tgt, *res, *lam, *grad;
+  std::vector<void*> tmp;
+  auto release = [&]() {
+    for (void* p : tmp) dfree(h, p);
+  };
+  if ((rc = dalloc(h, &ck, CL.bytes * (size_t)(nseg + 1))) || (tmp.push_back(ck), false) ||
+      (rc = dalloc(h, &tgt, (size_t)nobs * nt)) || (tmp.push_back(tgt), false) ||
+      (rc = dalloc(h, &res, (size_t)nobs * nt)) || (tmp.push_back(res), false) ||
+      (rc = dalloc(h, &lam, 4 * nt)) || (tmp.push_back(lam), false) ||
+      (rc = dalloc(h, &grad, (size_t)h->ncls * 5)) || (tmp.push_back(grad), false)) {
+    release();
+    return rc;
+  }
+  const int ng = h->ncls * 5;
+  cudaError_t e = cudaMemcpyAsync(tgt, spec->target, (size_t)nobs * nt * 8, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(grad, 0, (size_t)ng * 8, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&h->d.ctl->loss, 0, 8, h->stream);
+  // ---- forward: checkpoint every `seg` steps, observe every `every` steps
+  for (int sg = 0; sg < nseg && e == cudaSuccess; sg++) {
+    e = ckpt_copy(h, ck + (size_t)sg * CL.bytes, true);
+    const int j1 = std::min(n_steps, (sg + 1) * seg);
+    for (int j = sg * seg; j < j1 && e == cudaSuccess; j++) {
+      e = cudaGraphLaunch(h->gexec, h->stream);
+      if ((j + 1) % every == 0) {
+        const int k = (j + 1) / every - 1;
+        launch_observe(h->d, h->grid, h->stream, tgt + (size_t)k * nt, res + (size_t)k * nt, nullptr);
+      }
+    }
+  }
+  if (e == cudaSuccess) e = ckpt_copy(h, ck + (size_t)nseg * CL.bytes, true);   // end state
+  // ---- reverse: per segment, replay it with the tape, then sweep it backwards
+  double *lx = lam, *lv = lam + nt, *nx = lam + 2 * nt, *nv = lam + 3 * nt;
+  if (e == cudaSuccess) e = cudaMemsetAsync(lam, 0, 2 * nt * 8, h->stream);
+  for (int sg = nseg - 1; sg >= 0 && e == cudaSuccess; sg--) {
+    const int j0 = sg * seg, j1 = std::min(n_steps, (sg + 1) * seg);
+    e = ckpt_copy(h, ck + (size_t)sg * CL.bytes, false);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->tape, 0, (size_t)seg * nt * sizeof(TapeRec), h->stream);
+    launch_tape_begin(h->d, h->stream);
+    for (int j = j0; j < j1 && e == cudaSuccess; j++) e = cudaGraphLaunch(h->gexec_tape, h->stream);
+    for (int j = j1 - 1; j >= j0 && e == cudaSuccess; j--) {
+      e = cudaMemsetAsync(nx, 0, 2 * nt * 8, h->stream);
+      const double* r = ((j + 1) % every == 0) ? res + (size_t)((j + 1) / every - 1) * nt : nullptr;
+      launch_adj_step(dtape, h->grid, h->stream, h->tape + (size_t)(j - j0) * nt, lx, lv, r, nx, nv, grad, h->ncls);
+      std::swap(lx, nx);
+      std::swap(lv, nv);
+    }
+  }
+  if (e == cudaSuccess) e = ckpt_copy(h, ck + (size_t)nseg * CL.bytes, false);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(grad_out, grad, (size_t)ng * 8, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(loss_out, &h->d.ctl->loss, 8, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  release();
+  if (e != cudaSuccess) return cuda_fail(h, e, "adjoint");
+  return check_device(h);
+}
+
 const char* sim_last_error(const sim_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
 void sim_destroy(sim_handle* h) {
   if (!h) return;
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->graph) cudaGraphDestroy(h->graph);
+  if (h->gexec_tape) cudaGraphExecDestroy(h->gexec_tape);
+  if (h->graph_tape) cudaGraphDestroy(h->graph_tape);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (void* p : h->allocs) cudaFree(p);
   delete h;

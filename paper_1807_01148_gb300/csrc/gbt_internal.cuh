@@ -63,6 +63,31 @@ struct Ctl {
   int n_elig;      // vehicles eligible for a lane change this step
   unsigned long long veh_steps, departed, arrived;
   unsigned long long route_cursor;  // bump allocator of the route store
+  long long tape_t0;                // first step of the segment being taped
+  double loss;                      // calibration loss accumulator
+};
+
+// Forms of Eq. 7 an acceleration can come from (adjoint tape).
+constexpr uint8_t kFormNone = 0, kFormLead = 1, kFormFree = 2, kFormStop = 3, kFormNext = 4;
+// How a move ended.
+constexpr uint8_t kBrNormal = 0, kBrStop = 1, kBrClamp = 2, kBrArrive = 3;
+
+// One taped vehicle-step (32 bytes): leader, link, the gap / speeds / acceleration
+// that entered Eq. 7 and the ballistic update, and the discrete outcome.
+struct __align__(16) TapeRec {
+  int32_t lead;
+  int32_t link;
+  float s, v, vl, a;
+  uint8_t kind, branch, crossed, valid;
+  int32_t pad;
+};
+static_assert(sizeof(TapeRec) == 32, "TapeRec must be 32 bytes");
+
+// The form chosen for a lane change (per trip, rewritten each step).
+struct TapeForm {
+  int32_t lead;
+  float s, vl;
+  uint8_t kind, pad0, pad1, pad2;
 };
 
 struct Dev {
@@ -72,6 +97,8 @@ struct Dev {
   const int32_t* node_x;
   const int32_t* node_y;
   const ClassPar* cls;
+  const float* cls_b;            // comfortable deceleration b per class (adjoint)
+  const uint8_t* cls_v0_param;   // 1 when the class sets v0 (else v0 = link speed limit)
   const float* tau;      // mandatory-switch table [256]
   int n_links, n_nodes, n_lanes, n_trips;
   // parameters
@@ -105,6 +132,8 @@ struct Dev {
   int8_t* intent;
   uint8_t* flags;
   int32_t* elig;              // sorted positions of lane-change candidates
+  TapeRec* tape;              // adjoint tape of the current segment (nullptr: not taping)
+  TapeForm* tform;            // lane-change forms of the current step (taping only)
   // per node
   int32_t* holder;
   unsigned long long* acq;

@@ -187,24 +187,39 @@ __device__ __forceinline__ bool line_closed(const Dev& d, const LinkRec& L, int 
 // `lane`: leader = rearmost vehicle of the mapped lane of its next link (gap across
 // the link end); a closed stop line is a standing obstacle (smaller acceleration).
 __device__ __forceinline__ float acc_front(const Dev& d, const LinkRec& L, const ClassPar& P, int vid, int nxt,
-                                           int lane, float x, float v, bool closed) {
-  if (nxt < 0) return idm_acc(P, L.v0, d.s_min, 0.0f, v, 0.0f, false);
+                                           int lane, float x, float v, bool closed, TapeForm* f = nullptr) {
+  if (nxt < 0) {
+    if (f) *f = TapeForm{-1, 0.0f, 0.0f, kFormFree, 0, 0, 0};
+    return idm_acc(P, L.v0, d.s_min, 0.0f, v, 0.0f, false);
+  }
   const LinkRec Ln = d.links[nxt];
   int m = lane < Ln.lanes - 1 ? lane : Ln.lanes - 1;
   int g = Ln.lane_base + m;
   int r = d.lane_start[g];
   float a1;
+  TapeForm f1;
   if (r < d.lane_start[g + 1] && d.B.vid[r] != vid) {
     float s = ((L.len - x) + d.B.x[r]) - d.vlen;
     a1 = idm_acc(P, L.v0, d.s_min, s, v, d.B.v[r], true);
+    if (f) f1 = TapeForm{d.B.vid[r], s, d.B.v[r], kFormNext, 0, 0, 0};
   } else {
     a1 = idm_acc(P, L.v0, d.s_min, 0.0f, v, 0.0f, false);
+    if (f) f1 = TapeForm{-1, 0.0f, 0.0f, kFormFree, 0, 0, 0};
   }
   if (closed) {
-    float a2 = idm_acc(P, L.v0, d.s_min, L.len - x, v, 0.0f, true);
-    return fminf(a1, a2);
+    const float s2 = L.len - x;
+    const float a2 = idm_acc(P, L.v0, d.s_min, s2, v, 0.0f, true);
+    if (a2 < a1) {
+      if (f) *f = TapeForm{-1, s2, 0.0f, kFormStop, 0, 0, 0};
+      return a2;
+    }
   }
+  if (f) *f = f1;
   return a1;
+}
+
+__device__ __forceinline__ TapeRec* tape_slot(const Dev& d, int t, int vid) {
+  return d.tape + (size_t)(t - (int)d.ctl->tape_t0) * (size_t)d.n_trips + (size_t)vid;
 }
 
 __global__ void k_own(Dev d) {
@@ -220,11 +235,21 @@ __global__ void k_own(Dev d) {
     const bool front = (p + 1 == d.lane_start[g + 1]);
     const bool hold = is_holder(d, L, t, vid, lane, front);
     float a;
+    TapeForm f;
     if (!front) {
-      a = idm_acc(P, L.v0, d.s_min, (d.B.x[p + 1] - x) - d.vlen, v, d.B.v[p + 1], true);
+      const float sg = (d.B.x[p + 1] - x) - d.vlen;
+      a = idm_acc(P, L.v0, d.s_min, sg, v, d.B.v[p + 1], true);
+      if (d.tape) f = TapeForm{d.B.vid[p + 1], sg, d.B.v[p + 1], kFormLead, 0, 0, 0};
     } else {
       bool closed = nxt >= 0 && line_closed(d, L, t, hold);
-      a = acc_front(d, L, P, vid, nxt, lane, x, v, closed);
+      a = acc_front(d, L, P, vid, nxt, lane, x, v, closed, d.tape ? &f : nullptr);
+    }
+    if (d.tape) {
+      TapeRec* rec = tape_slot(d, t, vid);
+      rec->lead = f.lead;
+      rec->kind = f.kind;
+      rec->s = f.s;
+      rec->vl = f.vl;
     }
     float xo, vo;
     ballistic(x, v, a, d.dt, d.hdt2, xo, vo);
@@ -324,12 +349,14 @@ __global__ void __launch_bounds__(256, 4) k_decide(Dev d) {
       const int Ln = up < s1 ? up : -1;
       const int Fn = up > s0 ? up - 1 : -1;
       float ac;
+      TapeForm cf;
       if (Ln >= 0) {
         float sl = (d.B.x[Ln] - x) - d.vlen;
         if (!(sl > 0.0f)) continue;
         ac = idm_acc(P, L.v0, d.s_min, sl, v, d.B.v[Ln], true);
+        cf = TapeForm{d.B.vid[Ln], sl, d.B.v[Ln], kFormLead, 0, 0, 0};
       } else {
-        ac = acc_front(d, L, P, vid, nxt, l2, x, v, closed_self);
+        ac = acc_front(d, L, P, vid, nxt, l2, x, v, closed_self, &cf);
       }
       if (!(ac >= -d.mbsafe)) continue;
       float an = 0.0f;
@@ -342,6 +369,7 @@ __global__ void __launch_bounds__(256, 4) k_decide(Dev d) {
       if (mand) {
         chosen = dd;
         chosen_at = ac;
+        if (d.tape) d.tform[vid] = cf;
         break;
       }
       float dc = ac - d.a_own[p];
@@ -369,6 +397,7 @@ __global__ void __launch_bounds__(256, 4) k_decide(Dev d) {
         chosen = dd;
         chosen_inc = inc;
         chosen_at = ac;
+        if (d.tape) d.tform[vid] = cf;
       }
     }
     d.intent[p] = (int8_t)chosen;
@@ -409,6 +438,23 @@ __global__ void k_move(Dev d) {
     const float acc = change ? d.at[p] : d.a_own[p];
     float x1, v1;
     ballistic(x, v, acc, d.dt, d.hdt2, x1, v1);
+    TapeRec* rec = nullptr;
+    if (d.tape) {
+      rec = tape_slot(d, t, vid);
+      if (change) {
+        const TapeForm cf = d.tform[vid];
+        rec->lead = cf.lead;
+        rec->kind = cf.kind;
+        rec->s = cf.s;
+        rec->vl = cf.vl;
+      }
+      rec->link = e;
+      rec->v = v;
+      rec->a = acc;
+      rec->branch = (v + acc * d.dt >= 0.0f) ? kBrNormal : kBrStop;
+      rec->crossed = 0;
+      rec->valid = 1;
+    }
     d.dec[vid] = (int8_t)change;
     const bool hold = (fl & kFlagHolder) != 0;
     int nl = lane + change, nlink = e, ncur = cur, nnxt = nxt;
@@ -417,6 +463,7 @@ __global__ void k_move(Dev d) {
     if (x1 >= L.len) {
       if (nxt < 0) {
         d.A.link[p] = -1;
+        if (rec) rec->branch = kBrArrive;
         d.status[vid] = kArrived;
         d.arr_step[vid] = (int32_t)t;
         atomicAdd(&d.ctl->n_arr, 1);
@@ -435,9 +482,11 @@ __global__ void k_move(Dev d) {
         nl = m;
         nx = x1 - L.len;
         crossed = true;
+        if (rec) rec->crossed = 1;
       } else {
         nx = L.len;
         nv = 0.0f;
+        if (rec) rec->branch = kBrClamp;
       }
     }
     if (hold) d.holder[L.to] = crossed ? -1 : vid;

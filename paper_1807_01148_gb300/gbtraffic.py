@@ -23,7 +23,7 @@ F_ALL = (1 << 9) - 1
 N_KERNELS = 10
 EXPORTS = ["sim_create", "sim_create_batch", "sim_set_stream", "sim_route", "sim_set_routes", "sim_route_size",
            "sim_read_routes", "sim_step", "sim_step_timed", "sim_kernel_name", "sim_read_state", "sim_write_state", "sim_occupancy", "sim_n_lanes",
-           "sim_counters", "sim_last_error", "sim_destroy"]
+           "sim_counters", "sim_last_error", "sim_destroy", "sim_set_class_params", "sim_observe", "sim_adjoint"]
 
 
 class sim_network(C.Structure):
@@ -51,6 +51,11 @@ class sim_params(C.Structure):
 class sim_counters_t(C.Structure):
     _fields_ = [(k, C.c_int64) for k in
                 ("t", "departed", "waiting", "active", "arrived", "veh_steps", "pending", "active_last")]
+
+
+class sim_loss_spec(C.Structure):
+    _fields_ = [("n_steps", C.c_int32), ("obs_every", C.c_int32), ("checkpoint_every", C.c_int32),
+                ("target", C.c_void_p)]
 
 
 class sim_state_view(C.Structure):
@@ -92,6 +97,9 @@ def lib(path: str | None = None):
         L.sim_last_error.restype = C.c_char_p
         L.sim_destroy.argtypes = [vp]
         L.sim_destroy.restype = None
+        L.sim_set_class_params.argtypes = [vp] * 6
+        L.sim_observe.argtypes = [vp, i32, i32, vp]
+        L.sim_adjoint.argtypes = [vp, C.POINTER(sim_loss_spec), vp, vp]
         _lib = L
     return _lib
 
@@ -258,6 +266,24 @@ class Sim:
         self._check(lib().sim_occupancy(self.h, _p(start), _p(vids)))
         return start, vids[: start[-1]]
 
+    def set_class_params(self, v0, T, a, b, s0):
+        arrs = [np.ascontiguousarray(q, np.float32) for q in (v0, T, a, b, s0)]
+        self._check(lib().sim_set_class_params(self.h, *[_p(q) for q in arrs]))
+
+    def observe(self, n_steps, obs_every):
+        out = np.zeros((n_steps // obs_every, self.n_trips), np.float64)
+        self._check(lib().sim_observe(self.h, int(n_steps), int(obs_every), _p(out)))
+        return out
+
+    def adjoint(self, n_steps, obs_every, target, n_class, checkpoint_every=64):
+        """Loss and dL/d(v0, T, a, b, s0) per class from the current state (see sim_adjoint)."""
+        t = np.ascontiguousarray(target, np.float64)
+        spec = sim_loss_spec(int(n_steps), int(obs_every), int(checkpoint_every), t.ctypes.data)
+        g = np.zeros(n_class * 5, np.float64)
+        loss = np.zeros(1, np.float64)
+        self._check(lib().sim_adjoint(self.h, C.byref(spec), _p(g), _p(loss)))
+        return g.reshape(n_class, 5), float(loss[0])
+
     def counters(self):
         c = sim_counters_t()
         self._check(lib().sim_counters(self.h, C.byref(c)))
@@ -274,3 +300,36 @@ def setup(scenario, sim=None):
     if "init_state" in scenario:
         s.write_state(scenario["init_state"])
     return s
+
+
+PARAM_ORDER = ("v0", "T", "a", "b", "s0")
+
+
+def calibration_loss_fn():
+    """torch.autograd.Function for trajectory calibration: loss(theta), theta a
+    [n_class, 5] float64 tensor of (v0, T, a, b, s0) per class.  Forward sets the class
+    parameters, restores the start state and runs sim_adjoint (taped forward pass with
+    checkpoints + binary64 reverse sweep) when a gradient is needed, sim_observe
+    otherwise; backward returns the stored gradient scaled by the incoming one."""
+    import torch
+
+    class CalibrationLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, theta, sim, start_state, target, n_steps, obs_every, checkpoint_every):
+            th = theta.detach().cpu().double().numpy()
+            sim.set_class_params(*[th[:, k] for k in range(5)])
+            sim.write_state(start_state)
+            if theta.requires_grad:
+                g, loss = sim.adjoint(n_steps, obs_every, target, th.shape[0], checkpoint_every)
+                ctx.save_for_backward(torch.from_numpy(g).to(theta.device, theta.dtype))
+            else:
+                p = sim.observe(n_steps, obs_every)
+                loss = float(((p - target) ** 2).sum())
+            return torch.tensor(loss, dtype=theta.dtype, device=theta.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            (g,) = ctx.saved_tensors
+            return gout * g, None, None, None, None, None, None
+
+    return CalibrationLoss
