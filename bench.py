@@ -35,8 +35,8 @@ ALG_BYTES = {
     "rank": 16 + 4 + 28 + 28,        # scatter words; lane start; state gather from A; state write to B
     "own": 24 + 4 + 10,              # x, v, vid, link, nxt, lane; lane end; a_own, xo, flags, intent
     "decide": 13,                    # link, x, xo; intent (eligible vehicles read more, not counted)
-    "move": 28 + 9 + 28 + 1 + 12,    # sorted state; flags, intent, acceleration; next state; decision;
-                                     # next-lane count (read+write) and arrival index
+    "move_insert": 28 + 9 + 28 + 1 + 12,  # sorted state; flags, intent, acceleration; next state; decision;
+                                          # next-lane count (read+write) and arrival index
 }
 
 
@@ -222,6 +222,14 @@ def measure_batched(G, S, torch, steps):
     b = G.Sim.batch(scs)
     b.set_stream(stream.cuda_stream)
     b.route()
+    # block shape / execution mode picked by the autotuner on warm-up steps of a copy
+    tune = G.Sim.batch(scs)
+    tune.set_stream(stream.cuda_stream)
+    tune.route()
+    tune.step(600)
+    choice = tune.autotune(trial_steps=50)
+    tune.close()
+    b.set_exec(**choice)
     torch.cuda.synchronize()
     e0.record(stream)
     b.step(steps)
@@ -246,9 +254,11 @@ def measure_batched(G, S, torch, steps):
     return {"scenarios": len(scs), "steps": steps, "trips": int(sum(s["demand"]["n_trips"] for s in scs)),
             "batched": {"value": vb / tb, "seconds": tb, "veh_steps": vb},
             "sequential": {"value": vs / ts, "seconds": ts, "veh_steps": vs},
-            "ratio": (vb / tb) / (vs / ts), "unit": UNIT,
-            "note": "one handle over the disjoint union (one launch sequence per step for all scenarios) vs "
-                    "64 handles stepped one after another; identical vehicle-steps"}
+            "ratio": (vb / tb) / (vs / ts), "unit": UNIT, "exec": choice,
+            "note": "one handle over the disjoint union of the 64 scenarios, execution configuration chosen by "
+                    "sim_autotune (mode 1 = all steps in one persistent cooperative launch captured as a CUDA "
+                    "graph, mode 0 = one graph of the step kernels per step) vs 64 handles stepped one after "
+                    "another; identical vehicle-steps"}
 
 
 # ---------------------------------------------------------------------------- adjoint
@@ -356,7 +366,7 @@ def run_cuda(args):
     ms = ev0.elapsed_time(ev1)
     c1 = g.counters()
     veh_steps = c1["veh_steps"] - c0["veh_steps"]
-    kernels_per_step = G.N_KERNELS - (0 if int((snap["status"] == 0).sum()) else 1)
+    kernels_per_step = G.N_KERNELS
     clk = clocks.stop()
 
     # -- per-kernel device times over the same K steps (events after every kernel)

@@ -171,7 +171,7 @@ int sim_read_routes(sim_handle* h, int32_t* offsets, int32_t* links);
 int sim_step(sim_handle* h, int32_t n_steps);
 
 /* Number of kernels in one step (see sim_kernel_name). */
-#define SIM_N_KERNELS 10
+#define SIM_N_KERNELS 8
 
 /* Advance n_steps like sim_step, but launch every kernel directly with a CUDA event
  * after each one, and add each kernel's device time (ms, including its launch gap)
@@ -181,6 +181,33 @@ int sim_step_timed(sim_handle* h, int32_t n_steps, float* kernel_ms);
 
 /* Name of kernel k of a step (0 <= k < SIM_N_KERNELS), "" otherwise. */
 const char* sim_kernel_name(int32_t k);
+
+/* How sim_step runs the steps.  SIM_EXEC_GRAPH: one CUDA graph of the step's kernels
+ * per step, grid = grid_per_sm x SMs blocks of 256 threads.  SIM_EXEC_PERSISTENT: all
+ * n steps in one cooperative launch of blocks_per_sm x SMs blocks of `threads`
+ * threads, the phases of a step separated by a grid barrier whose wait is bounded by
+ * barrier_timeout_cycles SM cycles (<= 0: 2e9, about a second); a wait that runs out
+ * makes sim_step return SIM_ETIMEOUT (the state is then undefined until the next
+ * sim_write_state / sim_route).  Every configuration gives identical results. */
+enum { SIM_EXEC_GRAPH = 0, SIM_EXEC_PERSISTENT = 1 };
+typedef struct {
+  int32_t mode;
+  int32_t threads;                  /* persistent: 256, 512 or 1024 */
+  int32_t blocks_per_sm;            /* persistent: 1 .. co-resident limit */
+  int32_t grid_per_sm;              /* graph: 1 .. 64 */
+  int64_t barrier_timeout_cycles;   /* persistent: bound of a barrier wait */
+} sim_exec;
+
+int sim_set_exec(sim_handle* h, const sim_exec* e);
+int sim_get_exec(sim_handle* h, sim_exec* e);
+
+/* Pick the fastest execution configuration for this handle: time trial_steps steps
+ * from the current state under every candidate (graph with 2/4/8/16 blocks per SM;
+ * persistent with 256/512/1024 threads and 1..4 co-resident blocks per SM), restore
+ * the state, and keep the best.  cache_path (or NULL): a JSON-lines file keyed by
+ * device name, SM count and a hash of the network and demand sizes; a hit skips the
+ * trials, a new result is appended.  *chosen (or NULL) receives the choice. */
+int sim_autotune(sim_handle* h, int32_t trial_steps, const char* cache_path, sim_exec* chosen);
 
 /* Read the per-trip state (fields = OR of SIM_F_*).  on_device = 1: the view's
  * pointers are device pointers (e.g. from torch tensors) of n_trips elements each;

@@ -29,6 +29,9 @@ void launch_tape_begin(const Dev& d, cudaStream_t s);
 void launch_adj_step(const Dev& d, int grid, cudaStream_t s, const TapeRec* slab, const double* lx,
                      const double* lv, const double* res, double* nx, double* nv, double* grad, int n_class);
 void launch_first_links(const int32_t* roff, const int32_t* routes, int n, int32_t* out, cudaStream_t s);
+int persistent_max_blocks_per_sm(int threads);
+cudaError_t launch_persistent(const Dev& d, GridSync* gs, int blocks, int threads, int n_steps, long long limit,
+                              cudaStream_t s);
 }  // namespace gbt
 
 using namespace gbt;
@@ -72,6 +75,15 @@ struct sim_handle {
   cudaGraphExec_t gexec_tape = nullptr;
   cudaGraph_t graph_tape = nullptr;
   bool tape_graph_dirty = true;
+  // execution configuration of sim_step
+  sim_exec exec{SIM_EXEC_GRAPH, 256, 0, 8, 0};
+  GridSync* gs = nullptr;
+  // the persistent launch captured as a graph (for one step count at a time)
+  cudaGraphExec_t pexec = nullptr;
+  cudaGraph_t pgraph = nullptr;
+  int pgraph_n = -1;
+  sim_exec pgraph_cfg{};
+  bool pgraph_unsupported = false;
 };
 
 namespace {
@@ -385,11 +397,12 @@ int create_from_flat(Flat& F, sim_handle** out) {
     TRY(dalloc(h, &d.holder, (size_t)F.nn));
     TRY(dalloc(h, &d.acq, (size_t)F.nn));
     TRY(dalloc(h, &d.ctl, 1));
+    TRY(dalloc(h, &h->gs, 1));
     if (cudaMemset(d.cnt, 0, (size_t)nlan * 4) != cudaSuccess ||
         cudaMemset(d.best, 0xFF, (size_t)nlan * 8) != cudaSuccess ||
         cudaMemset(d.acq, 0xFF, (size_t)F.nn * 8) != cudaSuccess ||
         cudaMemset(d.holder, 0xFF, (size_t)F.nn * 4) != cudaSuccess ||
-        cudaMemset(d.ctl, 0, sizeof(Ctl)) != cudaSuccess ||
+        cudaMemset(d.ctl, 0, sizeof(Ctl)) != cudaSuccess || cudaMemset(h->gs, 0, sizeof(GridSync)) != cudaSuccess ||
         cudaMemset(d.A.link, 0xFF, nt ? nt * 4 : 4) != cudaSuccess ||
         cudaMemset(d.status, 0, nt ? nt : 1) != cudaSuccess) {
       rc = fail(h, SIM_ECUDA, "initial cudaMemset failed");
@@ -461,6 +474,7 @@ int build_queues(sim_handle* h, const std::vector<uint8_t>& status) {
   h->d.qlinks = h->qlinks;
   h->d.n_qlinks = (int)ql.size();
   h->graph_dirty = true;
+  h->pgraph_n = -1;
   h->tape_graph_dirty = true;
   return SIM_OK;
 }
@@ -498,7 +512,11 @@ int check_device(sim_handle* h) {
   if (c.err) {
     char buf[160];
     snprintf(buf, sizeof buf, "device error word 0x%x (info %d) at step %lld", c.err, c.err_info, c.t);
-    return fail(h, SIM_EDEVICE, buf);
+    const int code = (c.err & kErrTimeout) ? SIM_ETIMEOUT : SIM_EDEVICE;
+    // clear the word so that the handle stays usable after the caller resets the state
+    CK(cudaMemsetAsync(&h->d.ctl->err, 0, sizeof(int), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return fail(h, code, buf);
   }
   return SIM_OK;
 }
@@ -705,6 +723,7 @@ int sim_route(sim_handle* h, const int32_t* link_cost_ds) {
   CK(cudaStreamSynchronize(h->stream));
   h->routed = true;
   h->graph_dirty = true;
+  h->pgraph_n = -1;
   return SIM_OK;
 }
 
@@ -745,6 +764,7 @@ int sim_set_routes(sim_handle* h, const int32_t* offsets, const int32_t* links) 
   CK(cudaStreamSynchronize(h->stream));
   h->routed = true;
   h->graph_dirty = true;
+  h->pgraph_n = -1;
   return SIM_OK;
 }
 
@@ -793,8 +813,73 @@ int sim_step(sim_handle* h, int32_t n_steps) {
     CK(cudaGraphInstantiate(&h->gexec, h->graph, 0));
     h->graph_dirty = false;
   }
-  for (int s = 0; s < n_steps; s++) CK(cudaGraphLaunch(h->gexec, h->stream));
+  if (h->exec.mode == SIM_EXEC_PERSISTENT) {
+    const int blocks = h->exec.blocks_per_sm * h->sm_count;
+    const long long limit = h->exec.barrier_timeout_cycles > 0 ? h->exec.barrier_timeout_cycles : 2000000000LL;
+    const sim_exec& x = h->exec;
+    const bool same = h->pexec && h->pgraph_n == n_steps && h->pgraph_cfg.threads == x.threads &&
+                      h->pgraph_cfg.blocks_per_sm == x.blocks_per_sm &&
+                      h->pgraph_cfg.barrier_timeout_cycles == x.barrier_timeout_cycles;
+    if (!same && !h->pgraph_unsupported) {
+      // capture the single persistent launch as a graph (rebuilt when the step count or
+      // the configuration changes); direct launch where capture is not available
+      if (h->pexec) cudaGraphExecDestroy(h->pexec);
+      if (h->pgraph) cudaGraphDestroy(h->pgraph);
+      h->pexec = nullptr;
+      h->pgraph = nullptr;
+      bool ok = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        cudaError_t le = launch_persistent(h->d, h->gs, blocks, x.threads, n_steps, limit, h->cap_stream);
+        cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &h->pgraph);
+        ok = le == cudaSuccess && ce == cudaSuccess && h->pgraph &&
+             cudaGraphInstantiate(&h->pexec, h->pgraph, 0) == cudaSuccess;
+      }
+      if (!ok) {
+        cudaGetLastError();
+        if (h->pgraph) cudaGraphDestroy(h->pgraph);
+        h->pgraph = nullptr;
+        h->pexec = nullptr;
+        h->pgraph_unsupported = true;
+      } else {
+        h->pgraph_n = n_steps;
+        h->pgraph_cfg = x;
+      }
+    }
+    if (h->pexec) CK(cudaGraphLaunch(h->pexec, h->stream));
+    else CK(launch_persistent(h->d, h->gs, blocks, x.threads, n_steps, limit, h->stream));
+  } else {
+    for (int s = 0; s < n_steps; s++) CK(cudaGraphLaunch(h->gexec, h->stream));
+  }
   return check_device(h);
+}
+
+int sim_set_exec(sim_handle* h, const sim_exec* e) {
+  if (!h || !e) return SIM_EINVAL;
+  sim_exec x = *e;
+  if (x.mode == SIM_EXEC_GRAPH) {
+    if (x.grid_per_sm < 1 || x.grid_per_sm > 64) return fail(h, SIM_EINVAL, "grid_per_sm must be 1..64");
+    h->grid = x.grid_per_sm * h->sm_count;
+    h->graph_dirty = true;
+  h->pgraph_n = -1;
+    h->tape_graph_dirty = true;
+  } else if (x.mode == SIM_EXEC_PERSISTENT) {
+    if (x.threads != 256 && x.threads != 512 && x.threads != 1024)
+      return fail(h, SIM_EINVAL, "persistent threads must be 256, 512 or 1024");
+    const int mx = persistent_max_blocks_per_sm(x.threads);
+    if (mx < 1) return fail(h, SIM_EINVAL, "the persistent kernel does not fit this block size");
+    if (x.blocks_per_sm < 1 || x.blocks_per_sm > mx)
+      return fail(h, SIM_EINVAL, "blocks_per_sm exceeds the co-resident limit of the persistent kernel");
+  } else {
+    return fail(h, SIM_EINVAL, "unknown execution mode");
+  }
+  h->exec = x;
+  return SIM_OK;
+}
+
+int sim_get_exec(sim_handle* h, sim_exec* e) {
+  if (!h || !e) return SIM_EINVAL;
+  *e = h->exec;
+  return SIM_OK;
 }
 
 int sim_step_timed(sim_handle* h, int32_t n_steps, float* kernel_ms) {
@@ -1157,6 +1242,127 @@ int sim_adjoint(sim_handle* h, const sim_loss_spec* spec, double* grad_out, doub
   return check_device(h);
 }
 
+// ---------------------------------------------------------------- autotuner
+namespace {
+
+std::string tune_key(const sim_handle* h) {
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, h->device);
+  unsigned long long hsh = 1469598103934665603ULL;
+  auto mix = [&](unsigned long long v) {
+    hsh ^= v;
+    hsh *= 1099511628211ULL;
+  };
+  mix((unsigned long long)h->nn);
+  mix((unsigned long long)h->nl);
+  mix((unsigned long long)h->nt);
+  mix((unsigned long long)h->n_lanes);
+  mix((unsigned long long)h->has_stop);
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s|sm%d|%016llx", prop.name, h->sm_count, hsh);
+  return buf;
+}
+
+bool tune_cache_lookup(const char* path, const std::string& key, sim_exec* out) {
+  if (!path) return false;
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  char line[512];
+  bool found = false;
+  while (fgets(line, sizeof line, f)) {
+    char k[300];
+    sim_exec e{};
+    long long lim = 0;
+    if (sscanf(line, "{\"key\": \"%299[^\"]\", \"mode\": %d, \"threads\": %d, \"blocks_per_sm\": %d, "
+                     "\"grid_per_sm\": %d, \"barrier_timeout_cycles\": %lld",
+               k, &e.mode, &e.threads, &e.blocks_per_sm, &e.grid_per_sm, &lim) == 6 &&
+        key == k) {
+      e.barrier_timeout_cycles = lim;
+      *out = e;
+      found = true;
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+void tune_cache_store(const char* path, const std::string& key, const sim_exec& e, double us) {
+  if (!path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f,
+          "{\"key\": \"%s\", \"mode\": %d, \"threads\": %d, \"blocks_per_sm\": %d, \"grid_per_sm\": %d, "
+          "\"barrier_timeout_cycles\": %lld, \"us_per_step\": %.3f}\n",
+          key.c_str(), e.mode, e.threads, e.blocks_per_sm, e.grid_per_sm, (long long)e.barrier_timeout_cycles, us);
+  fclose(f);
+}
+
+}  // namespace
+
+int sim_autotune(sim_handle* h, int32_t trial_steps, const char* cache_path, sim_exec* chosen) {
+  if (!h || trial_steps < 1) return SIM_EINVAL;
+  if (!h->routed) return fail(h, SIM_ESTATE, "sim_autotune before routes exist");
+  const std::string key = tune_key(h);
+  sim_exec best{};
+  if (tune_cache_lookup(cache_path, key, &best) && sim_set_exec(h, &best) == SIM_OK) {
+    if (chosen) *chosen = h->exec;
+    return SIM_OK;
+  }
+  if (int rc = check_horizon(h, trial_steps * 40)) return rc;
+  // candidates; every one gives the same results, only the time differs
+  std::vector<sim_exec> cand;
+  for (int g : {2, 4, 8, 16}) cand.push_back(sim_exec{SIM_EXEC_GRAPH, 256, 0, g, 0});
+  for (int t : {256, 512, 1024}) {
+    const int mx = persistent_max_blocks_per_sm(t);
+    for (int b = 1; b <= mx && b <= 4; b++) cand.push_back(sim_exec{SIM_EXEC_PERSISTENT, t, b, 8, 0});
+  }
+  const CkptLayout CL = ckpt_layout(h);
+  unsigned char* ck;
+  int rc = dalloc(h, &ck, CL.bytes);
+  if (rc) return rc;
+  const sim_exec orig = h->exec;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaError_t err = ckpt_copy(h, ck, true);
+  double best_us = 1e30;
+  for (const sim_exec& c : cand) {
+    if (err != cudaSuccess) break;
+    if (sim_set_exec(h, &c) != SIM_OK) continue;
+    err = ckpt_copy(h, ck, false);
+    if (err != cudaSuccess) break;
+    if ((rc = sim_step(h, 1))) break;   // warm-up (builds the graph)
+    err = ckpt_copy(h, ck, false);
+    if (err != cudaSuccess) break;
+    cudaEventRecord(e0, h->stream);
+    if ((rc = sim_step(h, trial_steps))) break;
+    cudaEventRecord(e1, h->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double us = 1e3 * ms / trial_steps;
+    if (us < best_us) {
+      best_us = us;
+      best = c;
+    }
+  }
+  if (err == cudaSuccess && !rc) err = ckpt_copy(h, ck, false);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  dfree(h, ck);
+  if (rc) {
+    sim_set_exec(h, &orig);
+    return rc;
+  }
+  if (err != cudaSuccess) return cuda_fail(h, err, "autotune");
+  if (best_us >= 1e30) return fail(h, SIM_ECUDA, "no execution configuration ran");
+  if ((rc = sim_set_exec(h, &best))) return rc;
+  tune_cache_store(cache_path, key, best, best_us);
+  if (chosen) *chosen = best;
+  return SIM_OK;
+}
+
 const char* sim_last_error(const sim_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
 void sim_destroy(sim_handle* h) {
@@ -1165,6 +1371,8 @@ void sim_destroy(sim_handle* h) {
   if (h->graph) cudaGraphDestroy(h->graph);
   if (h->gexec_tape) cudaGraphExecDestroy(h->gexec_tape);
   if (h->graph_tape) cudaGraphDestroy(h->graph_tape);
+  if (h->pexec) cudaGraphExecDestroy(h->pexec);
+  if (h->pgraph) cudaGraphDestroy(h->pgraph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (void* p : h->allocs) cudaFree(p);
   delete h;

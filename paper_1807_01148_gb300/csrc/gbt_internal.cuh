@@ -20,7 +20,13 @@ constexpr int kTurnThrough = 0, kTurnLeft = 1, kTurnRight = 2;
 
 // error word bits (device -> host)
 constexpr int kErrLane = 1, kErrLink = 2, kErrSlot = 4, kErrRoute = 8, kErrUnreach = 16,
-              kErrRouteCap = 32, kErrQueue = 64;
+              kErrRouteCap = 32, kErrQueue = 64, kErrTimeout = 128;
+
+// Grid barrier of the persistent step kernel (one per handle, in device memory).
+struct GridSync {
+  unsigned count;
+  unsigned gen;
+};
 
 // Per-link record, 32 bytes: everything a vehicle step needs about its link and
 // the node at its end, in one aligned load.
@@ -182,8 +188,7 @@ struct RouteDev {
 void launch_route(const RouteDev& R, int n_cta, cudaStream_t s);
 
 // kernels of one step, in launch order
-enum { kKScanSum, kKScanTop, kKScanFin, kKScatter, kKRank, kKOwn, kKDecide, kKMove, kKInsert, kKFinish,
-       kNumKernels };
+enum { kKScanSum, kKScanFin, kKScatter, kKRank, kKOwn, kKDecide, kKMoveInsert, kKFinish, kNumKernels };
 extern const char* const kKernelNames[kNumKernels];
 
 constexpr uint8_t kFlagFront = 1, kFlagHolder = 2, kFlagCand = 4;

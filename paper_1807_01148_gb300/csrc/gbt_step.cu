@@ -63,62 +63,72 @@ __device__ __forceinline__ int block_excl_scan(int val, int* smem_warp, int& tot
   return res;
 }
 
-__global__ void k_scan_sum(Dev d) {
-  __shared__ int sw[33];
-  int base = blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
-  int s = 0;
-#pragma unroll
-  for (int k = 0; k < kScanItems; k++) {
-    int i = base + k;
-    if (i < d.n_lanes) s += d.cnt[i];
-  }
-  int tot;
-  block_excl_scan(s, sw, tot);
-  if (threadIdx.x == 0) d.bsum[blockIdx.x] = tot;
-}
+int scan_blocks(int n_lanes) { return (n_lanes + kScanChunk - 1) / kScanChunk; }
 
-__global__ void k_scan_top(Dev d, int nblocks) {
+// Per-chunk sums of the lane counts (chunks of kScanChunk lanes, one per block pass).
+__device__ __forceinline__ void ph_scan_sum(const Dev& d) {
   __shared__ int sw[33];
-  int carry = 0;
-  for (int b0 = 0; b0 < nblocks; b0 += blockDim.x) {
-    int i = b0 + threadIdx.x;
-    int v = i < nblocks ? d.bsum[i] : 0;
-    int tot;
-    int ex = block_excl_scan(v, sw, tot);
-    if (i < nblocks) d.bsum[i] = carry + ex;
-    carry += tot;
-  }
-  if (threadIdx.x == 0) {
-    d.ctl->nB = carry;
-    d.lane_start[d.n_lanes] = carry;
-  }
-}
-
-__global__ void k_scan_fin(Dev d) {
-  __shared__ int sw[33];
-  int base = blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
-  int v[kScanItems];
-  int s = 0;
+  const int nb = (d.n_lanes + kScanChunk - 1) / kScanChunk;
+  for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+    int base = b * kScanChunk + threadIdx.x * kScanItems;
+    int s = 0;
 #pragma unroll
-  for (int k = 0; k < kScanItems; k++) {
-    int i = base + k;
-    v[k] = i < d.n_lanes ? d.cnt[i] : 0;
-    s += v[k];
-  }
-  int tot;
-  int ex = block_excl_scan(s, sw, tot) + d.bsum[blockIdx.x];
-#pragma unroll
-  for (int k = 0; k < kScanItems; k++) {
-    int i = base + k;
-    if (i < d.n_lanes) {
-      d.lane_start[i] = ex;
-      d.cnt[i] = 0;
+    for (int k = 0; k < kScanItems; k++) {
+      int i = base + k;
+      if (i < d.n_lanes && threadIdx.x < kScanThreads) s += d.cnt[i];
     }
-    ex += v[k];
+    int tot;
+    block_excl_scan(threadIdx.x < kScanThreads ? s : 0, sw, tot);
+    if (threadIdx.x == 0) d.bsum[b] = tot;
   }
 }
 
-__global__ void k_scatter(Dev d) {
+__global__ void k_scan_sum(Dev d) { ph_scan_sum(d); }
+
+
+// Lane starts = chunk offset + exclusive scan inside the chunk; counts reset to zero.
+// Each block sums the chunk totals before its chunk itself (a few hundred at most), so
+// no separate pass over the chunk totals is needed; the block of the last chunk
+// writes the total (the number of vehicles in the sorted buffer).
+__device__ __forceinline__ void ph_scan_fin(const Dev& d) {
+  __shared__ int sw[33];
+  const int nb = (d.n_lanes + kScanChunk - 1) / kScanChunk;
+  for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+    int before = 0;
+    for (int i = threadIdx.x; i < b; i += blockDim.x) before += d.bsum[i];
+    int tot_before;
+    block_excl_scan(before, sw, tot_before);
+    int base = b * kScanChunk + threadIdx.x * kScanItems;
+    const bool lanes_of_thread = threadIdx.x < kScanThreads;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+      int i = base + k;
+      v[k] = (lanes_of_thread && i < d.n_lanes) ? d.cnt[i] : 0;
+      s += v[k];
+    }
+    int tot;
+    int ex = block_excl_scan(s, sw, tot) + tot_before;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+      int i = base + k;
+      if (lanes_of_thread && i < d.n_lanes) {
+        d.lane_start[i] = ex;
+        d.cnt[i] = 0;
+      }
+      ex += v[k];
+    }
+    if (b == nb - 1 && threadIdx.x == 0) {
+      d.ctl->nB = tot_before + tot;
+      d.lane_start[d.n_lanes] = tot_before + tot;
+    }
+  }
+}
+
+__global__ void k_scan_fin(Dev d) { ph_scan_fin(d); }
+
+__device__ __forceinline__ void ph_scatter(const Dev& d) {
   const int nA = d.ctl->nA;
   GRID_STRIDE(s, nA) {
     int e = d.A.link[s];
@@ -132,12 +142,14 @@ __global__ void k_scatter(Dev d) {
   }
 }
 
+__global__ void k_scatter(Dev d) { ph_scatter(d); }
+
 // Rank of each vehicle inside its lane segment by (x, vid); the vehicle's state
 // moves from its slot in A to position lane_start + rank in B.  The vehicle that
 // lands last in its segment is the lane's front: if its link ends at a free stop-
 // controlled node, it bids for the node here (Sec. 6.3.2 stop signs, one vehicle at
 // a time): the bid with the smallest (round-robin rank of its link, lane) acquires it.
-__global__ void k_rank(Dev d) {
+__device__ __forceinline__ void ph_rank(const Dev& d) {
   const int nB = d.ctl->nB;
   const int t = (int)d.ctl->t;
   GRID_STRIDE(p, nB) {
@@ -167,6 +179,8 @@ __global__ void k_rank(Dev d) {
     }
   }
 }
+
+__global__ void k_rank(Dev d) { ph_rank(d); }
 
 // ------------------------------------------------------------------ neighbours / IDM
 __device__ __forceinline__ bool is_holder(const Dev& d, const LinkRec& L, int t, int vid, int lane,
@@ -222,7 +236,7 @@ __device__ __forceinline__ TapeRec* tape_slot(const Dev& d, int t, int vid) {
   return d.tape + (size_t)(t - (int)d.ctl->tape_t0) * (size_t)d.n_trips + (size_t)vid;
 }
 
-__global__ void k_own(Dev d) {
+__device__ __forceinline__ void ph_own(const Dev& d) {
   const int nB = d.ctl->nB;
   const int t = (int)d.ctl->t;
   GRID_STRIDE(p, nB) {
@@ -290,6 +304,8 @@ __global__ void k_own(Dev d) {
   }
 }
 
+__global__ void k_own(Dev d) { ph_own(d); }
+
 // First position q in [s0, s1) whose (x, vid) exceeds (x, vid) of the probe.
 __device__ __forceinline__ int upper_pos(const Dev& d, int s0, int s1, float x, int vid) {
   int lo = s0, hi = s1;
@@ -307,7 +323,7 @@ __device__ __forceinline__ int upper_pos(const Dev& d, int s0, int s1, float x, 
 // Helbing 2007) for discretionary changes, mandatory changes toward the lanes of
 // the next movement once within the drawn switch distance, and gap acceptance =
 // no overlap and both the changer's and the new follower's accelerations >= -b_safe.
-__global__ void __launch_bounds__(256, 4) k_decide(Dev d) {
+__device__ __forceinline__ void ph_decide(const Dev& d) {
   const int ne = d.ctl->n_elig;
   const int t = (int)d.ctl->t;
   GRID_STRIDE(i, ne) {
@@ -405,8 +421,10 @@ __global__ void __launch_bounds__(256, 4) k_decide(Dev d) {
   }
 }
 
+__global__ void __launch_bounds__(256, 4) k_decide(Dev d) { ph_decide(d); }
+
 // ------------------------------------------------------------------ move
-__global__ void k_move(Dev d) {
+__device__ __forceinline__ void ph_move(const Dev& d) {
   const int nB = d.ctl->nB;
   const int t = (int)d.ctl->t;
   GRID_STRIDE(p, nB) {
@@ -503,11 +521,12 @@ __global__ void k_move(Dev d) {
   }
 }
 
+
 // ------------------------------------------------------------------ departures
 // The head of each link's queue of due trips enters at x = 0, v = 0 in the allowed
 // lane with the largest rear space (ties to the lowest lane) that received no
 // vehicle from upstream in this step, if that space is at least s0 + vehicle length.
-__global__ void k_insert(Dev d) {
+__device__ __forceinline__ void ph_insert(const Dev& d) {
   const int nq = d.n_qlinks;
   const int t = (int)d.ctl->t;
   const int nB = d.ctl->nB;
@@ -553,7 +572,15 @@ __global__ void k_insert(Dev d) {
   }
 }
 
-__global__ void k_finish(Dev d) {
+
+// Move and departures touch disjoint slots of buffer A (departures append after the
+// sorted vehicles) and read only state of step t, so they share one launch.
+__global__ void k_move_insert(Dev d) {
+  ph_move(d);
+  if (d.n_qlinks > 0) ph_insert(d);
+}
+
+__device__ __forceinline__ void ph_finish(const Dev& d) {
   Ctl* c = d.ctl;
   c->veh_steps += (unsigned long long)c->nB;
   c->departed += (unsigned long long)c->n_ins;
@@ -566,9 +593,9 @@ __global__ void k_finish(Dev d) {
   c->t += 1;
 }
 
-// ------------------------------------------------------------------ launch sequence
-int scan_blocks(int n_lanes) { return (n_lanes + kScanChunk - 1) / kScanChunk; }
+__global__ void k_finish(Dev d) { ph_finish(d); }
 
+// ------------------------------------------------------------------ launch sequence
 void launch_kernel(int k, const Dev& d, int grid, cudaStream_t s);
 void launch_count(const Dev& d, int grid, cudaStream_t s);
 
@@ -582,12 +609,13 @@ void launch_occupancy(const Dev& d, int grid, cudaStream_t s) {
 // Kernels of one step, in launch order (names reported by the timed step).  The
 // lane counts the scan starts from are made by the previous step's move and insert
 // kernels (or by k_count after a state is loaded).
-const char* const kKernelNames[kNumKernels] = {"scan_sum", "scan_top", "scan_fin", "scatter", "rank",
-                                               "own", "decide", "move", "insert", "finish"};
+const char* const kKernelNames[kNumKernels] = {"scan_sum", "scan_fin", "scatter", "rank", "own", "decide",
+                                               "move_insert", "finish"};
 
 bool kernel_enabled(int k, const Dev& d, bool has_stop) {
+  (void)k;
+  (void)d;
   (void)has_stop;
-  if (k == kKInsert) return d.n_qlinks > 0;
   return true;
 }
 
@@ -595,18 +623,12 @@ void launch_kernel(int k, const Dev& d, int grid, cudaStream_t s) {
   const int nb = scan_blocks(d.n_lanes);
   switch (k) {
     case kKScanSum: k_scan_sum<<<nb, kScanThreads, 0, s>>>(d); break;
-    case kKScanTop: k_scan_top<<<1, 1024, 0, s>>>(d, nb); break;
     case kKScanFin: k_scan_fin<<<nb, kScanThreads, 0, s>>>(d); break;
     case kKScatter: k_scatter<<<grid, 256, 0, s>>>(d); break;
     case kKRank: k_rank<<<grid, 256, 0, s>>>(d); break;
     case kKOwn: k_own<<<grid, 256, 0, s>>>(d); break;
     case kKDecide: k_decide<<<grid, 256, 0, s>>>(d); break;
-    case kKMove: k_move<<<grid, 256, 0, s>>>(d); break;
-    case kKInsert: {
-      int g = (d.n_qlinks + 255) / 256;
-      k_insert<<<g < grid ? g : grid, 256, 0, s>>>(d);
-      break;
-    }
+    case kKMoveInsert: k_move_insert<<<grid, 256, 0, s>>>(d); break;
     case kKFinish: k_finish<<<1, 1, 0, s>>>(d); break;
     default: break;
   }
@@ -645,6 +667,83 @@ cudaError_t launch_steps_timed(const Dev& d, int grid, bool has_stop, cudaStream
   }
   for (int k = 0; k <= kNumKernels; k++) cudaEventDestroy(ev[k]);
   return err;
+}
+
+// ------------------------------------------------------------------ persistent step
+// All phases of n steps in one cooperative launch: every block runs each phase's
+// grid-stride share, then waits at a grid barrier.  The barrier's wait is bounded:
+// after `limit` SM cycles (about a second by default) a block sets kErrTimeout in the
+// error word and leaves; every waiting block also leaves as soon as it sees the flag,
+// so the launch always ends and the host reports SIM_ETIMEOUT.
+__device__ __forceinline__ bool grid_barrier(GridSync* gs, int* err, long long limit) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned* vgen = &gs->gen;
+    volatile int* verr = err;
+    const unsigned g = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&gs->count, 1u);
+    if (arrived == gridDim.x - 1) {
+      gs->count = 0;
+      __threadfence();
+      atomicAdd(&gs->gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == g) {
+        if ((*verr & kErrTimeout) || clock64() - t0 > limit) {
+          atomicOr(err, kErrTimeout);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    if (*verr & kErrTimeout) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__global__ void k_persistent(Dev d, GridSync* gs, int n_steps, long long limit) {
+  int* err = &d.ctl->err;
+  for (int step = 0; step < n_steps; step++) {
+    // the previous step's counter update (block 0) needs no barrier of its own: nothing
+    // before this step's scatter reads what it writes
+    ph_scan_sum(d);
+    if (!grid_barrier(gs, err, limit)) return;
+    ph_scan_fin(d);
+    if (!grid_barrier(gs, err, limit)) return;
+    ph_scatter(d);
+    if (!grid_barrier(gs, err, limit)) return;
+    ph_rank(d);
+    if (!grid_barrier(gs, err, limit)) return;
+    ph_own(d);
+    if (!grid_barrier(gs, err, limit)) return;
+    ph_decide(d);
+    if (!grid_barrier(gs, err, limit)) return;
+    ph_move(d);
+    if (d.n_qlinks > 0) ph_insert(d);
+    if (!grid_barrier(gs, err, limit)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ph_finish(d);
+  }
+  // the last counter update must be visible when the launch ends (it is: kernel end)
+}
+
+// Largest co-resident grid of the persistent kernel for a block size (0 if none).
+int persistent_max_blocks_per_sm(int threads) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent, threads, 0) != cudaSuccess) return 0;
+  return nb;
+}
+
+cudaError_t launch_persistent(const Dev& d, GridSync* gs, int blocks, int threads, int n_steps, long long limit,
+                              cudaStream_t s) {
+  Dev dd = d;
+  void* args[] = {&dd, &gs, &n_steps, &limit};
+  return cudaLaunchCooperativeKernel((const void*)k_persistent, dim3(blocks), dim3(threads), args, 0, s);
 }
 
 // ------------------------------------------------------------------ state I/O kernels

@@ -20,10 +20,12 @@ ERR_NAMES = {0: "SIM_OK", -1: "SIM_EINVAL", -2: "SIM_ENOMEM", -3: "SIM_ECUDA", -
 F_STATUS, F_LINK, F_LANE, F_CURSOR, F_X, F_V, F_INSERT, F_ARRIVE, F_LANECHANGE = (1 << k for k in range(9))
 F_ALL = (1 << 9) - 1
 
-N_KERNELS = 10
+N_KERNELS = 8
 EXPORTS = ["sim_create", "sim_create_batch", "sim_set_stream", "sim_route", "sim_set_routes", "sim_route_size",
            "sim_read_routes", "sim_step", "sim_step_timed", "sim_kernel_name", "sim_read_state", "sim_write_state", "sim_occupancy", "sim_n_lanes",
-           "sim_counters", "sim_last_error", "sim_destroy", "sim_set_class_params", "sim_observe", "sim_adjoint"]
+           "sim_counters", "sim_last_error", "sim_destroy", "sim_set_class_params", "sim_observe", "sim_adjoint",
+           "sim_set_exec", "sim_get_exec", "sim_autotune"]
+SIM_EXEC_GRAPH, SIM_EXEC_PERSISTENT = 0, 1
 
 
 class sim_network(C.Structure):
@@ -51,6 +53,14 @@ class sim_params(C.Structure):
 class sim_counters_t(C.Structure):
     _fields_ = [(k, C.c_int64) for k in
                 ("t", "departed", "waiting", "active", "arrived", "veh_steps", "pending", "active_last")]
+
+
+class sim_exec(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("threads", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("grid_per_sm", C.c_int32), ("barrier_timeout_cycles", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class sim_loss_spec(C.Structure):
@@ -100,6 +110,9 @@ def lib(path: str | None = None):
         L.sim_set_class_params.argtypes = [vp] * 6
         L.sim_observe.argtypes = [vp, i32, i32, vp]
         L.sim_adjoint.argtypes = [vp, C.POINTER(sim_loss_spec), vp, vp]
+        L.sim_set_exec.argtypes = [vp, C.POINTER(sim_exec)]
+        L.sim_get_exec.argtypes = [vp, C.POINTER(sim_exec)]
+        L.sim_autotune.argtypes = [vp, i32, C.c_char_p, C.POINTER(sim_exec)]
         _lib = L
     return _lib
 
@@ -283,6 +296,22 @@ class Sim:
         loss = np.zeros(1, np.float64)
         self._check(lib().sim_adjoint(self.h, C.byref(spec), _p(g), _p(loss)))
         return g.reshape(n_class, 5), float(loss[0])
+
+    def set_exec(self, mode=SIM_EXEC_GRAPH, threads=256, blocks_per_sm=1, grid_per_sm=8,
+                 barrier_timeout_cycles=0):
+        e = sim_exec(mode, threads, blocks_per_sm, grid_per_sm, barrier_timeout_cycles)
+        self._check(lib().sim_set_exec(self.h, C.byref(e)))
+
+    def get_exec(self):
+        e = sim_exec()
+        self._check(lib().sim_get_exec(self.h, C.byref(e)))
+        return e.as_dict()
+
+    def autotune(self, trial_steps=20, cache_path=None):
+        e = sim_exec()
+        self._check(lib().sim_autotune(self.h, int(trial_steps),
+                                       cache_path.encode() if cache_path else None, C.byref(e)))
+        return e.as_dict()
 
     def counters(self):
         c = sim_counters_t()

@@ -1,0 +1,93 @@
+"""Execution configurations of sim_step: the CUDA-graph path with several grid sizes
+and the single persistent cooperative launch with several block shapes must give
+bit-identical results (checked against the oracle); the autotuner picks among them
+and caches its choice; a barrier wait that runs out returns SIM_ETIMEOUT and leaves
+the handle usable."""
+import json
+
+import numpy as np
+import pytest
+
+from paper_1807_01148_gb300 import scenarios as S
+
+from .parity import diff_state, run_lockstep, setup_pair
+
+pytestmark = pytest.mark.gpu
+
+CONFIGS = [dict(mode=0, grid_per_sm=2), dict(mode=0, grid_per_sm=16), dict(mode=1, threads=256, blocks_per_sm=1),
+           dict(mode=1, threads=256, blocks_per_sm=2), dict(mode=1, threads=512, blocks_per_sm=1),
+           dict(mode=1, threads=1024, blocks_per_sm=1)]
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_1807_01148_gb300 import gbtraffic
+    return gbtraffic
+
+
+@pytest.mark.parametrize("cfg", CONFIGS, ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
+def test_persistent_and_graph_configs_bitexact(G, cfg):
+    import oracle
+    sc = S.small_metro()
+    g, o = setup_pair(sc, G.Sim, oracle.OracleSim)
+    try:
+        g.set_exec(**cfg)
+    except G.SimError:
+        pytest.skip("configuration does not fit this device")
+    run_lockstep(g, o, 1200, 150)
+
+
+def test_batched_ensemble_persistent_equals_graph(G):
+    scs = [S.small_grid(n=n, n_trips=100 * n, steps=500, seed=2000 + n, window_steps=400) for n in (4, 7, 5, 9)]
+    a = G.Sim.batch(scs)
+    a.route()
+    b = G.Sim.batch(scs)
+    b.route()
+    b.set_exec(mode=1, threads=256, blocks_per_sm=1)
+    for _ in range(5):
+        a.step(100)
+        b.step(100)
+        d = diff_state(a.state(), b.state())
+        assert not d, d
+
+
+def test_autotune_choice_and_cache(G, tmp_path):
+    scs = [S.small_grid(n=n, n_trips=150 * n, steps=400, seed=3000 + n) for n in (5, 8)]
+    cache = str(tmp_path / "tune.jsonl")
+    a = G.Sim.batch(scs)
+    a.route()
+    a.step(50)
+    ref = G.Sim.batch(scs)
+    ref.route()
+    ref.step(50)
+    choice = a.autotune(trial_steps=10, cache_path=cache)
+    assert choice["mode"] in (0, 1)
+    # the trials left the state where it was
+    assert not diff_state(a.state(), ref.state())
+    a.step(200)
+    ref.step(200)
+    assert not diff_state(a.state(), ref.state())
+    lines = [json.loads(x) for x in open(cache)]
+    assert len(lines) == 1 and lines[0]["mode"] == choice["mode"]
+    b = G.Sim.batch(scs)
+    b.route()
+    assert b.autotune(trial_steps=10, cache_path=cache) == choice      # cache hit
+    assert len(open(cache).readlines()) == 1
+
+
+def test_barrier_timeout_returns_error_and_handle_recovers(G):
+    sc = S.small_grid(n=6, n_trips=400, steps=300)
+    g = G.Sim(sc)
+    g.route()
+    g.step(50)
+    g.set_exec(mode=1, threads=256, blocks_per_sm=1, barrier_timeout_cycles=1)
+    with pytest.raises(G.SimError) as e:
+        g.step(5)
+    assert e.value.code == G.SIM_ETIMEOUT
+    # back to a sane configuration: reset the state and step again
+    g.set_exec(mode=0, grid_per_sm=8)
+    n = sc["demand"]["n_trips"]
+    g.write_state(dict(status=np.zeros(n, np.uint8), link=np.zeros(n, np.int32), lane=np.zeros(n, np.int32),
+                       cursor=np.zeros(n, np.int32), x=np.zeros(n, np.float32), v=np.zeros(n, np.float32)))
+    g.step(100)
+    assert g.counters()["t"] == 100
