@@ -378,6 +378,7 @@ int create_from_flat(Flat& F, sim_handle** out) {
       TRY(dalloc(h, &b->nxt, nt));
       TRY(dalloc(h, &b->cur, nt));
       TRY(dalloc(h, &b->lane, nt));
+      TRY(dalloc(h, &b->gid, nt));
     }
     TRY(dalloc(h, &d.aidx, nt));
     TRY(dalloc(h, &d.tx, nt));
@@ -1101,7 +1102,7 @@ CkptLayout ckpt_layout(const sim_handle* h) {
   L.nn = (size_t)h->nn;
   L.nl = (size_t)h->nl;
   L.nlan = (size_t)h->n_lanes;
-  L.bytes = L.nt * (7 * 4 + 1 + 4 + 4 + 1 + 4) + L.nn * 4 + L.nl * 4 + L.nlan * 4 + sizeof(Ctl) + 64;
+  L.bytes = L.nt * (8 * 4 + 1 + 4 + 4 + 1 + 4) + L.nn * 4 + L.nl * 4 + L.nlan * 4 + sizeof(Ctl) + 64;
   return L;
 }
 
@@ -1110,7 +1111,7 @@ cudaError_t ckpt_copy(sim_handle* h, unsigned char* buf, bool save) {
   Dev& d = h->d;
   struct Item { void* p; size_t n; } items[] = {
       {d.A.x, L.nt * 4}, {d.A.v, L.nt * 4}, {d.A.vid, L.nt * 4}, {d.A.link, L.nt * 4}, {d.A.nxt, L.nt * 4},
-      {d.A.cur, L.nt * 4}, {d.A.lane, L.nt * 4}, {d.status, L.nt}, {d.ins_step, L.nt * 4}, {d.arr_step, L.nt * 4},
+      {d.A.cur, L.nt * 4}, {d.A.lane, L.nt * 4}, {d.A.gid, L.nt * 4}, {d.status, L.nt}, {d.ins_step, L.nt * 4}, {d.arr_step, L.nt * 4},
       {d.dec, L.nt}, {d.aidx, L.nt * 4}, {d.holder, L.nn * 4}, {h->q_head, L.nl * 4}, {d.cnt, L.nlan * 4},
       {d.ctl, sizeof(Ctl)}};
   size_t off = 0;

@@ -57,6 +57,7 @@ struct VehBuf {
   int32_t* nxt;    // next link of the route, -1 on the last link
   int32_t* cur;    // index of the current link in the route
   int32_t* lane;
+  int32_t* gid;    // global lane id (lane_base of the link + lane)
 };
 
 struct Ctl {

@@ -20,6 +20,20 @@ namespace gbt {
 
 #define GRID_STRIDE(i, n) for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
 
+// Append `pos` to list[] (counter *n) for the lanes of the warp where `pred` holds,
+// with one atomic per warp.
+__device__ __forceinline__ void warp_append(bool pred, int pos, int* n, int32_t* list) {
+  const unsigned act = __activemask();
+  const unsigned m = __ballot_sync(act, pred);
+  if (m) {
+    const int ln = threadIdx.x & 31, lead = __ffs(m) - 1;
+    int base = 0;
+    if (ln == lead) base = atomicAdd(n, __popc(m));
+    base = __shfl_sync(act, base, lead);
+    if (pred) list[base + __popc(m & ((1u << ln) - 1u))] = pos;
+  }
+}
+
 // ------------------------------------------------------------------ occupancy
 __global__ void k_count(Dev d) {
   const int nA = d.ctl->nA;
@@ -29,6 +43,7 @@ __global__ void k_count(Dev d) {
     int lane = d.A.lane[s];
     const LinkRec& L = d.links[e];
     if ((unsigned)lane >= L.lanes) { set_err(d, kErrLane, s); continue; }
+    d.A.gid[s] = L.lane_base + lane;
     d.aidx[s] = atomicAdd(&d.cnt[L.lane_base + lane], 1);
   }
 }
@@ -122,6 +137,7 @@ __device__ __forceinline__ void ph_scan_fin(const Dev& d) {
     if (b == nb - 1 && threadIdx.x == 0) {
       d.ctl->nB = tot_before + tot;
       d.lane_start[d.n_lanes] = tot_before + tot;
+      d.ctl->n_elig = 0;
     }
   }
 }
@@ -133,7 +149,7 @@ __device__ __forceinline__ void ph_scatter(const Dev& d) {
   GRID_STRIDE(s, nA) {
     int e = d.A.link[s];
     if (e < 0) continue;
-    int g = d.links[e].lane_base + d.A.lane[s];
+    int g = d.A.gid[s];
     int p = d.lane_start[g] + d.aidx[s];
     d.tx[p] = d.A.x[s];
     d.tvid[p] = d.A.vid[s];
@@ -180,7 +196,7 @@ __device__ __forceinline__ void ph_rank(const Dev& d) {
   }
 }
 
-__global__ void k_rank(Dev d) { ph_rank(d); }
+__global__ void __launch_bounds__(256, 8) k_rank(Dev d) { ph_rank(d); }
 
 // ------------------------------------------------------------------ neighbours / IDM
 __device__ __forceinline__ bool is_holder(const Dev& d, const LinkRec& L, int t, int vid, int lane,
@@ -236,6 +252,7 @@ __device__ __forceinline__ TapeRec* tape_slot(const Dev& d, int t, int vid) {
   return d.tape + (size_t)(t - (int)d.ctl->tape_t0) * (size_t)d.n_trips + (size_t)vid;
 }
 
+template <bool TAPE>
 __device__ __forceinline__ void ph_own(const Dev& d) {
   const int nB = d.ctl->nB;
   const int t = (int)d.ctl->t;
@@ -253,12 +270,12 @@ __device__ __forceinline__ void ph_own(const Dev& d) {
     if (!front) {
       const float sg = (d.B.x[p + 1] - x) - d.vlen;
       a = idm_acc(P, L.v0, d.s_min, sg, v, d.B.v[p + 1], true);
-      if (d.tape) f = TapeForm{d.B.vid[p + 1], sg, d.B.v[p + 1], kFormLead, 0, 0, 0};
+      if (TAPE) f = TapeForm{d.B.vid[p + 1], sg, d.B.v[p + 1], kFormLead, 0, 0, 0};
     } else {
       bool closed = nxt >= 0 && line_closed(d, L, t, hold);
-      a = acc_front(d, L, P, vid, nxt, lane, x, v, closed, d.tape ? &f : nullptr);
+      a = acc_front(d, L, P, vid, nxt, lane, x, v, closed, TAPE ? &f : nullptr);
     }
-    if (d.tape) {
+    if (TAPE) {
       TapeRec* rec = tape_slot(d, t, vid);
       rec->lead = f.lead;
       rec->kind = f.kind;
@@ -273,15 +290,7 @@ __device__ __forceinline__ void ph_own(const Dev& d) {
     // lane-change candidates (multi-lane link, away from both link ends) go to a
     // compact list so that the decision kernel runs full warps
     const bool elig = L.lanes >= 2 && x >= d.zone && xo < L.len - d.zone;
-    const unsigned act = __activemask();
-    const unsigned em = __ballot_sync(act, elig);
-    if (em) {
-      const int ln = threadIdx.x & 31, lead = __ffs(em) - 1;
-      int base = 0;
-      if (ln == lead) base = atomicAdd(&d.ctl->n_elig, __popc(em));
-      base = __shfl_sync(act, base, lead);
-      if (elig) d.elig[base + __popc(em & ((1u << ln) - 1u))] = p;
-    }
+    warp_append(elig, p, &d.ctl->n_elig, d.elig);
     uint8_t fl = (front ? kFlagFront : 0) | (hold ? kFlagHolder : 0);
     // admission candidate: front, route continues, stop line open, move reaches the end
     if (front && nxt >= 0 && !line_closed(d, L, t, hold) && xo >= L.len) {
@@ -304,7 +313,8 @@ __device__ __forceinline__ void ph_own(const Dev& d) {
   }
 }
 
-__global__ void k_own(Dev d) { ph_own(d); }
+template <bool TAPE>
+__global__ void k_own(Dev d) { ph_own<TAPE>(d); }
 
 // First position q in [s0, s1) whose (x, vid) exceeds (x, vid) of the probe.
 __device__ __forceinline__ int upper_pos(const Dev& d, int s0, int s1, float x, int vid) {
@@ -323,6 +333,7 @@ __device__ __forceinline__ int upper_pos(const Dev& d, int s0, int s1, float x, 
 // Helbing 2007) for discretionary changes, mandatory changes toward the lanes of
 // the next movement once within the drawn switch distance, and gap acceptance =
 // no overlap and both the changer's and the new follower's accelerations >= -b_safe.
+template <bool TAPE>
 __device__ __forceinline__ void ph_decide(const Dev& d) {
   const int ne = d.ctl->n_elig;
   const int t = (int)d.ctl->t;
@@ -370,9 +381,9 @@ __device__ __forceinline__ void ph_decide(const Dev& d) {
         float sl = (d.B.x[Ln] - x) - d.vlen;
         if (!(sl > 0.0f)) continue;
         ac = idm_acc(P, L.v0, d.s_min, sl, v, d.B.v[Ln], true);
-        cf = TapeForm{d.B.vid[Ln], sl, d.B.v[Ln], kFormLead, 0, 0, 0};
+        if (TAPE) cf = TapeForm{d.B.vid[Ln], sl, d.B.v[Ln], kFormLead, 0, 0, 0};
       } else {
-        ac = acc_front(d, L, P, vid, nxt, l2, x, v, closed_self, &cf);
+        ac = acc_front(d, L, P, vid, nxt, l2, x, v, closed_self, TAPE ? &cf : nullptr);
       }
       if (!(ac >= -d.mbsafe)) continue;
       float an = 0.0f;
@@ -385,7 +396,7 @@ __device__ __forceinline__ void ph_decide(const Dev& d) {
       if (mand) {
         chosen = dd;
         chosen_at = ac;
-        if (d.tape) d.tform[vid] = cf;
+        if (TAPE) d.tform[vid] = cf;
         break;
       }
       float dc = ac - d.a_own[p];
@@ -413,7 +424,7 @@ __device__ __forceinline__ void ph_decide(const Dev& d) {
         chosen = dd;
         chosen_inc = inc;
         chosen_at = ac;
-        if (d.tape) d.tform[vid] = cf;
+        if (TAPE) d.tform[vid] = cf;
       }
     }
     d.intent[p] = (int8_t)chosen;
@@ -421,9 +432,11 @@ __device__ __forceinline__ void ph_decide(const Dev& d) {
   }
 }
 
-__global__ void __launch_bounds__(256, 4) k_decide(Dev d) { ph_decide(d); }
+template <bool TAPE>
+__global__ void __launch_bounds__(256, 4) k_decide(Dev d) { ph_decide<TAPE>(d); }
 
 // ------------------------------------------------------------------ move
+template <bool TAPE>
 __device__ __forceinline__ void ph_move(const Dev& d) {
   const int nB = d.ctl->nB;
   const int t = (int)d.ctl->t;
@@ -457,7 +470,7 @@ __device__ __forceinline__ void ph_move(const Dev& d) {
     float x1, v1;
     ballistic(x, v, acc, d.dt, d.hdt2, x1, v1);
     TapeRec* rec = nullptr;
-    if (d.tape) {
+    if (TAPE) {
       rec = tape_slot(d, t, vid);
       if (change) {
         const TapeForm cf = d.tform[vid];
@@ -510,6 +523,7 @@ __device__ __forceinline__ void ph_move(const Dev& d) {
     if (hold) d.holder[L.to] = crossed ? -1 : vid;
     // lane count for the next occupancy rebuild
     const int gb = crossed ? d.links[nlink].lane_base : L.lane_base;
+    d.A.gid[p] = gb + nl;
     d.aidx[p] = atomicAdd(&d.cnt[gb + nl], 1);
     d.A.x[p] = nx;
     d.A.v[p] = nv;
@@ -565,6 +579,7 @@ __device__ __forceinline__ void ph_insert(const Dev& d) {
     d.A.nxt[slot] = e2;
     d.A.cur[slot] = 0;
     d.A.lane[slot] = bl;
+    d.A.gid[slot] = L.lane_base + bl;
     d.aidx[slot] = atomicAdd(&d.cnt[L.lane_base + bl], 1);
     d.status[h] = kActive;
     d.ins_step[h] = (int32_t)t;
@@ -575,8 +590,9 @@ __device__ __forceinline__ void ph_insert(const Dev& d) {
 
 // Move and departures touch disjoint slots of buffer A (departures append after the
 // sorted vehicles) and read only state of step t, so they share one launch.
+template <bool TAPE>
 __global__ void k_move_insert(Dev d) {
-  ph_move(d);
+  ph_move<TAPE>(d);
   if (d.n_qlinks > 0) ph_insert(d);
 }
 
@@ -626,9 +642,18 @@ void launch_kernel(int k, const Dev& d, int grid, cudaStream_t s) {
     case kKScanFin: k_scan_fin<<<nb, kScanThreads, 0, s>>>(d); break;
     case kKScatter: k_scatter<<<grid, 256, 0, s>>>(d); break;
     case kKRank: k_rank<<<grid, 256, 0, s>>>(d); break;
-    case kKOwn: k_own<<<grid, 256, 0, s>>>(d); break;
-    case kKDecide: k_decide<<<grid, 256, 0, s>>>(d); break;
-    case kKMoveInsert: k_move_insert<<<grid, 256, 0, s>>>(d); break;
+    case kKOwn:
+      if (d.tape) k_own<true><<<grid, 256, 0, s>>>(d);
+      else k_own<false><<<grid, 256, 0, s>>>(d);
+      break;
+    case kKDecide:
+      if (d.tape) k_decide<true><<<grid, 256, 0, s>>>(d);
+      else k_decide<false><<<grid, 256, 0, s>>>(d);
+      break;
+    case kKMoveInsert:
+      if (d.tape) k_move_insert<true><<<grid, 256, 0, s>>>(d);
+      else k_move_insert<false><<<grid, 256, 0, s>>>(d);
+      break;
     case kKFinish: k_finish<<<1, 1, 0, s>>>(d); break;
     default: break;
   }
@@ -720,11 +745,11 @@ __global__ void k_persistent(Dev d, GridSync* gs, int n_steps, long long limit) 
     if (!grid_barrier(gs, err, limit)) return;
     ph_rank(d);
     if (!grid_barrier(gs, err, limit)) return;
-    ph_own(d);
+    ph_own<false>(d);
     if (!grid_barrier(gs, err, limit)) return;
-    ph_decide(d);
+    ph_decide<false>(d);
     if (!grid_barrier(gs, err, limit)) return;
-    ph_move(d);
+    ph_move<false>(d);
     if (d.n_qlinks > 0) ph_insert(d);
     if (!grid_barrier(gs, err, limit)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) ph_finish(d);
