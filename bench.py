@@ -42,8 +42,8 @@ ALG_BYTES = {
 
 # DRAM bytes per active vehicle per launch from the ncu capture summarised in
 # profiles/step_kernels_metro_snapshot.md, valid only for the kernel source it was taken on.
-PROFILED_SRC_SHA = "e9ce4229aa9a6eda"
-PROFILED_TRAFFIC = {"decide": 61.9, "own": 49.0, "move": 65.7, "rank": 44.1}
+PROFILED_SRC_SHA = "57265aba677ecb3a"
+PROFILED_TRAFFIC = {"own": 48.9, "decide": 50.7, "move_insert": 70.5, "rank": 60.4}
 
 
 def kernel_source_sha():
