@@ -93,6 +93,17 @@ struct orc_sim {
   float *x0, *v0s;
   double* tgt;              /* targets of the taped run */
   int tgt_nobs, tgt_every;
+  /* measured outputs, each enabled by orc_set_outputs: per-trip fuel and CO (Eq. 8-9),
+   * per-link traversal times (Sec. 6.3.1), per-edge samples (Sec. 6.4) */
+  uint32_t out_flags;
+  double *fuel, *co;        /* [nt] */
+  int32_t* enter;           /* [nt] step at which the trip entered its current link, -1 unknown */
+  int64_t* tt_sum;          /* [nl] summed traversal steps */
+  int32_t* tt_n;            /* [nl] traversals */
+  int samp_every, samp_per, samp_max;
+  int64_t samp_k0;          /* first sample index taken since the outputs were cleared */
+  double *acc_u, *acc_s, *out_u, *out_s;
+  int32_t* out_n;
 };
 
 /* One taped vehicle-step: the form of Eq. 7 used (kind/lead/s/vl, see acc_form
@@ -177,15 +188,50 @@ int32_t orc_link_cost(float length_m, float speed_mps, int lanes, int mode) {
   return (int32_t)c;
 }
 
-/* SplitMix64 finaliser (Steele, Lea & Flood 2014) of seed ^ (vid << 32 | hop);
- * the top 8 bits index the mandatory-switch table. */
-uint32_t orc_mand_index(uint64_t seed, int32_t vid, int32_t hop) {
-  uint64_t z = seed ^ ((((uint64_t)(uint32_t)vid) << 32) | (uint64_t)(uint32_t)hop);
+/* SplitMix64 (Steele, Lea & Flood 2014): one increment and the finaliser. */
+static uint64_t splitmix64(uint64_t z) {
   z += 0x9E3779B97F4A7C15ULL;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-  z = z ^ (z >> 31);
+  return z ^ (z >> 31);
+}
+
+/* SplitMix64 of seed ^ (vid << 32 | hop); the top 8 bits index the
+ * mandatory-switch table. */
+uint32_t orc_mand_index(uint64_t seed, int32_t vid, int32_t hop) {
+  uint64_t z = splitmix64(seed ^ ((((uint64_t)(uint32_t)vid) << 32) | (uint64_t)(uint32_t)hop));
   return (uint32_t)(z >> 56);
+}
+
+/* Sec. 6.3.1 decaying reroute: trip vid is in the subset of round r when the top 16
+ * bits of SplitMix64 of seed ^ (vid << 32 | 2^31 | r) are below fraction_q16 (a
+ * fraction in 1/65536 units; 65536 takes every trip).  Bit 31 keeps these draws
+ * apart from the mandatory-switch draws, whose hop index stays below 2^31. */
+int orc_reroute_selected(uint64_t seed, int32_t vid, uint32_t round, uint32_t fraction_q16) {
+  uint64_t lo = 0x80000000ULL | (uint64_t)(round & 0x7FFFFFFFu);
+  uint64_t z = splitmix64(seed ^ ((((uint64_t)(uint32_t)vid) << 32) | lo));
+  return (uint32_t)(z >> 48) < fraction_q16;
+}
+
+/* Eq. 8: CO emission rate in g/s.  The equation takes the speed in miles per hour
+ * (1 mph = 0.44704 m/s); terms added left to right in binary32. */
+float orc_co_rate(float v) {
+  float vm = v / 0.44704f;
+  float d = vm - 50.0f;
+  return (-0.064f + 0.0056f * vm) + 0.00026f * (d * d);
+}
+
+/* Eq. 9: fuel rate in mL/s at speed v (m/s) and acceleration a (m/s^2), with the
+ * extra engine drag P_ea = 0.79296 a^2 v for a > 0.  The bracket is the tractive
+ * power (kW) of Akcelik's power-based model, which falls back to the idle rate
+ * (0.666 mL/s) when that power is not positive; terms added left to right. */
+float orc_fuel_rate(float v, float a) {
+  float p = 0.269f * v + 0.0171f * (v * v);
+  p = p + 0.000672f * ((v * v) * v);
+  p = p + (1.680f * a) * v;
+  if (a > 0.0f) p = p + ((0.79296f * a) * a) * v;
+  if (!(p > 0.0f)) p = 0.0f;
+  return 0.666f + 0.072f * p;
 }
 
 /* Mandatory switch (Sec. 6.3.2): a vehicle on the wrong lane turns mandatory with
@@ -375,7 +421,9 @@ void orc_destroy(orc_sim* S) {
                   S->v0l, S->lane_base, S->in_start, S->in_list, S->in_index, S->n_in, S->pv0, S->pT, S->pa,
                   S->pb, S->ps0, S->psab, S->orig, S->dest, S->dep, S->roff, S->rl, S->st, S->link, S->lane,
                   S->cur, S->x, S->v, S->ins_step, S->arr_step, S->dec, S->holder, S->q_start, S->q_items,
-                  S->q_head, S->rec, S->rec_step, S->st0, S->cur0, S->x0, S->v0s, S->tgt};
+                  S->q_head, S->rec, S->rec_step, S->st0, S->cur0, S->x0, S->v0s, S->tgt,
+                  S->fuel, S->co, S->enter, S->tt_sum, S->tt_n, S->acc_u, S->acc_s, S->out_u,
+                  S->out_s, S->out_n};
   for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); i++) free(ptrs[i]);
   free(S);
 }
@@ -417,6 +465,23 @@ static void rebuild_queues(orc_sim* S) {
   }
 }
 
+/* Outputs restart with the run: totals at zero, no link entered yet, sampling
+ * windows empty from the next sampling instant on. */
+static void clear_outputs(orc_sim* S) {
+  if (S->fuel)
+    for (int i = 0; i < S->nt; i++) { S->fuel[i] = 0.0; S->co[i] = 0.0; }
+  if (S->enter) {
+    for (int i = 0; i < S->nt; i++) S->enter[i] = -1;
+    for (int e = 0; e < S->nl; e++) { S->tt_sum[e] = 0; S->tt_n[e] = 0; }
+  }
+  if (S->acc_u) {
+    for (int e = 0; e < S->nl; e++) { S->acc_u[e] = 0.0; S->acc_s[e] = 0.0; }
+    for (int64_t q = 0; q < (int64_t)S->samp_max * S->nl; q++) { S->out_u[q] = 0.0; S->out_s[q] = 0.0; }
+    for (int w = 0; w < S->samp_max; w++) S->out_n[w] = 0;
+    S->samp_k0 = (S->t + S->samp_every - 1) / S->samp_every;
+  }
+}
+
 static void reset_state(orc_sim* S) {
   for (int i = 0; i < S->nt; i++) {
     S->st[i] = ST_PENDING; S->link[i] = -1; S->lane[i] = 0; S->cur[i] = 0; S->x[i] = 0.0f; S->v[i] = 0.0f;
@@ -424,14 +489,16 @@ static void reset_state(orc_sim* S) {
   }
   for (int n = 0; n < S->nn; n++) S->holder[n] = -1;
   S->t = 0; S->departed = 0; S->arrived = 0; S->veh_steps = 0; S->active_last = 0;
+  clear_outputs(S);
 }
 
 /* Trip planning (Sec. 6.3.1): every trip follows a shortest path from its origin
  * node to its destination node; one shortest-path tree per distinct origin is
  * shared by all trips from it (Sec. 6 "Simulation scale").  Ties between equally
  * short paths: walking back from the destination, take the lowest-id in-link
- * (u -> v) with dist[u] + c = dist[v]. */
-int orc_route(orc_sim* S, const int32_t* cost_in) {
+ * (u -> v) with dist[u] + c = dist[v].  With sel, only the trips with sel[i] set get
+ * a new path; the others keep theirs. */
+static int route_core(orc_sim* S, const int32_t* cost_in, const uint8_t* sel) {
   int nn = S->nn, nl = S->nl, nt = S->nt;
   int32_t* cost = (int32_t*)xcalloc(nl, 4);
   for (int e = 0; e < nl; e++) {
@@ -452,11 +519,21 @@ int orc_route(orc_sim* S, const int32_t* cost_in) {
   int32_t** paths = (int32_t**)xcalloc(nt, sizeof(int32_t*));
   int32_t* tmp = (int32_t*)xcalloc(nn + 1, 4);
   int rc = OK;
+  for (int i = 0; i < nt; i++) {
+    if (sel && !sel[i]) {   /* kept route */
+      rlen[i] = route_len(S, i);
+      paths[i] = (int32_t*)xcalloc(rlen[i], 4);
+      memcpy(paths[i], S->rl + S->roff[i], (size_t)rlen[i] * 4);
+    }
+  }
   for (int o = 0; o < nn && rc == OK; o++) {
-    if (ts[o] == ts[o + 1]) continue;
+    int any = 0;
+    for (int k = ts[o]; k < ts[o + 1]; k++) if (!sel || sel[tl[k]]) any = 1;
+    if (!any) continue;
     dijkstra(nn, os, ol, S->lt, cost, o, dist, heap);
     for (int k = ts[o]; k < ts[o + 1]; k++) {
       int i = tl[k];
+      if (sel && !sel[i]) continue;
       int d = S->dest[i];
       if (dist[d] == INT64_MAX) { rc = EUNREACH; break; }
       int n = 0, v = d;
@@ -489,6 +566,20 @@ int orc_route(orc_sim* S, const int32_t* cost_in) {
   }
   for (int i = 0; i < nt; i++) free(paths[i]);
   free(paths); free(tmp); free(rlen); free(heap); free(dist); free(ts); free(tl); free(os); free(ol); free(cost);
+  return rc;
+}
+
+int orc_route(orc_sim* S, const int32_t* cost_in) { return route_core(S, cost_in, NULL); }
+
+/* Sec. 6.3.1: new shortest paths under cost for the subset of round `round` (see
+ * orc_reroute_selected); the other trips keep their routes.  Restarts the run. */
+int orc_reroute(orc_sim* S, const int32_t* cost, uint32_t fraction_q16, uint32_t round) {
+  if (!S->routed) return ESTATE;
+  if (!cost || fraction_q16 > 65536u) return EINV;
+  uint8_t* sel = (uint8_t*)xcalloc(S->nt, 1);
+  for (int i = 0; i < S->nt; i++) sel[i] = (uint8_t)orc_reroute_selected(S->seed, i, round, fraction_q16);
+  int rc = route_core(S, cost, sel);
+  free(sel);
   return rc;
 }
 
@@ -731,8 +822,47 @@ static void rec_begin_step(orc_sim* S) {
   S->rec_step[S->rec_steps] = S->rec_n;
 }
 
+/* Sec. 6.4 per-edge sample at step t (taken from the state at t, when t is a multiple
+ * of samp_every): utilisation = vehicles on the edge / (length * lanes / (vehicle
+ * length + s0)), speed = mean speed of those vehicles, summed in occupancy order (lane,
+ * then position), or the free-flow speed of an empty edge.  Window w averages the
+ * samples w*samp_per .. w*samp_per + samp_per - 1 that were taken; it is written when
+ * its last sample is. */
+static void edge_sample(orc_sim* S, const occ_t* O, int64_t t) {
+  int64_t k = t / S->samp_every;
+  int64_t w = k / S->samp_per, j = k % S->samp_per;
+  int64_t first = w * S->samp_per > S->samp_k0 ? w * S->samp_per : S->samp_k0;
+  for (int e = 0; e < S->nl; e++) {
+    int g0 = S->lane_base[e], g1 = g0 + S->lanes[e];
+    int n = O->start[g1] - O->start[g0];
+    double sum = 0.0;
+    for (int p = O->start[g0]; p < O->start[g1]; p++) sum += (double)S->v[O->vids[p]];
+    double cap = ((double)S->len[e] * (double)S->lanes[e]) / ((double)S->len_v + (double)S->ps0[S->cls[e]]);
+    double util = (double)n / cap;
+    double spd = n > 0 ? sum / (double)n : (double)S->v0l[e];
+    S->acc_u[e] += util;
+    S->acc_s[e] += spd;
+    if (j == S->samp_per - 1) {
+      double cnt = (double)(k - first + 1);
+      S->out_u[w * S->nl + e] = S->acc_u[e] / cnt;
+      S->out_s[w * S->nl + e] = S->acc_s[e] / cnt;
+      S->acc_u[e] = 0.0;
+      S->acc_s[e] = 0.0;
+    }
+  }
+  if (j == S->samp_per - 1) S->out_n[w] = (int32_t)(k - first + 1);
+}
+
+/* Sec. 6.3.1 measurement: a trip leaving link e at step t (into its next link, or
+ * arriving) traversed it in t - enter steps, if it was seen entering it. */
+static void record_exit(orc_sim* S, int i, int e, int64_t t) {
+  if (S->enter[i] >= 0) { S->tt_sum[e] += t - S->enter[i]; S->tt_n[e] += 1; }
+}
+
 int orc_step(orc_sim* S, int32_t n_steps) {
   if (!S->routed) return ESTATE;
+  if (n_steps < 0) return EINV;
+  if (S->acc_u && n_steps > 0 && (S->t + n_steps - 1) / S->samp_every / S->samp_per >= S->samp_max) return EINV;
   int nt = S->nt;
   float* a_own = (float*)xcalloc(nt, 4);
   float* xo = (float*)xcalloc(nt, 4);
@@ -755,6 +885,7 @@ int orc_step(orc_sim* S, int32_t n_steps) {
     build_occ(S, &O);
     S->veh_steps += O.n;
     S->active_last = O.n;
+    if (S->acc_u && t % S->samp_every == 0) edge_sample(S, &O, t);
 
     /* stop signs (Sec. 6.3.2): one vehicle at a time.  A free stop-controlled node is
      * acquired by the front vehicle, within stop_acquire_m of the stop line, of the
@@ -924,6 +1055,11 @@ int orc_step(orc_sim* S, int32_t n_steps) {
       float acc = change[i] ? at[i] : a_own[i];
       float x1, v1;
       ballistic(S->x[i], S->v[i], acc, S->dt, S->hdt2, &x1, &v1);
+      if (S->fuel) {
+        /* Eq. 8-9 rates at the speed and acceleration of this step, times dt */
+        S->fuel[i] += (double)(orc_fuel_rate(S->v[i], acc) * S->dt);
+        S->co[i] += (double)(orc_co_rate(S->v[i]) * S->dt);
+      }
       orc_rec* rr = NULL;
       if (S->recording) {
         rr = rec_push(S);
@@ -942,6 +1078,7 @@ int orc_step(orc_sim* S, int32_t n_steps) {
         if (nx < 0) {
           nst[i] = ST_ARRIVED; nlink[i] = -1; nx_[i] = 0.0f; nv[i] = 0.0f;
           if (rr) rr->branch = BR_ARRIVE;
+          if (S->enter) record_exit(S, i, e, t);
           S->arr_step[i] = (int32_t)t;
           arrivals++;
           continue;
@@ -956,6 +1093,7 @@ int orc_step(orc_sim* S, int32_t n_steps) {
           nx_[i] = x1 - S->len[e]; nv[i] = v1;
           if (was_holder) S->holder[node] = -1;
           if (rr) rr->crossed = 1;
+          if (S->enter) { record_exit(S, i, e, t); S->enter[i] = (int32_t)t; }
         } else {
           nlane[i] = l1; nx_[i] = S->len[e]; nv[i] = 0.0f;
           if (rr) rr->branch = BR_CLAMP;
@@ -991,6 +1129,7 @@ int orc_step(orc_sim* S, int32_t n_steps) {
       if (!(brs >= need)) continue;
       nst[h] = ST_ACTIVE; nlink[h] = e; nlane[h] = bl; ncur[h] = 0; nx_[h] = 0.0f; nv[h] = 0.0f;
       S->ins_step[h] = (int32_t)t;
+      if (S->enter) S->enter[h] = (int32_t)t;
       S->q_head[e]++;
       ins++;
     }
@@ -1291,4 +1430,103 @@ int orc_replay_loss(const orc_sim* S, const double* pv0, const double* pT, const
   *loss = L;
   free(x); free(v); free(off); free(acc); free(st);
   return OK;
+}
+
+/* ------------------------------------------------------------------ measured outputs */
+int orc_set_outputs(orc_sim* S, uint32_t flags, int32_t sample_every, int32_t per_window, int32_t max_windows) {
+  if (flags & ~7u) return EINV;
+  if ((flags & 4u) && (sample_every < 1 || per_window < 1 || max_windows < 1)) return EINV;
+  free(S->fuel); free(S->co); free(S->enter); free(S->tt_sum); free(S->tt_n);
+  free(S->acc_u); free(S->acc_s); free(S->out_u); free(S->out_s); free(S->out_n);
+  S->fuel = S->co = NULL; S->enter = NULL; S->tt_sum = NULL; S->tt_n = NULL;
+  S->acc_u = S->acc_s = S->out_u = S->out_s = NULL; S->out_n = NULL;
+  S->out_flags = flags;
+  if (flags & 1u) {
+    S->fuel = (double*)xcalloc(zsz(S->nt), 8);
+    S->co = (double*)xcalloc(zsz(S->nt), 8);
+  }
+  if (flags & 2u) {
+    S->enter = (int32_t*)xcalloc(zsz(S->nt), 4);
+    S->tt_sum = (int64_t*)xcalloc(zsz(S->nl), 8);
+    S->tt_n = (int32_t*)xcalloc(zsz(S->nl), 4);
+  }
+  if (flags & 4u) {
+    S->samp_every = sample_every; S->samp_per = per_window; S->samp_max = max_windows;
+    S->acc_u = (double*)xcalloc(zsz(S->nl), 8);
+    S->acc_s = (double*)xcalloc(zsz(S->nl), 8);
+    S->out_u = (double*)xcalloc((size_t)max_windows * zsz(S->nl), 8);
+    S->out_s = (double*)xcalloc((size_t)max_windows * zsz(S->nl), 8);
+    S->out_n = (int32_t*)xcalloc((size_t)max_windows, 4);
+  }
+  clear_outputs(S);
+  return OK;
+}
+
+int orc_read_emissions(const orc_sim* S, double* fuel_ml, double* co_g) {
+  if (!S->fuel) return ESTATE;
+  memcpy(fuel_ml, S->fuel, (size_t)S->nt * 8);
+  memcpy(co_g, S->co, (size_t)S->nt * 8);
+  return OK;
+}
+
+int orc_read_link_times(const orc_sim* S, int64_t* sum_steps, int32_t* n_exits) {
+  if (!S->enter) return ESTATE;
+  memcpy(sum_steps, S->tt_sum, (size_t)S->nl * 8);
+  memcpy(n_exits, S->tt_n, (size_t)S->nl * 4);
+  return OK;
+}
+
+int orc_read_edge_samples(const orc_sim* S, double* util, double* speed, int32_t* n_samples) {
+  if (!S->acc_u) return ESTATE;
+  memcpy(util, S->out_u, (size_t)S->samp_max * S->nl * 8);
+  memcpy(speed, S->out_s, (size_t)S->samp_max * S->nl * 8);
+  memcpy(n_samples, S->out_n, (size_t)S->samp_max * 4);
+  return OK;
+}
+
+/* Sec. 6.3.1: the measured travel time of a link is the mean of its traversal times
+ * in deciseconds (traversal steps * dt_ds / traversals, rounded half up, kept within
+ * 1 .. 1e6); a link no trip left keeps its previous cost.  gap (optional) compares
+ * previous and measured costs, weighted by traversals:
+ * sum n_e |prev_e - meas_e| / sum n_e prev_e. */
+int orc_measured_costs(const orc_sim* S, const int32_t* prev, int32_t* out, double* gap) {
+  if (!S->enter) return ESTATE;
+  int64_t num = 0, den = 0;
+  for (int e = 0; e < S->nl; e++) {
+    int64_t n = S->tt_n[e];
+    if (n == 0) { out[e] = prev[e]; continue; }
+    int64_t c = (2 * S->tt_sum[e] * S->dt_ds + n) / (2 * n);
+    if (c < 1) c = 1;
+    if (c > 1000000) c = 1000000;
+    out[e] = (int32_t)c;
+    num += n * (c > prev[e] ? c - prev[e] : prev[e] - c);
+    den += n * (int64_t)prev[e];
+  }
+  if (gap) *gap = den > 0 ? (double)num / (double)den : 0.0;
+  return OK;
+}
+
+/* Sec. 6.3.1 iterative decaying equilibrium: iteration 0 routes every trip on the
+ * initial costs (cost_mode) and runs n_steps; iteration k >= 1 reroutes the subset
+ * fractions_q16[k] of round k on the costs measured in iteration k - 1 and runs again.
+ * gap[k] is the measured-versus-routed gap of iteration k; cost_out the costs measured
+ * in the last one.  Needs the link-time output. */
+int orc_equilibrium(orc_sim* S, int32_t n_iter, const uint32_t* fractions_q16, int32_t n_steps, int32_t* cost_out,
+                    double* gap) {
+  if (!S->enter) return ESTATE;
+  if (n_iter < 1 || n_steps < 1) return EINV;
+  for (int k = 1; k < n_iter; k++) if (fractions_q16[k] > 65536u) return EINV;
+  int32_t* cost = (int32_t*)xcalloc(zsz(S->nl), 4);
+  int32_t* meas = (int32_t*)xcalloc(zsz(S->nl), 4);
+  for (int e = 0; e < S->nl; e++) cost[e] = orc_link_cost(S->len[e], S->spd[e], S->lanes[e], S->cost_mode);
+  int rc = OK;
+  for (int k = 0; k < n_iter && rc == OK; k++) {
+    rc = k == 0 ? orc_route(S, cost) : orc_reroute(S, cost, fractions_q16[k], (uint32_t)k);
+    if (rc == OK) rc = orc_step(S, n_steps);
+    if (rc == OK) rc = orc_measured_costs(S, cost, meas, &gap[k]);
+    if (rc == OK) memcpy(cost, meas, (size_t)S->nl * 4);
+  }
+  if (rc == OK) memcpy(cost_out, cost, (size_t)S->nl * 4);
+  free(cost); free(meas);
+  return rc;
 }

@@ -64,7 +64,22 @@ int  orc_replay_loss(const orc_sim*, const double* v0, const double* T, const do
                      const double* s0, double* loss);
 int  orc_set_class_params(orc_sim*, const float* v0, const float* T, const float* a, const float* b, const float* s0);
 
+/* measured outputs (flags: 1 fuel and CO per trip, Eq. 8-9; 2 link traversal times,
+ * Sec. 6.3.1; 4 per-edge samples, Sec. 6.4), cleared whenever the run restarts */
+int  orc_set_outputs(orc_sim*, uint32_t flags, int32_t sample_every, int32_t per_window, int32_t max_windows);
+int  orc_read_emissions(const orc_sim*, double* fuel_ml, double* co_g);
+int  orc_read_link_times(const orc_sim*, int64_t* sum_steps, int32_t* n_exits);
+int  orc_read_edge_samples(const orc_sim*, double* util, double* speed, int32_t* n_samples);
+/* iterative decaying route equilibrium (Sec. 6.3.1) */
+int  orc_measured_costs(const orc_sim*, const int32_t* prev_cost_ds, int32_t* cost_ds, double* gap);
+int  orc_reroute(orc_sim*, const int32_t* link_cost_ds, uint32_t fraction_q16, uint32_t round);
+int  orc_equilibrium(orc_sim*, int32_t n_iter, const uint32_t* fractions_q16, int32_t n_steps,
+                     int32_t* cost_out, double* gap);
+
 /* building blocks exposed for the pin tests */
+int   orc_reroute_selected(uint64_t seed, int32_t vid, uint32_t round, uint32_t fraction_q16);
+float orc_co_rate(float v);
+float orc_fuel_rate(float v, float a);
 float orc_idm(float a, float b, float T, float s0, float v0, float s_min,
               float s, float v, float v_lead, int has_leader);
 void  orc_ballistic(float x, float v, float acc, float dt, float* x_out, float* v_out);

@@ -87,6 +87,19 @@ def lib():
         L.orc_mand_tau.restype = f32
         L.orc_turn.argtypes = [i64] * 6
         L.orc_signal_green.argtypes = [i64, i32, i32, i32, i32, C.c_int]
+        u32 = C.c_uint32
+        L.orc_set_outputs.argtypes = [vp, u32, i32, i32, i32]
+        L.orc_read_emissions.argtypes = [vp, vp, vp]
+        L.orc_read_link_times.argtypes = [vp, vp, vp]
+        L.orc_read_edge_samples.argtypes = [vp, vp, vp, vp]
+        L.orc_measured_costs.argtypes = [vp, vp, vp, vp]
+        L.orc_reroute.argtypes = [vp, vp, u32, u32]
+        L.orc_equilibrium.argtypes = [vp, i32, vp, i32, vp, vp]
+        L.orc_reroute_selected.argtypes = [C.c_uint64, i32, u32, u32]
+        L.orc_co_rate.argtypes = [f32]
+        L.orc_co_rate.restype = f32
+        L.orc_fuel_rate.argtypes = [f32, f32]
+        L.orc_fuel_rate.restype = f32
         _lib = L
     return _lib
 
@@ -137,6 +150,8 @@ class OracleSim:
         self.h = h
         self.n_trips = dem["n_trips"]
         self.n_nodes = net["n_nodes"]
+        self.n_links = net["n_links"]
+        self._max_windows = 0
         self.n_lanes = L.orc_n_lanes(h)
 
     def close(self):
@@ -225,6 +240,50 @@ class OracleSim:
         _check(lib().orc_replay_loss(self.h, *[_p(q) for q in arrs], _p(loss)), "orc_replay_loss")
         return float(loss[0])
 
+    # ---- measured outputs (Eq. 8-9, Sec. 6.3.1, Sec. 6.4)
+    def set_outputs(self, flags, sample_every=120, per_window=6, max_windows=0):
+        _check(lib().orc_set_outputs(self.h, int(flags), int(sample_every), int(per_window), int(max_windows)),
+               "orc_set_outputs")
+        self._max_windows = int(max_windows) if flags & 4 else 0
+
+    def emissions(self):
+        fuel = np.zeros(self.n_trips, np.float64)
+        co = np.zeros(self.n_trips, np.float64)
+        _check(lib().orc_read_emissions(self.h, _p(fuel), _p(co)), "orc_read_emissions")
+        return fuel, co
+
+    def link_times(self):
+        s = np.zeros(self.n_links, np.int64)
+        n = np.zeros(self.n_links, np.int32)
+        _check(lib().orc_read_link_times(self.h, _p(s), _p(n)), "orc_read_link_times")
+        return s, n
+
+    def edge_samples(self):
+        w = self._max_windows
+        u = np.zeros((w, self.n_links), np.float64)
+        sp = np.zeros((w, self.n_links), np.float64)
+        n = np.zeros(w, np.int32)
+        _check(lib().orc_read_edge_samples(self.h, _p(u), _p(sp), _p(n)), "orc_read_edge_samples")
+        return u, sp, n
+
+    def measured_costs(self, prev):
+        prev = np.ascontiguousarray(prev, np.int32)
+        out = np.zeros(self.n_links, np.int32)
+        gap = np.zeros(1, np.float64)
+        _check(lib().orc_measured_costs(self.h, _p(prev), _p(out), _p(gap)), "orc_measured_costs")
+        return out, float(gap[0])
+
+    def reroute(self, costs, fraction_q16, round_):
+        c = np.ascontiguousarray(costs, np.int32)
+        _check(lib().orc_reroute(self.h, _p(c), int(fraction_q16), int(round_)), "orc_reroute")
+
+    def equilibrium(self, fractions_q16, n_steps):
+        f = np.ascontiguousarray(fractions_q16, np.uint32)
+        cost = np.zeros(self.n_links, np.int32)
+        gap = np.zeros(len(f), np.float64)
+        _check(lib().orc_equilibrium(self.h, len(f), _p(f), int(n_steps), _p(cost), _p(gap)), "orc_equilibrium")
+        return cost, gap
+
     def node_holder(self):
         h = np.zeros(self.n_nodes, np.int32)
         _check(lib().orc_node_holder(self.h, _p(h)), "orc_node_holder")
@@ -268,3 +327,15 @@ def oracle_turn(a, b, c):
 
 def oracle_signal_green(t, dt_ds, offset, cycle, green, ew):
     return lib().orc_signal_green(t, dt_ds, offset, cycle, green, int(ew))
+
+
+def oracle_reroute_selected(seed, vid, round_, fraction_q16):
+    return bool(lib().orc_reroute_selected(seed & (2**64 - 1), vid, round_, fraction_q16))
+
+
+def oracle_co_rate(v):
+    return lib().orc_co_rate(v)
+
+
+def oracle_fuel_rate(v, a):
+    return lib().orc_fuel_rate(v, a)
