@@ -64,6 +64,8 @@ def parse():
                     help="skip the 64-scenario batched-ensemble comparison")
     ap.add_argument("--batched-steps", type=int, default=7200)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward time ratio")
+    ap.add_argument("--no-outputs", action="store_true",
+                    help="skip the measured-output overhead and the equilibrium timing")
     ap.add_argument("--workload", default="metro", choices=["metro", "metro-walk"],
                     help="metro: GPU-planned shortest-path routes; metro-walk: the first --trips trips on "
                          "random-walk routes (no trip planning; smaller cases for profiling)")
@@ -303,6 +305,50 @@ def measure_adjoint(G, S, torch, reps=3):
             "grad_norm": float(np.linalg.norm(grad))}
 
 
+# ---------------------------------------------------------------------------- outputs
+def measure_outputs(G, g, snap, args, stream, torch, plain_ms):
+    """The metro snapshot stepped again with every measured output on: fuel and CO per
+    trip (Eq. 8-9), link traversal times (Sec. 6.3.1) and per-edge samples every 60 s in
+    6-minute windows (Sec. 6.4).  Device time per step against the plain steps."""
+    g.set_outputs(G.OUT_EMISSIONS | G.OUT_LINK_TIMES | G.OUT_EDGE_SAMPLES, 120, 6,
+                  (args.warmup + args.steps) // 720 + 1)
+    g.write_state(snap)
+    g.step(args.warmup)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    g.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    fuel, co = g.emissions()
+    _, n_exit = g.link_times()
+    g.set_outputs(0)
+    return {"ms_per_step": ms, "overhead_frac": ms / plain_ms - 1.0, "every_steps": 120, "per_window": 6,
+            "fuel_l_total": float(fuel.sum() / 1e3), "co_kg_total": float(co.sum() / 1e3),
+            "link_exits": int(n_exit.sum())}
+
+
+def measure_equilibrium(G, S, torch):
+    """Sec. 6.3.1 iterative decaying equilibrium on the 20x20 signalised grid (20,000
+    trips, 9,000 steps per run): four runs routed on 100%, 100%, 50% and 25% of the trips,
+    the first on sqrt(lanes) * length / speed, the others on the travel times measured in
+    the previous run.  Wall time of the whole sim_equilibrium call."""
+    sc = S.grid()
+    sc["params"]["cost_mode"] = 1
+    g = G.Sim(sc)
+    g.set_outputs(G.OUT_LINK_TIMES)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cost, gap = g.equilibrium([65536, 65536, 32768, 16384], sc["steps"])
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    c = g.counters()
+    g.close()
+    return {"workload": "20x20 grid, 20000 trips, 4 x 9000 steps", "seconds": secs, "gap": [float(x) for x in gap],
+            "last_run_arrived": c["arrived"], "last_run_veh_steps": c["veh_steps"]}
+
+
 # ---------------------------------------------------------------------------- cuda arm
 def run_cuda(args):
     import torch
@@ -412,6 +458,11 @@ def run_cuda(args):
                "steps": e_steps, "pattern": "sim_write_state(host snapshot) then per step sim_step(1) + "
                                             "sim_read_state(x, v -> pinned host)"}
 
+    outputs = equilibrium = None
+    if not args.no_outputs:
+        outputs = measure_outputs(G, g, snap, args, stream, torch, ms / args.steps)
+        equilibrium = measure_equilibrium(G, S, torch)
+
     # -- aggregate over ranks (replicas only: each rank runs its own copy)
     secs = ms / 1e3
     tot_vs = veh_steps
@@ -458,6 +509,8 @@ def run_cuda(args):
         "per_kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
         "routing": {"seconds": route_s, "mode": "gpu sim_route" if args.workload == "metro" else "set_routes", "origins_trees": int(len(np.unique(m["demand"]["origin"]))),
                     "trips": m["demand"]["n_trips"], "hops": int(off[-1])},
+        "outputs": outputs,
+        "equilibrium": equilibrium,
         "batched_ensemble": batched,
         "adjoint_forward": adjoint,
         "cpu_baseline": cpu,

@@ -261,6 +261,91 @@ typedef struct {
  * after the n_steps.  Errors: SIM_EINVAL, SIM_ESTATE, SIM_ENOMEM. */
 int sim_adjoint(sim_handle* h, const sim_loss_spec* spec, double* grad_out, double* loss_out);
 
+/* ---------------------------------------------------------------- measured outputs
+ * Optional per-run measurements taken by the step kernels (sim_step in either
+ * execution mode; sim_step_timed counts the edge-sample kernel under "own").  All
+ * enabled outputs are cleared by sim_set_outputs, sim_reset_outputs, sim_route,
+ * sim_reroute, sim_set_routes and sim_write_state (after which t = 0).
+ *
+ * SIM_OUT_EMISSIONS (Eq. 8-9, Sec. 6.3.4): per trip, the fuel burnt (mL) and the CO
+ *   emitted (g).  Every step a vehicle on the road adds dt times the rates at its speed
+ *   v and the acceleration a it applies in that step, computed in binary32:
+ *   fuel = 0.666 + 0.072 * max(0, 0.269 v + 0.0171 v^2 + 0.000672 v^3 + 1.680 a v
+ *   + [a > 0] 0.79296 a^2 v) mL/s (the bracket is tractive power in kW; the engine
+ *   idles when it is not positive) and CO = -0.064 + 0.0056 m + 0.00026 (m - 50)^2
+ *   g/s, m = v / 0.44704 the speed in mph.  Sums are binary64.
+ * SIM_OUT_LINK_TIMES (Sec. 6.3.1): per link, the number of trips that left it (into
+ *   their next link, or arriving at its end) and their summed traversal times in
+ *   steps, from the step they entered it (departure or crossing) to the step they
+ *   left.  Trips already on a link when the outputs were cleared are not counted on
+ *   that link.
+ * SIM_OUT_EDGE_SAMPLES (Sec. 6.4): every every_steps steps (at t = 0, every_steps,
+ *   ...), per link, the utilisation n / (length * lanes / (veh_len + s0)) with n the
+ *   vehicles on the link and s0 its class's minimum gap, and the mean speed of those
+ *   vehicles (the desired speed v0 of the link when it is empty).  Window w averages
+ *   the samples w*per_window .. w*per_window + per_window - 1 taken since the last
+ *   clear and is written when its last sample is; the paper samples every minute and
+ *   averages over 6 minutes (every_steps = 60 / dt, per_window = 6). */
+#define SIM_OUT_EMISSIONS 1u
+#define SIM_OUT_LINK_TIMES 2u
+#define SIM_OUT_EDGE_SAMPLES 4u
+typedef struct {
+  int32_t every_steps;   /* >= 1 */
+  int32_t per_window;    /* >= 1 */
+  int32_t max_windows;   /* windows stored; sim_step refuses (SIM_EINVAL) to run past them */
+} sim_sampling;
+
+/* Turn the outputs in flags on (and the others off), allocating their device
+ * arrays (emissions 16 B per trip; link times 4 B per trip + 12 B per link; edge
+ * samples 16 B per link and 16 B per link per window).  sampling is read for
+ * SIM_OUT_EDGE_SAMPLES only.  sim_adjoint and sim_autotune refuse to run (SIM_ESTATE)
+ * while any output is on.
+ * Errors: SIM_EINVAL (unknown flag, sizes < 1), SIM_ENOMEM. */
+int sim_set_outputs(sim_handle* h, uint32_t flags, const sim_sampling* sampling);
+
+/* Clear the enabled outputs without touching the vehicle state; sampling windows
+ * restart at the next sampling instant. */
+int sim_reset_outputs(sim_handle* h);
+
+/* Per-trip totals (host arrays [n_trips], trip order).  SIM_ESTATE when off. */
+int sim_read_emissions(sim_handle* h, double* fuel_ml, double* co_g);
+
+/* Per-link traversal sums (host arrays [n_links]).  SIM_ESTATE when off. */
+int sim_read_link_times(sim_handle* h, int64_t* sum_steps, int32_t* n_exits);
+
+/* Window means, host arrays util[max_windows][n_links], speed[max_windows][n_links]
+ * (m/s), and n_samples[max_windows], the samples behind each finished window (0: not
+ * finished; its util and speed are 0).  SIM_ESTATE when off. */
+int sim_read_edge_samples(sim_handle* h, double* util, double* speed, int32_t* n_samples);
+
+/* Sec. 6.3.1 measured routing weights: cost_ds[e] = the mean traversal time of link
+ * e in deciseconds (summed steps * dt_ds / traversals, rounded half up, within
+ * 1..1e6), or prev_cost_ds[e] when no trip left e.  gap (may be NULL) =
+ * sum_e n_e |cost_e - prev_e| / sum_e n_e prev_e, n_e the traversals (0 when none).
+ * Host arrays [n_links].  Needs SIM_OUT_LINK_TIMES (SIM_ESTATE); SIM_EINVAL when a
+ * previous cost is outside 1..1e6. */
+int sim_measured_costs(sim_handle* h, const int32_t* prev_cost_ds, int32_t* cost_ds, double* gap);
+
+/* Sec. 6.3.1 decaying reroute: new shortest paths (as sim_route, on link_cost_ds)
+ * for the subset of trips of round `round`, the others keep their routes.  Trip
+ * vid (scenario-local id in a batch) is in the subset when the top 16 bits of
+ * SplitMix64(seed ^ (vid << 32) ^ (2^31 | round)) are below fraction_q16 (0..65536;
+ * 65536 reroutes every trip, 32768 about half).  Resets the vehicle state like
+ * sim_route.  Errors as sim_route, SIM_ESTATE before any routes; a failure after
+ * the search started leaves the handle without routes. */
+int sim_reroute(sim_handle* h, const int32_t* link_cost_ds, uint32_t fraction_q16, uint32_t round);
+
+/* Sec. 6.3.1 iterative decaying equilibrium, n_iter runs of n_steps from t = 0:
+ * iteration 0 routes every trip on the initial weights (Eq. 4; cost_mode 1 for the
+ * paper's sqrt(lanes) * length / speed), iteration k >= 1 reroutes the subset
+ * fractions_q16[k] of round k (fractions_q16[0] is not read) on the weights measured
+ * in iteration k - 1.  gap_out[k] is sim_measured_costs's gap after iteration k and
+ * cost_out [n_links] the weights measured in the last one.  The paper's schedule is
+ * four iterations with 100%, 100%, 50% and 25% of the trips routed.  The handle is
+ * left at the end of the last run.  Needs SIM_OUT_LINK_TIMES (SIM_ESTATE). */
+int sim_equilibrium(sim_handle* h, int32_t n_iter, const uint32_t* fractions_q16, int32_t n_steps,
+                    int32_t* cost_out, double* gap_out);
+
 /* Largest graph sim_sssp_static accepts (nodes). */
 #define SIM_SSSP_STATIC_MAX_NODES 262144
 

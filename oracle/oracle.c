@@ -1462,6 +1462,12 @@ int orc_set_outputs(orc_sim* S, uint32_t flags, int32_t sample_every, int32_t pe
   return OK;
 }
 
+/* clear the outputs in the middle of a run (windows restart at the next sampling instant) */
+int orc_reset_outputs(orc_sim* S) {
+  clear_outputs(S);
+  return OK;
+}
+
 int orc_read_emissions(const orc_sim* S, double* fuel_ml, double* co_g) {
   if (!S->fuel) return ESTATE;
   memcpy(fuel_ml, S->fuel, (size_t)S->nt * 8);

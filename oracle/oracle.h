@@ -67,6 +67,7 @@ int  orc_set_class_params(orc_sim*, const float* v0, const float* T, const float
 /* measured outputs (flags: 1 fuel and CO per trip, Eq. 8-9; 2 link traversal times,
  * Sec. 6.3.1; 4 per-edge samples, Sec. 6.4), cleared whenever the run restarts */
 int  orc_set_outputs(orc_sim*, uint32_t flags, int32_t sample_every, int32_t per_window, int32_t max_windows);
+int  orc_reset_outputs(orc_sim*);
 int  orc_read_emissions(const orc_sim*, double* fuel_ml, double* co_g);
 int  orc_read_link_times(const orc_sim*, int64_t* sum_steps, int32_t* n_exits);
 int  orc_read_edge_samples(const orc_sim*, double* util, double* speed, int32_t* n_samples);

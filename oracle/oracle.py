@@ -89,6 +89,7 @@ def lib():
         L.orc_signal_green.argtypes = [i64, i32, i32, i32, i32, C.c_int]
         u32 = C.c_uint32
         L.orc_set_outputs.argtypes = [vp, u32, i32, i32, i32]
+        L.orc_reset_outputs.argtypes = [vp]
         L.orc_read_emissions.argtypes = [vp, vp, vp]
         L.orc_read_link_times.argtypes = [vp, vp, vp]
         L.orc_read_edge_samples.argtypes = [vp, vp, vp, vp]
@@ -245,6 +246,9 @@ class OracleSim:
         _check(lib().orc_set_outputs(self.h, int(flags), int(sample_every), int(per_window), int(max_windows)),
                "orc_set_outputs")
         self._max_windows = int(max_windows) if flags & 4 else 0
+
+    def reset_outputs(self):
+        _check(lib().orc_reset_outputs(self.h), "orc_reset_outputs")
 
     def emissions(self):
         fuel = np.zeros(self.n_trips, np.float64)

@@ -29,6 +29,9 @@ void launch_tape_begin(const Dev& d, cudaStream_t s);
 void launch_adj_step(const Dev& d, int grid, cudaStream_t s, const TapeRec* slab, const double* lx,
                      const double* lv, const double* res, double* nx, double* nv, double* grad, int n_class);
 void launch_first_links(const int32_t* roff, const int32_t* routes, int n, int32_t* out, cudaStream_t s);
+void launch_measured_costs(const Dev& d, const int32_t* prev, int32_t* out, cudaStream_t s);
+void launch_compact_routes(const int32_t* roff, const int32_t* rlen, const int32_t* src, const int32_t* new_off,
+                           int32_t* dst, int n, cudaStream_t s);
 int persistent_max_blocks_per_sm(int threads);
 cudaError_t launch_persistent(const Dev& d, GridSync* gs, int blocks, int threads, int n_steps, long long limit,
                               cudaStream_t s);
@@ -65,6 +68,9 @@ struct sim_handle {
   cudaGraphExec_t gexec = nullptr;
   cudaGraph_t graph = nullptr;
   bool graph_dirty = true;
+  // the step graph with the per-edge sample kernel, launched at sampling instants only
+  cudaGraphExec_t gexec_samp = nullptr;
+  cudaGraph_t graph_samp = nullptr;
   // class parameters (host copies) and the adjoint's tape
   std::vector<float> v0c, Tc, ac, bc, s0c, spd_link;
   std::vector<uint8_t> cls_link;
@@ -84,6 +90,9 @@ struct sim_handle {
   int pgraph_n = -1;
   sim_exec pgraph_cfg{};
   bool pgraph_unsupported = false;
+  // per-trip hash bases (mandatory-switch and reroute draws), measured outputs
+  std::vector<unsigned long long> hseed;
+  uint32_t out_flags = 0;
 };
 
 namespace {
@@ -252,6 +261,7 @@ int create_from_flat(Flat& F, sim_handle** out) {
   h->depart = F.dep;
   h->origin = F.orig;
   h->dest = F.dest;
+  h->hseed = F.hseed;
   cudaGetDevice(&h->device);
   cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
   if (h->sm_count <= 0) h->sm_count = 1;
@@ -481,6 +491,34 @@ int build_queues(sim_handle* h, const std::vector<uint8_t>& status) {
 }
 
 // Reset the dynamic state: all trips pending, no vehicles, t = 0.
+// Measured outputs restart: totals at zero, no link entered yet, sampling windows
+// empty from the first sampling instant at or after step t (t < 0: read it).
+int clear_outputs(sim_handle* h, long long t) {
+  Dev& d = h->d;
+  const size_t nt = (size_t)std::max(1, h->nt), nl = (size_t)std::max(1, h->nl);
+  if (d.emis) CK(cudaMemsetAsync(d.emis, 0, nt * 16, h->stream));
+  if (d.enter) {
+    CK(cudaMemsetAsync(d.enter, 0xFF, nt * 4, h->stream));
+    CK(cudaMemsetAsync(d.tt_sum, 0, nl * 8, h->stream));
+    CK(cudaMemsetAsync(d.tt_n, 0, nl * 4, h->stream));
+  }
+  if (d.acc_u) {
+    CK(cudaMemsetAsync(d.acc_u, 0, nl * 8, h->stream));
+    CK(cudaMemsetAsync(d.acc_s, 0, nl * 8, h->stream));
+    CK(cudaMemsetAsync(d.out_u, 0, (size_t)d.samp_max * nl * 8, h->stream));
+    CK(cudaMemsetAsync(d.out_s, 0, (size_t)d.samp_max * nl * 8, h->stream));
+    CK(cudaMemsetAsync(d.out_n, 0, (size_t)d.samp_max * 4, h->stream));
+    if (t < 0) {
+      CK(cudaMemcpyAsync(&t, &d.ctl->t, sizeof(t), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+    }
+    const long long k0 = (t + d.samp_every - 1) / d.samp_every;
+    CK(cudaMemcpyAsync(&d.ctl->samp_k0, &k0, sizeof(k0), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  return SIM_OK;
+}
+
 int reset_dynamic(sim_handle* h) {
   Dev& d = h->d;
   const size_t nt = (size_t)h->nt;
@@ -493,16 +531,20 @@ int reset_dynamic(sim_handle* h) {
   CK(cudaMemsetAsync(d.best, 0xFF, (size_t)h->n_lanes * 8, h->stream));
   CK(cudaMemsetAsync(d.cnt, 0, (size_t)h->n_lanes * 4, h->stream));
   CK(cudaMemsetAsync(d.ctl, 0, sizeof(Ctl), h->stream));
-  return SIM_OK;
+  return clear_outputs(h, 0);
 }
 
 // Step times stay below 2^31 / dt_ds so that the device's 32-bit phase arithmetic is exact.
-int check_horizon(sim_handle* h, int n_steps) {
+int check_horizon(sim_handle* h, int n_steps, long long* t_now = nullptr) {
   Ctl c;
   CK(cudaMemcpyAsync(&c, h->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (t_now) *t_now = c.t;
   const long long limit = 2147483647LL / (h->d.dt_ds + 1);
   if (c.t + (long long)n_steps > limit) return fail(h, SIM_EINVAL, "simulation horizon beyond 2^31 deciseconds");
+  const Dev& d = h->d;
+  if (d.acc_u && n_steps > 0 && (c.t + n_steps - 1) / d.samp_every / d.samp_per >= d.samp_max)
+    return fail(h, SIM_EINVAL, "edge-sample windows would run past max_windows");
   return SIM_OK;
 }
 
@@ -522,53 +564,57 @@ int check_device(sim_handle* h) {
   return SIM_OK;
 }
 
-}  // namespace
-
-// ====================================================================== C ABI
-extern "C" {
-
-int sim_create(const sim_network* net, const sim_demand* dem, const sim_params* par, sim_handle** out) {
-  if (!out) return fail(nullptr, SIM_EINVAL, "out is NULL");
-  *out = nullptr;
-  Flat F;
-  int rc = flatten(1, &net, &dem, &par, F);
-  if (rc) return rc;
-  return create_from_flat(F, out);
+// Eq. 4: t0 = d / s, in deciseconds rounded half up, at least 1 (binary64); cost_mode 1
+// scales it by sqrt(lanes), the initial routing weight of Sec. 6.3.1.
+int32_t free_flow_cost(const sim_handle* h, int e) {
+  const double dd = (double)h->len[e], ss = (double)h->spd[e];
+  const double tt = h->cost_mode == 1 ? ((10.0 * std::sqrt((double)h->lanes[e])) * dd) / ss : (10.0 * dd) / ss;
+  double c = std::floor(tt + 0.5);
+  if (c < 1.0) c = 1.0;
+  if (c > 1.0e6) c = 1.0e6;
+  return (int32_t)c;
 }
 
-int sim_create_batch(int32_t n, const sim_network* const* nets, const sim_demand* const* dems,
-                     const sim_params* const* pars, sim_handle** out) {
-  if (!out) return fail(nullptr, SIM_EINVAL, "out is NULL");
-  *out = nullptr;
-  Flat F;
-  int rc = flatten(n, nets, dems, pars, F);
+// Rewrite the route store with every trip's route back to back (in trip order).
+int compact_routes(sim_handle* h) {
+  const int nt = h->nt;
+  std::vector<int32_t> len(nt > 0 ? nt : 1), off(nt > 0 ? nt : 1);
+  if (nt) CK(cudaMemcpy(len.data(), h->d.rlen, (size_t)nt * 4, cudaMemcpyDeviceToHost));
+  unsigned long long total = 0;
+  for (int i = 0; i < nt; i++) {
+    off[i] = (int32_t)total;
+    total += (unsigned long long)len[i];
+  }
+  if (total >= 2147483647ULL) return fail(h, SIM_EINVAL, "route store above 2^31 links");
+  int32_t *dst = nullptr, *doff = nullptr;
+  int rc = dalloc(h, &dst, (size_t)std::max<unsigned long long>(1, total));
   if (rc) return rc;
-  return create_from_flat(F, out);
-}
-
-int sim_set_stream(sim_handle* h, void* stream) {
-  if (!h) return SIM_EINVAL;
-  h->stream = (cudaStream_t)stream;
+  if ((rc = dalloc(h, &doff, (size_t)std::max(1, nt)))) {
+    dfree(h, dst);
+    return rc;
+  }
+  if (nt) {
+    CK(cudaMemcpy(doff, off.data(), (size_t)nt * 4, cudaMemcpyHostToDevice));
+    launch_compact_routes(h->d.roff, h->d.rlen, h->routes, doff, dst, nt, h->stream);
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaMemcpy(const_cast<int32_t*>(h->d.roff), doff, (size_t)nt * 4, cudaMemcpyDeviceToDevice));
+  }
+  dfree(h, doff);
+  dfree(h, h->routes);
+  h->routes = dst;
+  h->route_cap = total;
   return SIM_OK;
 }
 
-int sim_route(sim_handle* h, const int32_t* link_cost_ds) {
-  if (!h) return SIM_EINVAL;
+// Trip planning (Sec. 6.3.1) for every trip, or, with sel, only for the trips with
+// sel[i] set: their new routes are appended to a copy of the route store, which is
+// then compacted; the other trips keep theirs.  Restarts the run.
+int route_impl(sim_handle* h, const int32_t* link_cost_ds, const std::vector<uint8_t>* sel) {
   const int nn = h->nn, nl = h->nl, nt = h->nt;
   std::vector<int32_t> cost(nl);
   long long cmax = 1;
   for (int e = 0; e < nl; e++) {
-    if (link_cost_ds) {
-      cost[e] = link_cost_ds[e];
-    } else {
-      // Eq. 4: t0 = d / s, in deciseconds rounded half up, at least 1 (binary64)
-      const double dd = (double)h->len[e], ss = (double)h->spd[e];
-      const double tt = h->cost_mode == 1 ? ((10.0 * std::sqrt((double)h->lanes[e])) * dd) / ss : (10.0 * dd) / ss;
-      double c = std::floor(tt + 0.5);
-      if (c < 1.0) c = 1.0;
-      if (c > 1.0e6) c = 1.0e6;
-      cost[e] = (int32_t)c;
-    }
+    cost[e] = link_cost_ds ? link_cost_ds[e] : free_flow_cost(h, e);
     if (cost[e] < 1 || cost[e] > 1000000) return fail(h, SIM_EINVAL, "link costs must be 1..1e6 ds");
     cmax = std::max<long long>(cmax, cost[e]);
   }
@@ -581,7 +627,8 @@ int sim_route(sim_handle* h, const int32_t* link_cost_ds) {
     os[h->lfrom[e] + 1]++;
     is[h->lto[e] + 1]++;
   }
-  for (int i = 0; i < nt; i++) ts[h->origin[i] + 1]++;
+  for (int i = 0; i < nt; i++)
+    if (!sel || (*sel)[i]) ts[h->origin[i] + 1]++;
   for (int v = 0; v < nn; v++) {
     os[v + 1] += os[v];
     is[v + 1] += is[v];
@@ -593,7 +640,8 @@ int sim_route(sim_handle* h, const int32_t* link_cost_ds) {
       ol[fo[h->lfrom[e]]++] = e;
       il[fi[h->lto[e]]++] = e;
     }
-    for (int i = 0; i < nt; i++) tl[ft[h->origin[i]]++] = i;
+    for (int i = 0; i < nt; i++)
+      if (!sel || (*sel)[i]) tl[ft[h->origin[i]]++] = i;
   }
   std::vector<int32_t> origins;
   for (int v = 0; v < nn; v++)
@@ -613,6 +661,7 @@ int sim_route(sim_handle* h, const int32_t* link_cost_ds) {
     for (void* p : tmp) dfree(h, p);
     tmp.clear();
   };
+
   RouteDev R{};
   int rc = SIM_OK;
   int32_t *dos, *dol, *dis, *dil, *dlt, *dcost, *dorig, *dts, *dtl, *ddest;
@@ -677,38 +726,60 @@ int sim_route(sim_handle* h, const int32_t* link_cost_ds) {
   R.work = work;
   R.delta = delta;
   R.ctl = h->d.ctl;
+  // the kept routes (subset mode) stay at the front of the store, new ones follow
+  int32_t* old_routes = nullptr;
+  unsigned long long kept = 0;
+  if (sel) {
+    old_routes = h->routes;
+    kept = h->route_cap;
+    h->routes = nullptr;
+  }
+  unsigned long long n_new = 0;
+  for (int i = 0; i < nt; i++) n_new += (!sel || (*sel)[i]) ? 1 : 0;
   // initial reservation of the route store; a second pass with the exact size follows if it overflows
-  unsigned long long cap = std::max<unsigned long long>(1024, (unsigned long long)std::max(1, nt) * 96ULL);
+  unsigned long long cap = kept + std::max<unsigned long long>(1024, std::max<unsigned long long>(1, n_new) * 96ULL);
   for (int attempt = 0; attempt < 2; attempt++) {
     dfree(h, h->routes);
     h->routes = nullptr;
     if ((rc = dalloc(h, &h->routes, cap))) {
+      dfree(h, old_routes);
+      if (sel) h->routed = false;   // the kept routes are gone with the failed store
       cleanup();
       return rc;
     }
+    if (kept) cudaMemcpy(h->routes, old_routes, kept * 4, cudaMemcpyDeviceToDevice);
     R.routes = h->routes;
     R.cap = cap;
     cudaMemset(work, 0, 4);
     cudaMemset(h->d.ctl, 0, sizeof(Ctl));
+    if (kept) cudaMemcpy(&h->d.ctl->route_cursor, &kept, sizeof(kept), cudaMemcpyHostToDevice);
     if (cudaDeviceSynchronize() != cudaSuccess) {
+      dfree(h, old_routes);
+      if (sel) h->routed = false;   // the kept routes are gone with the failed store
       cleanup();
       return fail(h, SIM_ECUDA, "route setup failed");
     }
     if (R.n_origins > 0) launch_route(R, n_cta, h->stream);
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
+      dfree(h, old_routes);
+      if (sel) h->routed = false;   // the kept routes are gone with the failed store
       cleanup();
       return cuda_fail(h, e, "route kernel");
     }
     Ctl c;
     cudaMemcpy(&c, h->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost);
     if (c.err & kErrUnreach) {
+      dfree(h, old_routes);
+      if (sel) h->routed = false;   // the kept routes are gone with the failed store
       cleanup();
       char buf[96];
       snprintf(buf, sizeof buf, "trip %d: destination unreachable", c.err_info);
       return fail(h, SIM_EUNREACHABLE, buf);
     }
     if (c.err) {
+      dfree(h, old_routes);
+      if (sel) h->routed = false;   // the kept routes are gone with the failed store
       cleanup();
       return fail(h, SIM_EDEVICE, "route extraction failed");
     }
@@ -717,6 +788,10 @@ int sim_route(sim_handle* h, const int32_t* link_cost_ds) {
     cap = c.route_cursor;
   }
   cleanup();
+  if (sel) {
+    dfree(h, old_routes);
+    if ((rc = compact_routes(h))) return rc;
+  }
   h->d.routes = h->routes;
   if ((rc = reset_dynamic(h))) return rc;
   std::vector<uint8_t> st(nt, SIM_PENDING);
@@ -726,6 +801,50 @@ int sim_route(sim_handle* h, const int32_t* link_cost_ds) {
   h->graph_dirty = true;
   h->pgraph_n = -1;
   return SIM_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+int sim_create(const sim_network* net, const sim_demand* dem, const sim_params* par, sim_handle** out) {
+  if (!out) return fail(nullptr, SIM_EINVAL, "out is NULL");
+  *out = nullptr;
+  Flat F;
+  int rc = flatten(1, &net, &dem, &par, F);
+  if (rc) return rc;
+  return create_from_flat(F, out);
+}
+
+int sim_create_batch(int32_t n, const sim_network* const* nets, const sim_demand* const* dems,
+                     const sim_params* const* pars, sim_handle** out) {
+  if (!out) return fail(nullptr, SIM_EINVAL, "out is NULL");
+  *out = nullptr;
+  Flat F;
+  int rc = flatten(n, nets, dems, pars, F);
+  if (rc) return rc;
+  return create_from_flat(F, out);
+}
+
+int sim_set_stream(sim_handle* h, void* stream) {
+  if (!h) return SIM_EINVAL;
+  h->stream = (cudaStream_t)stream;
+  return SIM_OK;
+}
+
+int sim_route(sim_handle* h, const int32_t* link_cost_ds) {
+  if (!h) return SIM_EINVAL;
+  return route_impl(h, link_cost_ds, nullptr);
+}
+
+int sim_reroute(sim_handle* h, const int32_t* link_cost_ds, uint32_t fraction_q16, uint32_t round) {
+  if (!h || !link_cost_ds) return SIM_EINVAL;
+  if (!h->routed) return fail(h, SIM_ESTATE, "sim_reroute before routes exist");
+  if (fraction_q16 > 65536u) return fail(h, SIM_EINVAL, "fraction_q16 must be 0..65536");
+  std::vector<uint8_t> sel(h->nt);
+  for (int i = 0; i < h->nt; i++) sel[i] = reroute_selected(h->hseed[i], round, fraction_q16) ? 1 : 0;
+  return route_impl(h, link_cost_ds, &sel);
 }
 
 int sim_set_routes(sim_handle* h, const int32_t* offsets, const int32_t* links) {
@@ -802,16 +921,27 @@ int sim_step(sim_handle* h, int32_t n_steps) {
   if (!h || n_steps < 0) return SIM_EINVAL;
   if (!h->routed) return fail(h, SIM_ESTATE, "sim_step before sim_route / sim_set_routes");
   if (n_steps == 0) return SIM_OK;
-  if (int rc = check_horizon(h, n_steps)) return rc;
+  long long t0 = 0;
+  if (int rc = check_horizon(h, n_steps, &t0)) return rc;
   if (h->graph_dirty) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->graph) cudaGraphDestroy(h->graph);
-    h->gexec = nullptr;
-    h->graph = nullptr;
+    if (h->gexec_samp) cudaGraphExecDestroy(h->gexec_samp);
+    if (h->graph_samp) cudaGraphDestroy(h->graph_samp);
+    h->gexec = h->gexec_samp = nullptr;
+    h->graph = h->graph_samp = nullptr;
+    Dev dn = h->d;
+    dn.acc_u = nullptr;   // steps between sampling instants skip the sample kernel
     CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-    launch_step(h->d, h->grid, h->has_stop, h->cap_stream);
+    launch_step(dn, h->grid, h->has_stop, h->cap_stream);
     CK(cudaStreamEndCapture(h->cap_stream, &h->graph));
     CK(cudaGraphInstantiate(&h->gexec, h->graph, 0));
+    if (h->d.acc_u) {
+      CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+      launch_step(h->d, h->grid, h->has_stop, h->cap_stream);
+      CK(cudaStreamEndCapture(h->cap_stream, &h->graph_samp));
+      CK(cudaGraphInstantiate(&h->gexec_samp, h->graph_samp, 0));
+    }
     h->graph_dirty = false;
   }
   if (h->exec.mode == SIM_EXEC_PERSISTENT) {
@@ -849,7 +979,11 @@ int sim_step(sim_handle* h, int32_t n_steps) {
     if (h->pexec) CK(cudaGraphLaunch(h->pexec, h->stream));
     else CK(launch_persistent(h->d, h->gs, blocks, x.threads, n_steps, limit, h->stream));
   } else {
-    for (int s = 0; s < n_steps; s++) CK(cudaGraphLaunch(h->gexec, h->stream));
+    const long long every = h->d.acc_u ? h->d.samp_every : 0;
+    for (int s = 0; s < n_steps; s++) {
+      const bool samp = every > 0 && (t0 + s) % every == 0;
+      CK(cudaGraphLaunch(samp ? h->gexec_samp : h->gexec, h->stream));
+    }
   }
   return check_device(h);
 }
@@ -1136,6 +1270,7 @@ cudaError_t ckpt_copy(sim_handle* h, unsigned char* buf, bool save) {
 int sim_adjoint(sim_handle* h, const sim_loss_spec* spec, double* grad_out, double* loss_out) {
   if (!h || !spec || !grad_out || !loss_out || !spec->target) return SIM_EINVAL;
   if (!h->routed) return fail(h, SIM_ESTATE, "sim_adjoint before routes exist");
+  if (h->out_flags) return fail(h, SIM_ESTATE, "sim_adjoint with measured outputs on (sim_set_outputs(h, 0, NULL))");
   const int n_steps = spec->n_steps, every = spec->obs_every;
   const int seg = spec->checkpoint_every > 0 ? spec->checkpoint_every : 64;
   if (n_steps <= 0 || every <= 0 || n_steps % every) return fail(h, SIM_EINVAL, "n_steps must be a multiple of obs_every");
@@ -1303,6 +1438,7 @@ void tune_cache_store(const char* path, const std::string& key, const sim_exec& 
 int sim_autotune(sim_handle* h, int32_t trial_steps, const char* cache_path, sim_exec* chosen) {
   if (!h || trial_steps < 1) return SIM_EINVAL;
   if (!h->routed) return fail(h, SIM_ESTATE, "sim_autotune before routes exist");
+  if (h->out_flags) return fail(h, SIM_ESTATE, "sim_autotune with measured outputs on (its trial steps would count)");
   const std::string key = tune_key(h);
   sim_exec best{};
   if (tune_cache_lookup(cache_path, key, &best) && sim_set_exec(h, &best) == SIM_OK) {
@@ -1364,10 +1500,155 @@ int sim_autotune(sim_handle* h, int32_t trial_steps, const char* cache_path, sim
   return SIM_OK;
 }
 
+// ------------------------------------------------------------------ measured outputs
+int sim_set_outputs(sim_handle* h, uint32_t flags, const sim_sampling* sampling) {
+  if (!h) return SIM_EINVAL;
+  if (flags & ~(uint32_t)(SIM_OUT_EMISSIONS | SIM_OUT_LINK_TIMES | SIM_OUT_EDGE_SAMPLES))
+    return fail(h, SIM_EINVAL, "unknown output flag");
+  int every = 0, per = 0, maxw = 0;
+  if (flags & SIM_OUT_EDGE_SAMPLES) {
+    if (!sampling) return fail(h, SIM_EINVAL, "edge samples need a sim_sampling");
+    every = sampling->every_steps;
+    per = sampling->per_window;
+    maxw = sampling->max_windows;
+    if (every < 1 || per < 1 || maxw < 1) return fail(h, SIM_EINVAL, "sampling sizes must be >= 1");
+    if ((double)maxw * (double)std::max(1, h->nl) * 16.0 > 64.0e9)
+      return fail(h, SIM_EINVAL, "edge-sample store above 64 GB");
+  }
+  Dev& d = h->d;
+  void* olds[] = {d.emis, d.enter, d.tt_sum, d.tt_n, d.acc_u, d.acc_s, d.out_u, d.out_s, d.out_n};
+  for (void* q : olds) dfree(h, q);
+  d.emis = nullptr;
+  d.enter = nullptr;
+  d.tt_sum = nullptr;
+  d.tt_n = nullptr;
+  d.acc_u = d.acc_s = d.out_u = d.out_s = nullptr;
+  d.out_n = nullptr;
+  d.samp_every = d.samp_per = d.samp_max = 0;
+  h->out_flags = 0;
+  h->graph_dirty = true;
+  h->pgraph_n = -1;
+  h->tape_graph_dirty = true;
+  const size_t nt = (size_t)std::max(1, h->nt), nl = (size_t)std::max(1, h->nl);
+  int rc = SIM_OK;
+  if (flags & SIM_OUT_EMISSIONS) {
+    if ((rc = dalloc(h, &d.emis, nt))) return rc;
+  }
+  if (flags & SIM_OUT_LINK_TIMES) {
+    if ((rc = dalloc(h, &d.enter, nt)) || (rc = dalloc(h, &d.tt_sum, nl)) || (rc = dalloc(h, &d.tt_n, nl))) return rc;
+  }
+  if (flags & SIM_OUT_EDGE_SAMPLES) {
+    if ((rc = dalloc(h, &d.acc_u, nl)) || (rc = dalloc(h, &d.acc_s, nl)) ||
+        (rc = dalloc(h, &d.out_u, (size_t)maxw * nl)) || (rc = dalloc(h, &d.out_s, (size_t)maxw * nl)) ||
+        (rc = dalloc(h, &d.out_n, (size_t)maxw)))
+      return rc;
+    d.samp_every = every;
+    d.samp_per = per;
+    d.samp_max = maxw;
+  }
+  h->out_flags = flags;
+  return clear_outputs(h, -1);
+}
+
+int sim_reset_outputs(sim_handle* h) {
+  if (!h) return SIM_EINVAL;
+  return clear_outputs(h, -1);
+}
+
+int sim_read_emissions(sim_handle* h, double* fuel_ml, double* co_g) {
+  if (!h || !fuel_ml || !co_g) return SIM_EINVAL;
+  if (!h->d.emis) return fail(h, SIM_ESTATE, "emissions output is off");
+  std::vector<double2> q((size_t)std::max(1, h->nt));
+  if (h->nt) CK(cudaMemcpyAsync(q.data(), h->d.emis, (size_t)h->nt * 16, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int i = 0; i < h->nt; i++) {
+    fuel_ml[i] = q[i].x;
+    co_g[i] = q[i].y;
+  }
+  return SIM_OK;
+}
+
+int sim_read_link_times(sim_handle* h, int64_t* sum_steps, int32_t* n_exits) {
+  if (!h || !sum_steps || !n_exits) return SIM_EINVAL;
+  if (!h->d.tt_sum) return fail(h, SIM_ESTATE, "link-time output is off");
+  if (h->nl) {
+    CK(cudaMemcpyAsync(sum_steps, h->d.tt_sum, (size_t)h->nl * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(n_exits, h->d.tt_n, (size_t)h->nl * 4, cudaMemcpyDeviceToHost, h->stream));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+
+int sim_read_edge_samples(sim_handle* h, double* util, double* speed, int32_t* n_samples) {
+  if (!h || !util || !speed || !n_samples) return SIM_EINVAL;
+  const Dev& d = h->d;
+  if (!d.acc_u) return fail(h, SIM_ESTATE, "edge-sample output is off");
+  const size_t n = (size_t)d.samp_max * (size_t)h->nl;
+  if (n) {
+    CK(cudaMemcpyAsync(util, d.out_u, n * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(speed, d.out_s, n * 8, cudaMemcpyDeviceToHost, h->stream));
+  }
+  CK(cudaMemcpyAsync(n_samples, d.out_n, (size_t)d.samp_max * 4, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+
+int sim_measured_costs(sim_handle* h, const int32_t* prev_cost_ds, int32_t* cost_ds, double* gap) {
+  if (!h || !prev_cost_ds || !cost_ds) return SIM_EINVAL;
+  const Dev& d = h->d;
+  if (!d.tt_sum) return fail(h, SIM_ESTATE, "link-time output is off");
+  const int nl = h->nl;
+  for (int e = 0; e < nl; e++)
+    if (prev_cost_ds[e] < 1 || prev_cost_ds[e] > 1000000) return fail(h, SIM_EINVAL, "link costs must be 1..1e6 ds");
+  int32_t *dp = nullptr, *dc = nullptr;
+  int rc = dalloc(h, &dp, (size_t)std::max(1, nl));
+  if (rc) return rc;
+  if ((rc = dalloc(h, &dc, (size_t)std::max(1, nl)))) {
+    dfree(h, dp);
+    return rc;
+  }
+  cudaError_t e = cudaSuccess;
+  unsigned long long nd[2] = {0, 0};
+  if (nl) e = cudaMemcpyAsync(dp, prev_cost_ds, (size_t)nl * 4, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&d.ctl->gap_num, 0, 2 * sizeof(unsigned long long), h->stream);
+  if (e == cudaSuccess && nl) launch_measured_costs(d, dp, dc, h->stream);
+  if (e == cudaSuccess && nl) e = cudaMemcpyAsync(cost_ds, dc, (size_t)nl * 4, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(nd, &d.ctl->gap_num, sizeof(nd), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  dfree(h, dp);
+  dfree(h, dc);
+  if (e != cudaSuccess) return cuda_fail(h, e, "measured costs");
+  if (gap) *gap = nd[1] ? (double)nd[0] / (double)nd[1] : 0.0;
+  return SIM_OK;
+}
+
+int sim_equilibrium(sim_handle* h, int32_t n_iter, const uint32_t* fractions_q16, int32_t n_steps, int32_t* cost_out,
+                    double* gap_out) {
+  if (!h || !fractions_q16 || !cost_out || !gap_out) return SIM_EINVAL;
+  if (!h->d.tt_sum) return fail(h, SIM_ESTATE, "sim_equilibrium needs the link-time output");
+  if (n_iter < 1 || n_steps < 1) return fail(h, SIM_EINVAL, "n_iter and n_steps must be >= 1");
+  for (int k = 1; k < n_iter; k++)
+    if (fractions_q16[k] > 65536u) return fail(h, SIM_EINVAL, "fraction_q16 must be 0..65536");
+  const int nl = h->nl;
+  std::vector<int32_t> cost(std::max(1, nl)), meas(std::max(1, nl));
+  for (int e = 0; e < nl; e++) cost[e] = free_flow_cost(h, e);
+  for (int k = 0; k < n_iter; k++) {
+    int rc = k == 0 ? sim_route(h, cost.data()) : sim_reroute(h, cost.data(), fractions_q16[k], (uint32_t)k);
+    if (!rc) rc = sim_step(h, n_steps);
+    if (!rc) rc = sim_measured_costs(h, cost.data(), meas.data(), &gap_out[k]);
+    if (rc) return rc;
+    cost.swap(meas);
+  }
+  if (nl) memcpy(cost_out, cost.data(), (size_t)nl * 4);
+  return SIM_OK;
+}
+
 const char* sim_last_error(const sim_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
 void sim_destroy(sim_handle* h) {
   if (!h) return;
+  if (h->gexec_samp) cudaGraphExecDestroy(h->gexec_samp);
+  if (h->graph_samp) cudaGraphDestroy(h->graph_samp);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->graph) cudaGraphDestroy(h->graph);
   if (h->gexec_tape) cudaGraphExecDestroy(h->gexec_tape);

@@ -72,6 +72,8 @@ struct Ctl {
   unsigned long long route_cursor;  // bump allocator of the route store
   long long tape_t0;                // first step of the segment being taped
   double loss;                      // calibration loss accumulator
+  long long samp_k0;                // first edge-sample index since the outputs were cleared
+  unsigned long long gap_num, gap_den;  // measured-cost gap accumulators
 };
 
 // Forms of Eq. 7 an acceleration can come from (adjoint tape).
@@ -144,6 +146,19 @@ struct Dev {
   // per node
   int32_t* holder;
   unsigned long long* acq;
+  // measured outputs (nullptr when off): fuel and CO per trip (Eq. 8-9); link
+  // traversal times (Sec. 6.3.1); per-edge samples every samp_every steps averaged
+  // over windows of samp_per samples (Sec. 6.4)
+  double2* emis;                   // per trip: (fuel mL, CO g), one 16-byte record
+  int32_t* enter;                  // per trip: step it entered its current link, -1 unknown
+  unsigned long long* tt_sum;      // per link: summed traversal steps
+  int32_t* tt_n;                   // per link: traversals
+  double* acc_u;                   // per link: window sums of utilisation and speed
+  double* acc_s;
+  double* out_u;                   // [samp_max][n_links] window means
+  double* out_s;
+  int32_t* out_n;                  // [samp_max] samples in each finished window
+  int samp_every, samp_per, samp_max;
   // departure queues
   const int32_t* qlinks;
   int n_qlinks;
@@ -235,15 +250,47 @@ __host__ __device__ __forceinline__ void ballistic(float x, float v, float acc, 
   }
 }
 
-// Index into the mandatory-switch table: SplitMix64 finaliser (Steele, Lea & Flood
-// 2014) of (seed ^ vid << 32) ^ hop, top 8 bits.  hseed = seed ^ (vid << 32).
-__host__ __device__ __forceinline__ unsigned mand_index(unsigned long long hseed, int hop) {
-  unsigned long long z = hseed ^ (unsigned long long)(unsigned)hop;
+// SplitMix64 (Steele, Lea & Flood 2014): golden-ratio increment, then its finaliser.
+__host__ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
   z += 0x9E3779B97F4A7C15ULL;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-  z = z ^ (z >> 31);
-  return (unsigned)(z >> 56);
+  return z ^ (z >> 31);
+}
+
+// Index into the mandatory-switch table: top 8 bits of SplitMix64 of
+// (seed ^ vid << 32) ^ hop.  hseed = seed ^ (vid << 32).
+__host__ __device__ __forceinline__ unsigned mand_index(unsigned long long hseed, int hop) {
+  return (unsigned)(splitmix64(hseed ^ (unsigned long long)(unsigned)hop) >> 56);
+}
+
+// Reroute subset of round r (Sec. 6.3.1): the trip is in it when the top 16 bits of
+// SplitMix64 of hseed ^ (2^31 | r) fall below fraction_q16 (1/65536 units).  Bit 31
+// separates these draws from the mandatory-switch ones (hop < 2^31).
+__host__ __device__ __forceinline__ bool reroute_selected(unsigned long long hseed, unsigned round,
+                                                          unsigned fraction_q16) {
+  const unsigned long long lo = 0x80000000ULL | (unsigned long long)(round & 0x7FFFFFFFu);
+  return (unsigned)(splitmix64(hseed ^ lo) >> 48) < fraction_q16;
+}
+
+// Eq. 9, fuel rate (mL/s) at speed v (m/s), acceleration a (m/s^2): idle rate plus
+// 0.072 mL/kJ times the tractive power (drag, inertia, extra engine drag 0.79296 a^2 v
+// when accelerating), the power taken as 0 when negative (the engine idles).  binary32,
+// terms accumulated left to right.
+__device__ __forceinline__ float fuel_rate(float v, float a) {
+  const float v2 = v * v;
+  float pw = 0.269f * v + 0.0171f * v2;
+  pw = pw + 0.000672f * (v2 * v);
+  pw = pw + (1.680f * a) * v;
+  if (a > 0.0f) pw = pw + ((0.79296f * a) * a) * v;
+  return 0.666f + 0.072f * (pw > 0.0f ? pw : 0.0f);
+}
+
+// Eq. 8, CO emission rate (g/s); the equation's speed is in miles per hour.
+__device__ __forceinline__ float co_rate(float v) {
+  const float mph = v / 0.44704f;
+  const float dm = mph - 50.0f;
+  return (-0.064f + 0.0056f * mph) + 0.00026f * (dm * dm);
 }
 
 // Movement class of a -> b -> c from integer node positions.

@@ -218,4 +218,22 @@ void launch_first_links(const int32_t* roff, const int32_t* routes, int n, int32
   k_first_links<<<grid, 256, 0, s>>>(roff, routes, n, out);
 }
 
+// route of every trip copied to its new offset (compaction of the route store)
+__global__ void k_compact_routes(const int32_t* roff, const int32_t* rlen, const int32_t* src,
+                                 const int32_t* new_off, int32_t* dst, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int32_t* a = src + roff[i];
+    int32_t* b = dst + new_off[i];
+    for (int k = 0; k < rlen[i]; k++) b[k] = a[k];
+  }
+}
+
+void launch_compact_routes(const int32_t* roff, const int32_t* rlen, const int32_t* src, const int32_t* new_off,
+                           int32_t* dst, int n, cudaStream_t s) {
+  int grid = (n + 255) / 256;
+  if (grid > 4096) grid = 4096;
+  if (grid < 1) grid = 1;
+  k_compact_routes<<<grid, 256, 0, s>>>(roff, rlen, src, new_off, dst, n);
+}
+
 }  // namespace gbt

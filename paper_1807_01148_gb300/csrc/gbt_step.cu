@@ -435,8 +435,61 @@ __device__ __forceinline__ void ph_decide(const Dev& d) {
 template <bool TAPE>
 __global__ void __launch_bounds__(256, 4) k_decide(Dev d) { ph_decide<TAPE>(d); }
 
+// ------------------------------------------------------------------ measured outputs
+// Sec. 6.3.1: trip vid leaves link e in step t; it entered it in step enter[vid]
+// (-1 when it was already on the link when the outputs were cleared).
+__device__ __forceinline__ void note_exit(const Dev& d, int vid, int e, int t) {
+  const int te = d.enter[vid];
+  if (te >= 0) {
+    atomicAdd(&d.tt_sum[e], (unsigned long long)(t - te));
+    atomicAdd(&d.tt_n[e], 1);
+  }
+}
+
+// Sec. 6.4 per-edge sample of the state at step t (when t is a multiple of samp_every),
+// one thread per link over its contiguous run of the sorted buffer (lanes in order,
+// then position): utilisation = vehicles / (length * lanes / (vehicle length + s0)),
+// speed = their mean speed, or the link's free-flow speed when it is empty.  Window w
+// holds samples w * samp_per .. w * samp_per + samp_per - 1; its last sample writes
+// the means over the samples taken since the outputs were cleared.
+__device__ __forceinline__ void ph_edge_sample(const Dev& d) {
+  const long long t = d.ctl->t;
+  if (t % d.samp_every != 0) return;
+  const long long k = t / d.samp_every;
+  const long long w = k / d.samp_per;
+  const bool closes = (k % d.samp_per) == d.samp_per - 1;
+  const long long k0 = d.ctl->samp_k0;
+  const long long from = w * d.samp_per > k0 ? w * d.samp_per : k0;
+  const double taken = (double)(k - from + 1);
+  GRID_STRIDE(e, d.n_links) {
+    const LinkRec L = d.links[e];
+    const int r0 = d.lane_start[L.lane_base], r1 = d.lane_start[L.lane_base + L.lanes];
+    double vs = 0.0;
+    for (int r = r0; r < r1; r++) vs += (double)d.B.v[r];
+    const int n = r1 - r0;
+    const double cap = ((double)L.len * (double)L.lanes) / ((double)d.vlen + (double)d.cls[L.cls].s0);
+    const double u = d.acc_u[e] + (double)n / cap;
+    const double sp = d.acc_s[e] + (n > 0 ? vs / (double)n : (double)L.v0);
+    if (closes) {
+      const size_t o = (size_t)w * (size_t)d.n_links + (size_t)e;
+      d.out_u[o] = u / taken;
+      d.out_s[o] = sp / taken;
+      d.acc_u[e] = 0.0;
+      d.acc_s[e] = 0.0;
+    } else {
+      d.acc_u[e] = u;
+      d.acc_s[e] = sp;
+    }
+  }
+  if (closes && blockIdx.x == 0 && threadIdx.x == 0) d.out_n[w] = (int32_t)(k - from + 1);
+}
+
+__global__ void k_edge_sample(Dev d) { ph_edge_sample(d); }
+
 // ------------------------------------------------------------------ move
-template <bool TAPE>
+// OUT: the measured outputs are on (a separate instantiation keeps the plain kernel's
+// register count, and so its occupancy, as it is without them)
+template <bool TAPE, bool OUT>
 __device__ __forceinline__ void ph_move(const Dev& d) {
   const int nB = d.ctl->nB;
   const int t = (int)d.ctl->t;
@@ -469,6 +522,13 @@ __device__ __forceinline__ void ph_move(const Dev& d) {
     const float acc = change ? d.at[p] : d.a_own[p];
     float x1, v1;
     ballistic(x, v, acc, d.dt, d.hdt2, x1, v1);
+    if (OUT && d.emis) {
+      // Eq. 8-9 at this step's speed and acceleration, over dt
+      double2 q = d.emis[vid];
+      q.x += (double)(fuel_rate(v, acc) * d.dt);
+      q.y += (double)(co_rate(v) * d.dt);
+      d.emis[vid] = q;
+    }
     TapeRec* rec = nullptr;
     if (TAPE) {
       rec = tape_slot(d, t, vid);
@@ -495,6 +555,7 @@ __device__ __forceinline__ void ph_move(const Dev& d) {
       if (nxt < 0) {
         d.A.link[p] = -1;
         if (rec) rec->branch = kBrArrive;
+        if (OUT && d.tt_sum) note_exit(d, vid, e, t);
         d.status[vid] = kArrived;
         d.arr_step[vid] = (int32_t)t;
         atomicAdd(&d.ctl->n_arr, 1);
@@ -514,6 +575,10 @@ __device__ __forceinline__ void ph_move(const Dev& d) {
         nx = x1 - L.len;
         crossed = true;
         if (rec) rec->crossed = 1;
+        if (OUT && d.tt_sum) {
+          note_exit(d, vid, e, t);
+          d.enter[vid] = t;
+        }
       } else {
         nx = L.len;
         nv = 0.0f;
@@ -540,6 +605,7 @@ __device__ __forceinline__ void ph_move(const Dev& d) {
 // The head of each link's queue of due trips enters at x = 0, v = 0 in the allowed
 // lane with the largest rear space (ties to the lowest lane) that received no
 // vehicle from upstream in this step, if that space is at least s0 + vehicle length.
+template <bool OUT>
 __device__ __forceinline__ void ph_insert(const Dev& d) {
   const int nq = d.n_qlinks;
   const int t = (int)d.ctl->t;
@@ -583,6 +649,7 @@ __device__ __forceinline__ void ph_insert(const Dev& d) {
     d.aidx[slot] = atomicAdd(&d.cnt[L.lane_base + bl], 1);
     d.status[h] = kActive;
     d.ins_step[h] = (int32_t)t;
+    if (OUT && d.enter) d.enter[h] = t;
     d.q_head[e] = hd + 1;
   }
 }
@@ -590,11 +657,13 @@ __device__ __forceinline__ void ph_insert(const Dev& d) {
 
 // Move and departures touch disjoint slots of buffer A (departures append after the
 // sorted vehicles) and read only state of step t, so they share one launch.
-template <bool TAPE>
+template <bool TAPE, bool OUT>
 __global__ void k_move_insert(Dev d) {
-  ph_move<TAPE>(d);
-  if (d.n_qlinks > 0) ph_insert(d);
+  ph_move<TAPE, OUT>(d);
+  if (d.n_qlinks > 0) ph_insert<OUT>(d);
 }
+
+__host__ __device__ __forceinline__ bool outputs_on(const Dev& d) { return d.emis || d.tt_sum; }
 
 __device__ __forceinline__ void ph_finish(const Dev& d) {
   Ctl* c = d.ctl;
@@ -643,6 +712,9 @@ void launch_kernel(int k, const Dev& d, int grid, cudaStream_t s) {
     case kKScatter: k_scatter<<<grid, 256, 0, s>>>(d); break;
     case kKRank: k_rank<<<grid, 256, 0, s>>>(d); break;
     case kKOwn:
+      // the per-edge sample (when enabled) reads the sorted state, like own; its time
+      // is counted with own's
+      if (d.acc_u) k_edge_sample<<<grid, 256, 0, s>>>(d);
       if (d.tape) k_own<true><<<grid, 256, 0, s>>>(d);
       else k_own<false><<<grid, 256, 0, s>>>(d);
       break;
@@ -651,8 +723,9 @@ void launch_kernel(int k, const Dev& d, int grid, cudaStream_t s) {
       else k_decide<false><<<grid, 256, 0, s>>>(d);
       break;
     case kKMoveInsert:
-      if (d.tape) k_move_insert<true><<<grid, 256, 0, s>>>(d);
-      else k_move_insert<false><<<grid, 256, 0, s>>>(d);
+      if (d.tape) k_move_insert<true, false><<<grid, 256, 0, s>>>(d);
+      else if (outputs_on(d)) k_move_insert<false, true><<<grid, 256, 0, s>>>(d);
+      else k_move_insert<false, false><<<grid, 256, 0, s>>>(d);
       break;
     case kKFinish: k_finish<<<1, 1, 0, s>>>(d); break;
     default: break;
@@ -745,12 +818,19 @@ __global__ void k_persistent(Dev d, GridSync* gs, int n_steps, long long limit) 
     if (!grid_barrier(gs, err, limit)) return;
     ph_rank(d);
     if (!grid_barrier(gs, err, limit)) return;
+    // the edge sample and own read the sorted state and write disjoint arrays
+    if (d.acc_u) ph_edge_sample(d);
     ph_own<false>(d);
     if (!grid_barrier(gs, err, limit)) return;
     ph_decide<false>(d);
     if (!grid_barrier(gs, err, limit)) return;
-    ph_move<false>(d);
-    if (d.n_qlinks > 0) ph_insert(d);
+    if (outputs_on(d)) {
+      ph_move<false, true>(d);
+      if (d.n_qlinks > 0) ph_insert<true>(d);
+    } else {
+      ph_move<false, false>(d);
+      if (d.n_qlinks > 0) ph_insert<false>(d);
+    }
     if (!grid_barrier(gs, err, limit)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) ph_finish(d);
   }

@@ -24,7 +24,10 @@ N_KERNELS = 8
 EXPORTS = ["sim_create", "sim_create_batch", "sim_set_stream", "sim_route", "sim_set_routes", "sim_route_size",
            "sim_read_routes", "sim_step", "sim_step_timed", "sim_kernel_name", "sim_read_state", "sim_write_state", "sim_occupancy", "sim_n_lanes",
            "sim_counters", "sim_last_error", "sim_destroy", "sim_set_class_params", "sim_observe", "sim_adjoint",
-           "sim_set_exec", "sim_get_exec", "sim_autotune"]
+           "sim_set_exec", "sim_get_exec", "sim_autotune", "sim_set_outputs", "sim_reset_outputs",
+           "sim_read_emissions", "sim_read_link_times", "sim_read_edge_samples", "sim_measured_costs",
+           "sim_reroute", "sim_equilibrium"]
+OUT_EMISSIONS, OUT_LINK_TIMES, OUT_EDGE_SAMPLES = 1, 2, 4
 SIM_EXEC_GRAPH, SIM_EXEC_PERSISTENT = 0, 1
 
 
@@ -66,6 +69,10 @@ class sim_exec(C.Structure):
 class sim_loss_spec(C.Structure):
     _fields_ = [("n_steps", C.c_int32), ("obs_every", C.c_int32), ("checkpoint_every", C.c_int32),
                 ("target", C.c_void_p)]
+
+
+class sim_sampling(C.Structure):
+    _fields_ = [("every_steps", C.c_int32), ("per_window", C.c_int32), ("max_windows", C.c_int32)]
 
 
 class sim_state_view(C.Structure):
@@ -113,6 +120,15 @@ def lib(path: str | None = None):
         L.sim_set_exec.argtypes = [vp, C.POINTER(sim_exec)]
         L.sim_get_exec.argtypes = [vp, C.POINTER(sim_exec)]
         L.sim_autotune.argtypes = [vp, i32, C.c_char_p, C.POINTER(sim_exec)]
+        u32 = C.c_uint32
+        L.sim_set_outputs.argtypes = [vp, u32, C.POINTER(sim_sampling)]
+        L.sim_reset_outputs.argtypes = [vp]
+        L.sim_read_emissions.argtypes = [vp, vp, vp]
+        L.sim_read_link_times.argtypes = [vp, vp, vp]
+        L.sim_read_edge_samples.argtypes = [vp, vp, vp, vp]
+        L.sim_measured_costs.argtypes = [vp, vp, vp, vp]
+        L.sim_reroute.argtypes = [vp, vp, u32, u32]
+        L.sim_equilibrium.argtypes = [vp, i32, vp, i32, vp, vp]
         _lib = L
     return _lib
 
@@ -168,12 +184,14 @@ class Sim:
     ``sim_create_batch``.  Scenarios are the dicts of ``paper_1807_01148_gb300.scenarios``.
     """
 
-    def __init__(self, scenario=None, *, _handle=None, n_trips=None, n_nodes=None):
+    def __init__(self, scenario=None, *, _handle=None, n_trips=None, n_nodes=None, n_links=None):
         L = lib()
+        self._max_windows = 0
         if _handle is not None:
             self.h = _handle
             self.n_trips = n_trips
             self.n_nodes = n_nodes
+            self.n_links = n_links
         else:
             keep = _Keep()
             n, d, p = _structs(scenario, keep)
@@ -184,6 +202,7 @@ class Sim:
             self.h = h
             self.n_trips = scenario["demand"]["n_trips"]
             self.n_nodes = scenario["network"]["n_nodes"]
+            self.n_links = scenario["network"]["n_links"]
         ln = C.c_int64()
         L.sim_n_lanes(self.h, C.byref(ln))
         self.n_lanes = ln.value
@@ -202,7 +221,8 @@ class Sim:
         if rc != SIM_OK:
             raise SimError(rc, L.sim_last_error(None).decode())
         return cls(_handle=h, n_trips=sum(s["demand"]["n_trips"] for s in scenarios),
-                   n_nodes=sum(s["network"]["n_nodes"] for s in scenarios))
+                   n_nodes=sum(s["network"]["n_nodes"] for s in scenarios),
+                   n_links=sum(s["network"]["n_links"] for s in scenarios))
 
     def _check(self, rc):
         if rc != SIM_OK:
@@ -312,6 +332,53 @@ class Sim:
         self._check(lib().sim_autotune(self.h, int(trial_steps),
                                        cache_path.encode() if cache_path else None, C.byref(e)))
         return e.as_dict()
+
+    # ---- measured outputs (Eq. 8-9, Sec. 6.3.1, Sec. 6.4)
+    def set_outputs(self, flags, sample_every=120, per_window=6, max_windows=0):
+        smp = sim_sampling(int(sample_every), int(per_window), int(max_windows))
+        self._check(lib().sim_set_outputs(self.h, int(flags), C.byref(smp)))
+        self._max_windows = int(max_windows) if flags & OUT_EDGE_SAMPLES else 0
+
+    def reset_outputs(self):
+        self._check(lib().sim_reset_outputs(self.h))
+
+    def emissions(self):
+        fuel = np.zeros(self.n_trips, np.float64)
+        co = np.zeros(self.n_trips, np.float64)
+        self._check(lib().sim_read_emissions(self.h, _p(fuel), _p(co)))
+        return fuel, co
+
+    def link_times(self):
+        s = np.zeros(self.n_links, np.int64)
+        n = np.zeros(self.n_links, np.int32)
+        self._check(lib().sim_read_link_times(self.h, _p(s), _p(n)))
+        return s, n
+
+    def edge_samples(self):
+        w = self._max_windows
+        u = np.zeros((w, self.n_links), np.float64)
+        sp = np.zeros((w, self.n_links), np.float64)
+        n = np.zeros(w, np.int32)
+        self._check(lib().sim_read_edge_samples(self.h, _p(u), _p(sp), _p(n)))
+        return u, sp, n
+
+    def measured_costs(self, prev):
+        prev = np.ascontiguousarray(prev, np.int32)
+        out = np.zeros(self.n_links, np.int32)
+        gap = np.zeros(1, np.float64)
+        self._check(lib().sim_measured_costs(self.h, _p(prev), _p(out), _p(gap)))
+        return out, float(gap[0])
+
+    def reroute(self, costs, fraction_q16, round_):
+        c = np.ascontiguousarray(costs, np.int32)
+        self._check(lib().sim_reroute(self.h, _p(c), int(fraction_q16), int(round_)))
+
+    def equilibrium(self, fractions_q16, n_steps):
+        f = np.ascontiguousarray(fractions_q16, np.uint32)
+        cost = np.zeros(self.n_links, np.int32)
+        gap = np.zeros(len(f), np.float64)
+        self._check(lib().sim_equilibrium(self.h, len(f), _p(f), int(n_steps), _p(cost), _p(gap)))
+        return cost, gap
 
     def counters(self):
         c = sim_counters_t()

@@ -423,3 +423,26 @@ def test_equilibrium_loop_is_reroute_with_previous_measurement():
     first = links[off[:-1]]
     assert 0 < (first == 0).sum() < b.n_trips
     assert gaps[1] < gaps[0] and gaps[3] <= gaps[1]
+
+
+def test_mid_run_clear_restarts_windows():
+    # cleared at t = 130 with samples every 60 steps, windows of 2: the next instant is 180
+    # (sample 3), so window 1 closes with that one sample and window 2 with two
+    sc = S.small_grid()
+    o = O.OracleSim(sc)
+    o.route()
+    o.set_outputs(7, 60, 2, 16)
+    o.step(130)
+    assert o.edge_samples()[2][0] == 2
+    o.reset_outputs()
+    assert (o.emissions()[0] == 0).all() and (o.link_times()[1] == 0).all()
+    assert (o.edge_samples()[2] == 0).all()
+    st = o.state()
+    o.step(500)
+    n = o.edge_samples()[2]
+    assert n[0] == 0 and n[1] == 1 and (n[2:5] == 2).all()
+    # trips on a link at the clear are not counted on that link
+    s, cnt = o.link_times()
+    first_exit = cnt.sum()
+    assert first_exit > 0
+    del st
