@@ -1536,3 +1536,184 @@ int orc_equilibrium(orc_sim* S, int32_t n_iter, const uint32_t* fractions_q16, i
   free(cost); free(meas);
   return rc;
 }
+
+/* ------------------------------------------------------------------ static assignment */
+/* Eq. 3 (BPR): t = t0 (1 + alpha (x / c)^beta), integer beta by repeated products,
+ * t0 = length / speed (Eq. 4, seconds), binary64. */
+static double bpr_time(double t0, double x, double c, double alpha, int beta) {
+  double r = x / c, p = 1.0;
+  for (int k = 0; k < beta; k++) p = p * r;
+  return t0 * (1.0 + alpha * p);
+}
+
+/* Beckmann term of one link (Eq. 6 objective): integral of Eq. 3 from 0 to x. */
+static double bpr_integral(double t0, double x, double c, double alpha, int beta) {
+  double r = x / c, p = 1.0;
+  for (int k = 0; k < beta; k++) p = p * r;
+  return t0 * x * (1.0 + alpha * p / (double)(beta + 1));
+}
+
+/* Sums whose value steers the algorithm (the line search's derivative sign, the gap,
+ * the objective) are taken exactly: every term is rounded to the grid 2^-S, with S the
+ * largest shift for which n terms bounded by B stay below 2^62 in magnitude, and the
+ * integers are added.  The result then depends on no summation order. */
+static double fp_scale(double bound, int n) {
+  int E = 0;
+  frexp(bound * (double)(n > 0 ? n : 1), &E);
+  int S = 62 - E;
+  if (S > 100) S = 100;
+  return ldexp(1.0, S);
+}
+
+/* All-or-nothing assignment (Sec. 5.2, step 2 of Frank-Wolfe): every trip on its
+ * canonical shortest path under the integer costs q (the tie rule of orc_route);
+ * flow[e] = number of trips using link e. */
+static int aon_flows(const orc_sim* S, const int32_t* q, double* flow) {
+  int nn = S->nn, nl = S->nl, nt = S->nt;
+  int* os = (int*)xcalloc(nn + 1, sizeof(int));
+  int* ol = (int*)xcalloc(zsz(nl), sizeof(int));
+  build_csr(nn, nl, S->lf, os, ol);
+  int* ts = (int*)xcalloc(nn + 1, sizeof(int));
+  int* tl = (int*)xcalloc(zsz(nt), sizeof(int));
+  build_csr(nn, nt, S->orig, ts, tl);
+  int64_t* dist = (int64_t*)xcalloc(nn, 8);
+  hent* heap = (hent*)xcalloc(nl + 1, sizeof(hent));
+  int64_t* cnt = (int64_t*)xcalloc(zsz(nl), 8);
+  int rc = OK;
+  for (int o = 0; o < nn && rc == OK; o++) {
+    if (ts[o] == ts[o + 1]) continue;
+    dijkstra(nn, os, ol, S->lt, q, o, dist, heap);
+    for (int k = ts[o]; k < ts[o + 1] && rc == OK; k++) {
+      int d = S->dest[tl[k]];
+      if (d == o) { rc = EINV; break; }
+      if (dist[d] == INT64_MAX) { rc = EUNREACH; break; }
+      int v = d;
+      while (v != o) {
+        int pick = -1;
+        for (int j = S->in_start[v]; j < S->in_start[v + 1]; j++) {
+          int e = S->in_list[j];
+          int u = S->lf[e];
+          if (dist[u] != INT64_MAX && dist[u] + q[e] == dist[v]) { pick = e; break; }
+        }
+        if (pick < 0) { rc = ESTATE; break; }
+        cnt[pick]++;
+        v = S->lf[pick];
+      }
+    }
+  }
+  for (int e = 0; e < nl; e++) flow[e] = (double)cnt[e];
+  free(os); free(ol); free(ts); free(tl); free(dist); free(heap); free(cnt);
+  return rc;
+}
+
+/* Integer routing costs of the travel times t: units of max(0.1 s, max t / qmax), rounded
+ * half up, within 1 .. qmax, qmax = min(1e6, (2e9 - 1) / n_nodes) so that no path
+ * length can pass 2^31 in the shortest-path search. */
+static void quantize_costs(const orc_sim* S, const double* t, int32_t* q) {
+  int64_t qmax = (2000000000LL - 1) / (S->nn > 0 ? S->nn : 1);
+  if (qmax > 1000000) qmax = 1000000;
+  double tmax = 0.0;
+  for (int e = 0; e < S->nl; e++) if (t[e] > tmax) tmax = t[e];
+  double unit = tmax / (double)qmax;
+  if (unit < 0.1) unit = 0.1;
+  for (int e = 0; e < S->nl; e++) {
+    double c = floor(t[e] / unit + 0.5);
+    if (c < 1.0) c = 1.0;
+    if (c > (double)qmax) c = (double)qmax;
+    q[e] = (int32_t)c;
+  }
+}
+
+/* Static user equilibrium (Sec. 5.2, Eq. 6) by Frank-Wolfe with BPR link times (Eq. 3):
+ *   x_0 = all-or-nothing on the free-flow times;
+ *   iteration k: t = BPR(x_k); y_k = all-or-nothing on t; gap_k = (t.x - t.y) / t.x;
+ *     step a_k in [0, 1] minimising the Beckmann objective along x_k + a (y_k - x_k):
+ *     bisection (bisect_iter halvings) on the sign of its derivative
+ *     sum_e t_e(x_e + a d_e) d_e, a_k = 1 when that is not positive at a = 1 and 0 when it
+ *     is not negative at a = 0; x_{k+1} = x_k + a_k (y_k - x_k).
+ * Demand: one vehicle per trip.  capacity[e] > 0 in vehicles over the same period.
+ * Outputs: flow and BPR time at x_K, gap[k] and step[k] for k < K, objective[k] at
+ * x_k for k <= K. */
+int orc_assign_static(orc_sim* S, const double* capacity, double alpha, int32_t beta, int32_t max_iter,
+                      int32_t bisect_iter, double* flow_out, double* time_out, double* gap, double* step,
+                      double* objective) {
+  int nl = S->nl;
+  if (!capacity || beta < 1 || beta > 8 || !(alpha >= 0.0) || max_iter < 0 || bisect_iter < 0) return EINV;
+  for (int e = 0; e < nl; e++) if (!(capacity[e] > 0.0)) return EINV;
+  double* t0 = (double*)xcalloc(zsz(nl), 8);
+  double* x = (double*)xcalloc(zsz(nl), 8);
+  double* y = (double*)xcalloc(zsz(nl), 8);
+  double* t = (double*)xcalloc(zsz(nl), 8);
+  int32_t* q = (int32_t*)xcalloc(zsz(nl), 4);
+  for (int e = 0; e < nl; e++) t0[e] = (double)S->len[e] / (double)S->spd[e];
+  quantize_costs(S, t0, q);
+  int rc = aon_flows(S, q, x);
+  for (int k = 0; k <= max_iter && rc == OK; k++) {
+    /* objective at x_k */
+    double bo = 0.0;
+    for (int e = 0; e < nl; e++) {
+      double f = bpr_integral(t0[e], x[e], capacity[e], alpha, beta);
+      if (f > bo) bo = f;
+    }
+    double so = fp_scale(bo, nl);
+    long long io = 0;
+    for (int e = 0; e < nl; e++) io += llrint(bpr_integral(t0[e], x[e], capacity[e], alpha, beta) * so);
+    objective[k] = (double)io / so;
+    if (k == max_iter) break;
+    /* direction */
+    for (int e = 0; e < nl; e++) t[e] = bpr_time(t0[e], x[e], capacity[e], alpha, beta);
+    quantize_costs(S, t, q);
+    rc = aon_flows(S, q, y);
+    if (rc != OK) break;
+    double bg = 0.0;
+    for (int e = 0; e < nl; e++) {
+      double m = (x[e] > y[e] ? x[e] : y[e]) * t[e];
+      if (m > bg) bg = m;
+    }
+    double sg = fp_scale(bg, nl);
+    long long tx = 0, ty = 0;
+    for (int e = 0; e < nl; e++) { tx += llrint(t[e] * x[e] * sg); ty += llrint(t[e] * y[e] * sg); }
+    gap[k] = tx > 0 ? (double)(tx - ty) / (double)tx : 0.0;
+    /* line search */
+    double bl = 0.0;
+    for (int e = 0; e < nl; e++) {
+      double d = y[e] - x[e];
+      double m = bpr_time(t0[e], x[e] > y[e] ? x[e] : y[e], capacity[e], alpha, beta) * fabs(d);
+      if (m > bl) bl = m;
+    }
+    double sl = fp_scale(bl, nl);
+#define DERIV_SIGN(A, OUT) do { long long g_ = 0; \
+      for (int e = 0; e < nl; e++) { double d_ = y[e] - x[e]; \
+        g_ += llrint(bpr_time(t0[e], x[e] + (A) * d_, capacity[e], alpha, beta) * d_ * sl); } \
+      (OUT) = g_; } while (0)
+    long long g0, g1;
+    DERIV_SIGN(0.0, g0);
+    DERIV_SIGN(1.0, g1);
+    double a;
+    if (g0 >= 0) a = 0.0;
+    else if (g1 <= 0) a = 1.0;
+    else {
+      double lo = 0.0, hi = 1.0;
+      for (int it = 0; it < bisect_iter; it++) {
+        double mid = 0.5 * (lo + hi);
+        long long gm;
+        DERIV_SIGN(mid, gm);
+        if (gm > 0) hi = mid; else lo = mid;
+      }
+      a = 0.5 * (lo + hi);
+    }
+#undef DERIV_SIGN
+    step[k] = a;
+    for (int e = 0; e < nl; e++) x[e] = x[e] + a * (y[e] - x[e]);
+  }
+  if (rc == OK)
+    for (int e = 0; e < nl; e++) {
+      flow_out[e] = x[e];
+      time_out[e] = bpr_time(t0[e], x[e], capacity[e], alpha, beta);
+    }
+  free(t0); free(x); free(y); free(t); free(q);
+  return rc;
+}
+
+/* building block for the pins: all-or-nothing flows on integer costs */
+int orc_aon(orc_sim* S, const int32_t* cost, double* flow) { return aon_flows(S, cost, flow); }

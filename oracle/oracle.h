@@ -77,6 +77,12 @@ int  orc_reroute(orc_sim*, const int32_t* link_cost_ds, uint32_t fraction_q16, u
 int  orc_equilibrium(orc_sim*, int32_t n_iter, const uint32_t* fractions_q16, int32_t n_steps,
                      int32_t* cost_out, double* gap);
 
+/* static user equilibrium (Sec. 5.2, Eq. 6) by Frank-Wolfe on BPR times (Eq. 3) */
+int  orc_assign_static(orc_sim*, const double* capacity, double alpha, int32_t beta, int32_t max_iter,
+                       int32_t bisect_iter, double* flow, double* time, double* gap, double* step,
+                       double* objective);
+int  orc_aon(orc_sim*, const int32_t* cost, double* flow);
+
 /* building blocks exposed for the pin tests */
 int   orc_reroute_selected(uint64_t seed, int32_t vid, uint32_t round, uint32_t fraction_q16);
 float orc_co_rate(float v);

@@ -97,6 +97,8 @@ def lib():
         L.orc_reroute.argtypes = [vp, vp, u32, u32]
         L.orc_equilibrium.argtypes = [vp, i32, vp, i32, vp, vp]
         L.orc_reroute_selected.argtypes = [C.c_uint64, i32, u32, u32]
+        L.orc_assign_static.argtypes = [vp, vp, C.c_double, i32, i32, i32, vp, vp, vp, vp, vp]
+        L.orc_aon.argtypes = [vp, vp, vp]
         L.orc_co_rate.argtypes = [f32]
         L.orc_co_rate.restype = f32
         L.orc_fuel_rate.argtypes = [f32, f32]
@@ -287,6 +289,24 @@ class OracleSim:
         gap = np.zeros(len(f), np.float64)
         _check(lib().orc_equilibrium(self.h, len(f), _p(f), int(n_steps), _p(cost), _p(gap)), "orc_equilibrium")
         return cost, gap
+
+    # ---- static user equilibrium (Sec. 5.2, Eq. 3, Eq. 6)
+    def assign_static(self, capacity, alpha=0.15, beta=4, max_iter=20, bisect_iter=30):
+        cap = np.ascontiguousarray(capacity, np.float64)
+        flow = np.zeros(self.n_links, np.float64)
+        time = np.zeros(self.n_links, np.float64)
+        gap = np.zeros(max(1, max_iter), np.float64)
+        step = np.zeros(max(1, max_iter), np.float64)
+        obj = np.zeros(max_iter + 1, np.float64)
+        _check(lib().orc_assign_static(self.h, _p(cap), float(alpha), int(beta), int(max_iter), int(bisect_iter),
+                                       _p(flow), _p(time), _p(gap), _p(step), _p(obj)), "orc_assign_static")
+        return dict(flow=flow, time=time, gap=gap[:max_iter], step=step[:max_iter], objective=obj)
+
+    def aon(self, costs):
+        c = np.ascontiguousarray(costs, np.int32)
+        flow = np.zeros(self.n_links, np.float64)
+        _check(lib().orc_aon(self.h, _p(c), _p(flow)), "orc_aon")
+        return flow
 
     def node_holder(self):
         h = np.zeros(self.n_nodes, np.int32)

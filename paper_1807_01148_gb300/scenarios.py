@@ -349,6 +349,30 @@ def small_metro(nx: int = 24, ny: int = 20, n_trips: int = 4000, steps: int = 12
     return sc
 
 
+# --------------------------------------------------------------------------- BPR capacities
+# Table 3 (capacity defaults, vehicles per lane per hour, by edge type and lanes 1/2/3/4+)
+CAPACITY_VPHPL = {
+    "motorway": (1900, 2000, 2000, 2200), "trunk": (1900, 2000, 2000, 2000),
+    "primary": (1000, 1000, 1000, 1000), "secondary": (900, 900, 900, 900),
+    "tertiary": (900, 900, 900, 900), "unclassified": (800, 800, 800, 800), "road": (900, 900, 900, 900),
+}
+# edge type standing for each class of the synthetic networks: metro local / arterial /
+# freeway; the uniform grid's links are plain roads
+METRO_EDGE_TYPES = ("unclassified", "primary", "motorway")
+
+
+def bpr_capacity(sc: dict, period_h: float, edge_types=None) -> np.ndarray:
+    """Capacity of every link over an assignment period of period_h hours: the Table 3
+    lane capacity of its edge type and lane count, times lanes, times period_h."""
+    net = sc["network"]
+    lanes = net["link_lanes"].astype(np.int64)
+    cls = net["link_class"].astype(np.int64)
+    kinds = edge_types or ("road",) * (int(cls.max()) + 1 if len(cls) else 1)
+    per_lane = np.array([[CAPACITY_VPHPL[kinds[c]][min(k, 4) - 1] for k in (1, 2, 3, 4)]
+                         for c in range(len(kinds))], np.float64)
+    return per_lane[cls, np.minimum(lanes, 4) - 1] * lanes * float(period_h)
+
+
 # --------------------------------------------------------------------------- snapshots
 def random_walk_routes(sc: dict, min_hops: int = 20, max_hops: int = 120, seed: int = BASE_SEED + 20):
     """Explicit routes for every trip: a random walk from the trip's origin that never
