@@ -346,6 +346,36 @@ int sim_reroute(sim_handle* h, const int32_t* link_cost_ds, uint32_t fraction_q1
 int sim_equilibrium(sim_handle* h, int32_t n_iter, const uint32_t* fractions_q16, int32_t n_steps,
                     int32_t* cost_out, double* gap_out);
 
+/* ---------------------------------------------------------------- static assignment
+ * Static user equilibrium (Sec. 5.2, Eq. 6) of the handle's trips (one vehicle each) on
+ * its network, by Frank-Wolfe with BPR link times (Eq. 3):
+ *   t_e = t0_e (1 + alpha (x_e / capacity_e)^beta), t0_e = length / speed (Eq. 4, s);
+ *   x_0 = all-or-nothing assignment on t0; iteration k: y_k = all-or-nothing on t(x_k),
+ *   gap_k = (t.x_k - t.y_k) / t.x_k, step a_k in [0, 1] minimising the Beckmann objective
+ *   sum_e int_0^{x_e} t_e along x_k + a (y_k - x_k) (bisection on the sign of its
+ *   derivative; a_k = 0 when it is not negative at 0, 1 when it is not positive at 1),
+ *   x_{k+1} = x_k + a_k (y_k - x_k).
+ * All-or-nothing: every trip on the canonical shortest path of sim_route (GPU trees per
+ * origin) under integer costs, the times on a grid of max(0.1 s, max t / qmax) with
+ * qmax = min(1e6, (2e9 - 1) / n_nodes), rounded half up, within 1..qmax.  Sums that
+ * decide anything are exact: terms rounded to a 2^-S grid (S from a bound of the terms)
+ * and added as 64-bit integers, so results do not depend on the order of the GPU's
+ * atomics.  The vehicle state and routes of the handle are not touched. */
+typedef struct {
+  const double* capacity;   /* host [n_links], vehicles over the same period as the demand, > 0 */
+  double alpha;             /* 0.15 in the original BPR curve */
+  int32_t beta;             /* 4 in the original BPR curve; 1..8 */
+  int32_t max_iter;         /* Frank-Wolfe iterations after the initial assignment, >= 0 */
+  int32_t bisect_iter;      /* halvings of the line search, 0..60 (30 gives 1e-9) */
+} sim_assign_spec;
+
+/* Outputs (host arrays): flow [n_links] = x_K, time [n_links] = t(x_K), gap [max_iter],
+ * step [max_iter], objective [max_iter + 1] (at x_0 .. x_K; gap and step may be NULL when
+ * max_iter = 0).  Errors: SIM_EINVAL (spec, capacities, origin == destination),
+ * SIM_EUNREACHABLE, SIM_ENOMEM, SIM_ECUDA. */
+int sim_assign_static(sim_handle* h, const sim_assign_spec* spec, double* flow, double* time, double* gap,
+                      double* step, double* objective);
+
 /* Largest graph sim_sssp_static accepts (nodes). */
 #define SIM_SSSP_STATIC_MAX_NODES 262144
 

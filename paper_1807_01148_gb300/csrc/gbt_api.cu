@@ -30,6 +30,22 @@ void launch_adj_step(const Dev& d, int grid, cudaStream_t s, const TapeRec* slab
                      const double* lv, const double* res, double* nx, double* nv, double* grad, int n_class);
 void launch_first_links(const int32_t* roff, const int32_t* routes, int n, int32_t* out, cudaStream_t s);
 void launch_measured_costs(const Dev& d, const int32_t* prev, int32_t* out, cudaStream_t s);
+void launch_fw_t0(const float* len, const float* spd, double* t0, int n, cudaStream_t s);
+void launch_fw_counts(const unsigned* cnt, double* x, int n, cudaStream_t s);
+void launch_fw_time(const double* t0, const double* x, const double* cap, double alpha, int beta, double* t,
+                    unsigned long long* tmax, int n, cudaStream_t s);
+void launch_fw_quantize(const double* t, double unit, int qmax, int32_t* q, int n, cudaStream_t s);
+void launch_fw_bounds(const double* t0, const double* x, const unsigned* y, const double* t, const double* cap,
+                      double alpha, int beta, unsigned long long* out, int n, cudaStream_t s);
+void launch_fw_gap_sums(const double* t, const double* x, const unsigned* y, double scale, unsigned long long* out,
+                        int n, cudaStream_t s);
+void launch_fw_deriv(const double* t0, const double* x, const unsigned* y, const double* cap, double alpha, int beta,
+                     double a, double scale, unsigned long long* out, int n, cudaStream_t s);
+void launch_fw_update(double* x, const unsigned* y, double a, int n, cudaStream_t s);
+void launch_fw_objective(const double* t0, const double* x, const double* cap, double alpha, int beta, bool bound,
+                         double scale, unsigned long long* out, int n, cudaStream_t s);
+void launch_fw_final_time(const double* t0, const double* x, const double* cap, double alpha, int beta, double* t,
+                          int n, cudaStream_t s);
 void launch_compact_routes(const int32_t* roff, const int32_t* rlen, const int32_t* src, const int32_t* new_off,
                            int32_t* dst, int n, cudaStream_t s);
 int persistent_max_blocks_per_sm(int threads);
@@ -609,7 +625,10 @@ int compact_routes(sim_handle* h) {
 // Trip planning (Sec. 6.3.1) for every trip, or, with sel, only for the trips with
 // sel[i] set: their new routes are appended to a copy of the route store, which is
 // then compacted; the other trips keep theirs.  Restarts the run.
-int route_impl(sim_handle* h, const int32_t* link_cost_ds, const std::vector<uint8_t>* sel) {
+// With flow (device, [n_links]): all-or-nothing mode, flow[e] = trips whose path uses e;
+// routes and vehicle state are left as they are.
+int route_impl(sim_handle* h, const int32_t* link_cost_ds, const std::vector<uint8_t>* sel,
+               unsigned* flow = nullptr) {
   const int nn = h->nn, nl = h->nl, nt = h->nt;
   std::vector<int32_t> cost(nl);
   long long cmax = 1;
@@ -726,6 +745,38 @@ int route_impl(sim_handle* h, const int32_t* link_cost_ds, const std::vector<uin
   R.work = work;
   R.delta = delta;
   R.ctl = h->d.ctl;
+  if (flow) {
+    // counts on a scratch control block, so that the simulation's counters stay intact
+    Ctl* fctl;
+    if ((rc = talloc(&fctl, 1))) {
+      cleanup();
+      return rc;
+    }
+    R.ctl = fctl;
+    R.routes = nullptr;
+    R.cap = 0;
+    R.flow = flow;
+    cudaMemset(work, 0, 4);
+    cudaMemset(fctl, 0, sizeof(Ctl));
+    cudaMemset(flow, 0, (size_t)std::max(1, nl) * 4);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+      cleanup();
+      return fail(h, SIM_ECUDA, "all-or-nothing setup failed");
+    }
+    if (R.n_origins > 0) launch_route(R, n_cta, h->stream);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    Ctl c{};
+    if (e == cudaSuccess) e = cudaMemcpy(&c, fctl, sizeof(Ctl), cudaMemcpyDeviceToHost);
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(h, e, "all-or-nothing kernel");
+    if (c.err & kErrUnreach) {
+      char buf[96];
+      snprintf(buf, sizeof buf, "trip %d: destination unreachable", c.err_info);
+      return fail(h, SIM_EUNREACHABLE, buf);
+    }
+    if (c.err) return fail(h, SIM_EDEVICE, "all-or-nothing path extraction failed");
+    return SIM_OK;
+  }
   // the kept routes (subset mode) stay at the front of the store, new ones follow
   int32_t* old_routes = nullptr;
   unsigned long long kept = 0;
@@ -1640,6 +1691,157 @@ int sim_equilibrium(sim_handle* h, int32_t n_iter, const uint32_t* fractions_q16
     cost.swap(meas);
   }
   if (nl) memcpy(cost_out, cost.data(), (size_t)nl * 4);
+  return SIM_OK;
+}
+
+// ------------------------------------------------------------------ static assignment
+namespace {
+// 2^S with S the largest shift (<= 100) for which n terms of magnitude <= bound sum to
+// less than 2^62
+double fixed_scale(double bound, int n) {
+  int E = 0;
+  std::frexp(bound * (double)std::max(n, 1), &E);
+  return std::ldexp(1.0, std::min(62 - E, 100));
+}
+}  // namespace
+
+int sim_assign_static(sim_handle* h, const sim_assign_spec* spec, double* flow_out, double* time_out, double* gap_out,
+                      double* step_out, double* objective_out) {
+  if (!h || !spec || !spec->capacity || !flow_out || !time_out || !objective_out) return SIM_EINVAL;
+  const int nl = h->nl, nn = h->nn, K = spec->max_iter, beta = spec->beta;
+  const double alpha = spec->alpha;
+  if (beta < 1 || beta > 8 || !(alpha >= 0.0) || K < 0 || spec->bisect_iter < 0 || spec->bisect_iter > 60)
+    return fail(h, SIM_EINVAL, "need 1 <= beta <= 8, alpha >= 0, max_iter >= 0, 0 <= bisect_iter <= 60");
+  if (K > 0 && (!gap_out || !step_out)) return SIM_EINVAL;
+  for (int e = 0; e < nl; e++)
+    if (!(spec->capacity[e] > 0.0) || !std::isfinite(spec->capacity[e]))
+      return fail(h, SIM_EINVAL, "capacities must be finite and > 0");
+  const size_t L = (size_t)std::max(1, nl);
+  double *t0 = nullptr, *x = nullptr, *t = nullptr, *cap = nullptr;
+  unsigned* y = nullptr;
+  int32_t* q = nullptr;
+  float *dlen = nullptr, *dspd = nullptr;
+  unsigned long long* red = nullptr;
+  std::vector<void*> mine;
+  auto take = [&](auto** p, size_t n) -> int {
+    int rc = dalloc(h, p, n);
+    if (!rc) mine.push_back(*p);
+    return rc;
+  };
+  auto release = [&]() {
+    for (void* p : mine) dfree(h, p);
+    mine.clear();
+  };
+  int rc = SIM_OK;
+  if ((rc = take(&t0, L)) || (rc = take(&x, L)) || (rc = take(&t, L)) || (rc = take(&cap, L)) ||
+      (rc = take(&y, L)) || (rc = take(&q, L)) || (rc = take(&dlen, L)) || (rc = take(&dspd, L)) ||
+      (rc = take(&red, 4))) {
+    release();
+    return rc;
+  }
+  cudaStream_t s = h->stream;
+  const long long qmax = std::min<long long>(1000000, (2000000000LL - 1) / std::max(1, nn));
+  std::vector<int32_t> qh(L);
+  unsigned long long hr[4];
+  cudaError_t e = cudaSuccess;
+  auto put = [&](void* dst, const void* src, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+  };
+  auto get = [&](void* dst, const void* src, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  };
+  auto zero_red = [&]() {
+    if (e == cudaSuccess) e = cudaMemsetAsync(red, 0, 4 * sizeof(unsigned long long), s);
+  };
+  // direction finding: integer costs of the times in t (largest time in red[0]), then
+  // all-or-nothing counts into y
+  auto aon = [&]() -> int {
+    get(hr, red, sizeof(unsigned long long));
+    if (e != cudaSuccess) return cuda_fail(h, e, "assignment");
+    double tmax;
+    memcpy(&tmax, &hr[0], sizeof tmax);
+    const double unit = std::max(0.1, tmax / (double)qmax);
+    launch_fw_quantize(t, unit, (int)qmax, q, nl, s);
+    get(qh.data(), q, (size_t)nl * 4);
+    if (e != cudaSuccess) return cuda_fail(h, e, "assignment");
+    return route_impl(h, qh.data(), nullptr, y);
+  };
+  put(dlen, h->len.data(), (size_t)nl * 4);
+  put(dspd, h->spd.data(), (size_t)nl * 4);
+  put(cap, spec->capacity, (size_t)nl * 8);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, L * 8, s);
+  launch_fw_t0(dlen, dspd, t0, nl, s);
+  zero_red();
+  launch_fw_time(t0, x, cap, alpha, beta, t, red, nl, s);   // x = 0: t = t0
+  if ((rc = aon())) {
+    release();
+    return rc;
+  }
+  launch_fw_counts(y, x, nl, s);
+  for (int k = 0; k <= K; k++) {
+    // Beckmann objective at x_k
+    zero_red();
+    launch_fw_objective(t0, x, cap, alpha, beta, true, 0.0, red, nl, s);
+    get(hr, red, 8);
+    double bo;
+    memcpy(&bo, &hr[0], 8);
+    const double so = fixed_scale(bo, nl);
+    zero_red();
+    launch_fw_objective(t0, x, cap, alpha, beta, false, so, red, nl, s);
+    get(hr, red, 8);
+    objective_out[k] = (double)(long long)hr[0] / so;
+    if (k == K) break;
+    // direction
+    zero_red();
+    launch_fw_time(t0, x, cap, alpha, beta, t, red, nl, s);
+    if ((rc = aon())) {
+      release();
+      return rc;
+    }
+    zero_red();
+    launch_fw_bounds(t0, x, y, t, cap, alpha, beta, red, nl, s);
+    get(hr, red, 16);
+    double bg, bl;
+    memcpy(&bg, &hr[0], 8);
+    memcpy(&bl, &hr[1], 8);
+    const double sg = fixed_scale(bg, nl), sl = fixed_scale(bl, nl);
+    zero_red();
+    launch_fw_gap_sums(t, x, y, sg, red, nl, s);
+    get(hr, red, 16);
+    const long long tx = (long long)hr[0], ty = (long long)hr[1];
+    gap_out[k] = tx > 0 ? (double)(tx - ty) / (double)tx : 0.0;
+    // step: exact line search by bisection on the sign of the derivative
+    auto deriv = [&](double a) -> long long {
+      zero_red();
+      launch_fw_deriv(t0, x, y, cap, alpha, beta, a, sl, red, nl, s);
+      get(hr, red, 8);
+      return (long long)hr[0];
+    };
+    const long long g0 = deriv(0.0), g1 = deriv(1.0);
+    double a;
+    if (g0 >= 0) {
+      a = 0.0;
+    } else if (g1 <= 0) {
+      a = 1.0;
+    } else {
+      double lo = 0.0, hi = 1.0;
+      for (int it = 0; it < spec->bisect_iter; it++) {
+        const double mid = 0.5 * (lo + hi);
+        if (deriv(mid) > 0) hi = mid;
+        else lo = mid;
+      }
+      a = 0.5 * (lo + hi);
+    }
+    step_out[k] = a;
+    launch_fw_update(x, y, a, nl, s);
+    if (e != cudaSuccess) break;
+  }
+  launch_fw_final_time(t0, x, cap, alpha, beta, t, nl, s);
+  get(flow_out, x, (size_t)nl * 8);
+  get(time_out, t, (size_t)nl * 8);
+  release();
+  if (e != cudaSuccess) return cuda_fail(h, e, "assignment");
   return SIM_OK;
 }
 

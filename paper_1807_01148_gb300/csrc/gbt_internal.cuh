@@ -196,6 +196,7 @@ struct RouteDev {
   int32_t* rlen;
   int32_t* routes;
   unsigned long long cap;
+  unsigned* flow;               // all-or-nothing mode: trips per link instead of stored routes
   int* work;
   int delta;
   Ctl* ctl;

@@ -11,7 +11,9 @@
 // Distances are 64-bit words tagged with a per-CTA epoch, so no per-origin reset of
 // the distance array is needed.  The tree is then read back for every trip of the
 // origin by walking from the destination: at node v take the lowest-id in-link
-// u -> v with dist[u] + c = dist[v] (a unique, canonical shortest path).
+// u -> v with dist[u] + c = dist[v] (a unique, canonical shortest path).  In the
+// all-or-nothing mode (R.flow set) that walk adds one trip to every link of the path
+// instead of storing it: the direction finding of Frank-Wolfe (Sec. 5.2).
 #include <climits>
 
 #include "gbt_internal.cuh"
@@ -145,8 +147,10 @@ __global__ void __launch_bounds__(512) k_sssp_route(RouteDev R) {
       if (dval(dist, d, hi) == INT_MAX) {
         atomicOr(&R.ctl->err, kErrUnreach);
         atomicExch(&R.ctl->err_info, i);
-        R.roff[i] = 0;
-        R.rlen[i] = 0;
+        if (!R.flow) {
+          R.roff[i] = 0;
+          R.rlen[i] = 0;
+        }
         continue;
       }
       int n = 0, v = d;
@@ -166,16 +170,20 @@ __global__ void __launch_bounds__(512) k_sssp_route(RouteDev R) {
           bad = true;
           break;
         }
+        if (R.flow) atomicAdd(&R.flow[pick], 1u);
         n++;
         v = R.lfrom[pick];
       }
       if (bad) {
         atomicOr(&R.ctl->err, kErrRoute);
         atomicExch(&R.ctl->err_info, i);
-        R.roff[i] = 0;
-        R.rlen[i] = 0;
+        if (!R.flow) {
+          R.roff[i] = 0;
+          R.rlen[i] = 0;
+        }
         continue;
       }
+      if (R.flow) continue;   // all-or-nothing: the path is counted, not stored
       const unsigned long long off = atomicAdd(&R.ctl->route_cursor, (unsigned long long)n);
       R.rlen[i] = n;
       if (off + (unsigned long long)n > R.cap) {

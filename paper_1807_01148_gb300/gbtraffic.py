@@ -26,7 +26,7 @@ EXPORTS = ["sim_create", "sim_create_batch", "sim_set_stream", "sim_route", "sim
            "sim_counters", "sim_last_error", "sim_destroy", "sim_set_class_params", "sim_observe", "sim_adjoint",
            "sim_set_exec", "sim_get_exec", "sim_autotune", "sim_set_outputs", "sim_reset_outputs",
            "sim_read_emissions", "sim_read_link_times", "sim_read_edge_samples", "sim_measured_costs",
-           "sim_reroute", "sim_equilibrium"]
+           "sim_reroute", "sim_equilibrium", "sim_assign_static"]
 OUT_EMISSIONS, OUT_LINK_TIMES, OUT_EDGE_SAMPLES = 1, 2, 4
 SIM_EXEC_GRAPH, SIM_EXEC_PERSISTENT = 0, 1
 
@@ -73,6 +73,11 @@ class sim_loss_spec(C.Structure):
 
 class sim_sampling(C.Structure):
     _fields_ = [("every_steps", C.c_int32), ("per_window", C.c_int32), ("max_windows", C.c_int32)]
+
+
+class sim_assign_spec(C.Structure):
+    _fields_ = [("capacity", C.c_void_p), ("alpha", C.c_double), ("beta", C.c_int32), ("max_iter", C.c_int32),
+                ("bisect_iter", C.c_int32)]
 
 
 class sim_state_view(C.Structure):
@@ -129,6 +134,7 @@ def lib(path: str | None = None):
         L.sim_measured_costs.argtypes = [vp, vp, vp, vp]
         L.sim_reroute.argtypes = [vp, vp, u32, u32]
         L.sim_equilibrium.argtypes = [vp, i32, vp, i32, vp, vp]
+        L.sim_assign_static.argtypes = [vp, C.POINTER(sim_assign_spec), vp, vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -379,6 +385,18 @@ class Sim:
         gap = np.zeros(len(f), np.float64)
         self._check(lib().sim_equilibrium(self.h, len(f), _p(f), int(n_steps), _p(cost), _p(gap)))
         return cost, gap
+
+    # ---- static user equilibrium (Sec. 5.2, Eq. 3, Eq. 6)
+    def assign_static(self, capacity, alpha=0.15, beta=4, max_iter=20, bisect_iter=30):
+        cap = np.ascontiguousarray(capacity, np.float64)
+        spec = sim_assign_spec(cap.ctypes.data, float(alpha), int(beta), int(max_iter), int(bisect_iter))
+        flow = np.zeros(self.n_links, np.float64)
+        time = np.zeros(self.n_links, np.float64)
+        gap = np.zeros(max(1, max_iter), np.float64)
+        step = np.zeros(max(1, max_iter), np.float64)
+        obj = np.zeros(max_iter + 1, np.float64)
+        self._check(lib().sim_assign_static(self.h, C.byref(spec), _p(flow), _p(time), _p(gap), _p(step), _p(obj)))
+        return dict(flow=flow, time=time, gap=gap[:max_iter], step=step[:max_iter], objective=obj)
 
     def counters(self):
         c = sim_counters_t()
