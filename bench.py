@@ -64,6 +64,7 @@ def parse():
                     help="skip the 64-scenario batched-ensemble comparison")
     ap.add_argument("--batched-steps", type=int, default=7200)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward time ratio")
+    ap.add_argument("--no-assign", action="store_true", help="skip the static-assignment timing")
     ap.add_argument("--no-outputs", action="store_true",
                     help="skip the measured-output overhead and the equilibrium timing")
     ap.add_argument("--workload", default="metro", choices=["metro", "metro-walk"],
@@ -349,6 +350,27 @@ def measure_equilibrium(G, S, torch):
             "last_run_arrived": c["arrived"], "last_run_veh_steps": c["veh_steps"]}
 
 
+def measure_assignment(G, S, torch, iters=2):
+    """Static user equilibrium (Sec. 5.2) of the full metro demand (3,000,000 trips over
+    24 h, Table 3 capacities) on the 550,000-link network: the initial all-or-nothing
+    assignment plus `iters` Frank-Wolfe iterations, each one a full set of 225,000
+    shortest-path trees.  Wall time of sim_assign_static."""
+    sc = S.metro()
+    cap = S.bpr_capacity(sc, 24.0, S.METRO_EDGE_TYPES)
+    g = G.Sim(sc)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = g.assign_static(cap, max_iter=iters)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    g.close()
+    return {"workload": f"metro, 3000000 trips, capacities over 24 h, {iters} Frank-Wolfe iterations "
+                        f"({iters + 1} all-or-nothing assignments of 225000 trees)",
+            "seconds": secs, "seconds_per_assignment": secs / (iters + 1),
+            "gap": [float(x) for x in r["gap"]], "step": [float(x) for x in r["step"]],
+            "objective": [float(x) for x in r["objective"]]}
+
+
 # ---------------------------------------------------------------------------- cuda arm
 def run_cuda(args):
     import torch
@@ -458,10 +480,13 @@ def run_cuda(args):
                "steps": e_steps, "pattern": "sim_write_state(host snapshot) then per step sim_step(1) + "
                                             "sim_read_state(x, v -> pinned host)"}
 
-    outputs = equilibrium = None
+    outputs = equilibrium = assignment = None
     if not args.no_outputs:
         outputs = measure_outputs(G, g, snap, args, stream, torch, ms / args.steps)
         equilibrium = measure_equilibrium(G, S, torch)
+    if not args.no_assign:
+        g.close()
+        assignment = measure_assignment(G, S, torch)
 
     # -- aggregate over ranks (replicas only: each rank runs its own copy)
     secs = ms / 1e3
@@ -511,6 +536,7 @@ def run_cuda(args):
                     "trips": m["demand"]["n_trips"], "hops": int(off[-1])},
         "outputs": outputs,
         "equilibrium": equilibrium,
+        "static_assignment": assignment,
         "batched_ensemble": batched,
         "adjoint_forward": adjoint,
         "cpu_baseline": cpu,
