@@ -104,6 +104,11 @@ struct orc_sim {
   int64_t samp_k0;          /* first sample index taken since the outputs were cleared */
   double *acc_u, *acc_s, *out_u, *out_s;
   int32_t* out_n;
+  /* vehicle types (Sec. 6.3.5: trucks differ in size, acceleration and maximum speed);
+   * ttype == NULL: every vehicle is of the single class of orc_params */
+  int n_vty;
+  float *vty_len, *vty_ascale, *vty_vmax;
+  uint8_t* ttype;
 };
 
 /* One taped vehicle-step: the form of Eq. 7 used (kind/lead/s/vl, see acc_form
@@ -423,7 +428,7 @@ void orc_destroy(orc_sim* S) {
                   S->cur, S->x, S->v, S->ins_step, S->arr_step, S->dec, S->holder, S->q_start, S->q_items,
                   S->q_head, S->rec, S->rec_step, S->st0, S->cur0, S->x0, S->v0s, S->tgt,
                   S->fuel, S->co, S->enter, S->tt_sum, S->tt_n, S->acc_u, S->acc_s, S->out_u,
-                  S->out_s, S->out_n};
+                  S->out_s, S->out_n, S->vty_len, S->vty_ascale, S->vty_vmax, S->ttype};
   for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); i++) free(ptrs[i]);
   free(S);
 }
@@ -720,14 +725,36 @@ static int stopline_closed(const orc_sim* S, int i, int e) {
   return 0;
 }
 
-static float acc_free(const orc_sim* S, int e, float v) {
+/* Length of trip i's vehicle. */
+static float len_of(const orc_sim* S, int i) { return S->ttype ? S->vty_len[S->ttype[i]] : S->len_v; }
+
+/* Eq. 7 parameters of trip i on link e: its link class's, with the acceleration a
+ * scaled by its vehicle type and the desired speed capped at the type's maximum. */
+static void vpar(const orc_sim* S, int e, int i, float* a, float* sab, float* v0) {
   int c = S->cls[e];
-  return idm_acc(S->pa[c], S->psab[c], S->pT[c], S->ps0[c], S->v0l[e], S->s_min, 0.0f, v, 0.0f, 0);
+  if (S->ttype) {
+    int ty = S->ttype[i];
+    *a = S->pa[c] * S->vty_ascale[ty];
+    *sab = sqrtf(*a * S->pb[c]);
+    *v0 = fminf(S->v0l[e], S->vty_vmax[ty]);
+  } else {
+    *a = S->pa[c]; *sab = S->psab[c]; *v0 = S->v0l[e];
+  }
 }
 
-static float acc_gap(const orc_sim* S, int e, float s, float v, float vl) {
+/* Eq. 7 for trip i on link e: free road, or behind a leader at gap s with speed vl. */
+static float acc_free(const orc_sim* S, int e, int i, float v) {
   int c = S->cls[e];
-  return idm_acc(S->pa[c], S->psab[c], S->pT[c], S->ps0[c], S->v0l[e], S->s_min, s, v, vl, 1);
+  float a, sab, v0;
+  vpar(S, e, i, &a, &sab, &v0);
+  return idm_acc(a, sab, S->pT[c], S->ps0[c], v0, S->s_min, 0.0f, v, 0.0f, 0);
+}
+
+static float acc_gap(const orc_sim* S, int e, int i, float s, float v, float vl) {
+  int c = S->cls[e];
+  float a, sab, v0;
+  vpar(S, e, i, &a, &sab, &v0);
+  return idm_acc(a, sab, S->pT[c], S->ps0[c], v0, S->s_min, s, v, vl, 1);
 }
 
 /* Which form of Eq. 7 produced an acceleration (for the adjoint's tape): kind
@@ -752,23 +779,23 @@ static void set_form(accform* f, int kind, int lead, float s, float vl) {
  * road ahead is free. */
 static float acc_front(const orc_sim* S, const occ_t* O, int j, int e, int l, float x, float v, accform* f) {
   int nx = next_link(S, j, S->cur[j]);
-  if (nx < 0) { set_form(f, FORM_FREE, -1, 0.0f, 0.0f); return acc_free(S, e, v); }
+  if (nx < 0) { set_form(f, FORM_FREE, -1, 0.0f, 0.0f); return acc_free(S, e, j, v); }
   int m = l < S->lanes[nx] - 1 ? l : S->lanes[nx] - 1;
   int g = lane_id(S, nx, m);
   float a1;
   accform f1;
   if (O->start[g] < O->start[g + 1] && O->vids[O->start[g]] != j) {
     int r = O->vids[O->start[g]];
-    float s = ((S->len[e] - x) + S->x[r]) - S->len_v;
-    a1 = acc_gap(S, e, s, v, S->v[r]);
+    float s = ((S->len[e] - x) + S->x[r]) - len_of(S, r);
+    a1 = acc_gap(S, e, j, s, v, S->v[r]);
     f1 = (accform){FORM_NEXT, r, s, S->v[r]};
   } else {
-    a1 = acc_free(S, e, v);
+    a1 = acc_free(S, e, j, v);
     f1 = (accform){FORM_FREE, -1, 0.0f, 0.0f};
   }
   if (stopline_closed(S, j, e)) {
     float s2 = S->len[e] - x;
-    float a2 = acc_gap(S, e, s2, v, 0.0f);
+    float a2 = acc_gap(S, e, j, s2, v, 0.0f);
     if (a2 < a1) { set_form(f, FORM_STOP, -1, s2, 0.0f); return a2; }
   }
   if (f) *f = f1;
@@ -796,9 +823,9 @@ static float acc_own(const orc_sim* S, const occ_t* O, int i, accform* f) {
   int L = leader_of(S, O, i);
   int e = S->link[i];
   if (L >= 0) {
-    float s = (S->x[L] - S->x[i]) - S->len_v;
+    float s = (S->x[L] - S->x[i]) - len_of(S, L);
     set_form(f, FORM_LEAD, L, s, S->v[L]);
-    return acc_gap(S, e, s, S->v[i], S->v[L]);
+    return acc_gap(S, e, i, s, S->v[i], S->v[L]);
   }
   return acc_front(S, O, i, e, S->lane[i], S->x[i], S->v[i], f);
 }
@@ -934,7 +961,7 @@ int orc_step(orc_sim* S, int32_t n_steps) {
       if (O.start[g] < O.start[g + 1] && O.vids[O.start[g]] != i) {
         int r = O.vids[O.start[g]];
         float land = xo[i] - S->len[e];
-        float room = S->x[r] - S->len_v;
+        float room = S->x[r] - len_of(S, r);
         if (!(land <= room)) continue;
       }
       cand[i] = 1;
@@ -986,9 +1013,9 @@ int orc_step(orc_sim* S, int32_t n_steps) {
         float ac;
         accform cf;
         if (Ln >= 0) {
-          float sl = (S->x[Ln] - S->x[i]) - S->len_v;
+          float sl = (S->x[Ln] - S->x[i]) - len_of(S, Ln);
           if (!(sl > 0.0f)) continue;
-          ac = acc_gap(S, e, sl, S->v[i], S->v[Ln]);
+          ac = acc_gap(S, e, i, sl, S->v[i], S->v[Ln]);
           cf = (accform){FORM_LEAD, Ln, sl, S->v[Ln]};
         } else {
           ac = acc_front(S, &O, i, e, l2, S->x[i], S->v[i], &cf);
@@ -996,9 +1023,9 @@ int orc_step(orc_sim* S, int32_t n_steps) {
         if (!(ac >= -S->mbsafe)) continue;
         float an = 0.0f;
         if (Fn >= 0) {
-          float sg = (S->x[i] - S->x[Fn]) - S->len_v;
+          float sg = (S->x[i] - S->x[Fn]) - len_of(S, i);
           if (!(sg > 0.0f)) continue;
-          an = acc_gap(S, e, sg, S->v[Fn], S->v[i]);
+          an = acc_gap(S, e, Fn, sg, S->v[Fn], S->v[i]);
           if (!(an >= -S->mbsafe)) continue;
         }
         if (mand) { chosen = d; chosen_at = ac; tgt_f[i] = cf; break; }
@@ -1008,7 +1035,7 @@ int orc_step(orc_sim* S, int32_t n_steps) {
         int F = follower_of(S, &O, i);
         if (F >= 0) {
           int L = leader_of(S, &O, i);
-          float ao = (L >= 0) ? acc_gap(S, e, (S->x[L] - S->x[F]) - S->len_v, S->v[F], S->v[L])
+          float ao = (L >= 0) ? acc_gap(S, e, F, (S->x[L] - S->x[F]) - len_of(S, L), S->v[F], S->v[L])
                               : acc_front(S, &O, F, e, l, S->x[F], S->v[F], NULL);
           dn_o = ao - a_own[F];
         }
@@ -1023,13 +1050,14 @@ int orc_step(orc_sim* S, int32_t n_steps) {
 
     /* simultaneous changes into one lane (paper silent): a change is cancelled when
      * another vehicle with a lower trip id changes into the same lane of the same
-     * link less than (vehicle length + s0) away. */
+     * link less than (vehicle length + s0) away; with vehicle types, the longer of
+     * the two lengths. */
     for (int i = 0; i < nt; i++) {
       change[i] = 0;
       if (S->st[i] != ST_ACTIVE || intent[i] == 0) continue;
       int e = S->link[i];
       int tgt = S->lane[i] + intent[i];
-      float thr = S->len_v + S->ps0[S->cls[e]];
+      float len_i = len_of(S, i);
       int cancel = 0;
       /* changers into lane tgt come from lanes tgt - 1 and tgt + 1 of the same link */
       for (int src = tgt - 1; src <= tgt + 1 && !cancel; src += 2) {
@@ -1038,6 +1066,7 @@ int orc_step(orc_sim* S, int32_t n_steps) {
         for (int p = O.start[g]; p < O.start[g + 1] && !cancel; p++) {
           int j = O.vids[p];
           if (j >= i || intent[j] == 0 || S->lane[j] + intent[j] != tgt) continue;
+          float thr = fmaxf(len_i, len_of(S, j)) + S->ps0[S->cls[e]];
           if (fabsf(S->x[j] - S->x[i]) < thr) cancel = 1;
         }
       }
@@ -1121,11 +1150,11 @@ int orc_step(orc_sim* S, int32_t n_steps) {
         if (!((M >> l) & 1)) continue;
         int g = lane_id(S, e, l);
         if (best[g] != (1 << 30)) continue;
-        float rs = (O.start[g] < O.start[g + 1]) ? S->x[O.vids[O.start[g]]] - S->len_v : INFINITY;
+        float rs = (O.start[g] < O.start[g + 1]) ? S->x[O.vids[O.start[g]]] - len_of(S, O.vids[O.start[g]]) : INFINITY;
         if (bl < 0 || rs > brs) { bl = l; brs = rs; }
       }
       if (bl < 0) continue;
-      float need = S->ps0[S->cls[e]] + S->len_v;
+      float need = S->ps0[S->cls[e]] + len_of(S, h);
       if (!(brs >= need)) continue;
       nst[h] = ST_ACTIVE; nlink[h] = e; nlane[h] = bl; ncur[h] = 0; nx_[h] = 0.0f; nv[h] = 0.0f;
       S->ins_step[h] = (int32_t)t;
@@ -1288,6 +1317,7 @@ static idm_grad idm_partials(const orc_sim* S, int c, double v0, int kind, float
 
 int orc_adjoint(orc_sim* S, int32_t n_steps, int32_t obs_every, const double* target, double* grad, double* loss) {
   if (!S->routed) return ESTATE;
+  if (S->ttype) return ESTATE;   /* the calibration covers the single vehicle class */
   if (obs_every <= 0 || n_steps <= 0 || n_steps % obs_every) return EINV;
   int nt = S->nt, nobs = n_steps / obs_every;
   /* start state, kept for the taped replay */
@@ -1459,6 +1489,30 @@ int orc_set_outputs(orc_sim* S, uint32_t flags, int32_t sample_every, int32_t pe
     S->out_n = (int32_t*)xcalloc((size_t)max_windows, 4);
   }
   clear_outputs(S);
+  return OK;
+}
+
+/* Vehicle types (Sec. 6.3.5): n types with length, acceleration scale and maximum
+ * speed; trip_type[i] < n for every trip.  n = 0 returns to the single class. */
+int orc_set_vehicle_types(orc_sim* S, int32_t n, const float* length, const float* accel_scale,
+                          const float* max_speed, const uint8_t* trip_type) {
+  if (n < 0 || n > 8) return EINV;
+  for (int k = 0; k < n; k++)
+    if (!(length[k] > 0.0f) || !(accel_scale[k] > 0.0f) || !(max_speed[k] > 0.0f)) return EINV;
+  for (int i = 0; n > 0 && i < S->nt; i++) if (trip_type[i] >= n) return EINV;
+  free(S->vty_len); free(S->vty_ascale); free(S->vty_vmax); free(S->ttype);
+  S->vty_len = S->vty_ascale = S->vty_vmax = NULL;
+  S->ttype = NULL;
+  S->n_vty = n;
+  if (n == 0) return OK;
+  S->vty_len = (float*)xcalloc(n, 4);
+  S->vty_ascale = (float*)xcalloc(n, 4);
+  S->vty_vmax = (float*)xcalloc(n, 4);
+  S->ttype = (uint8_t*)xcalloc(zsz(S->nt), 1);
+  memcpy(S->vty_len, length, (size_t)n * 4);
+  memcpy(S->vty_ascale, accel_scale, (size_t)n * 4);
+  memcpy(S->vty_vmax, max_speed, (size_t)n * 4);
+  memcpy(S->ttype, trip_type, (size_t)S->nt);
   return OK;
 }
 

@@ -71,6 +71,9 @@ int  orc_reset_outputs(orc_sim*);
 int  orc_read_emissions(const orc_sim*, double* fuel_ml, double* co_g);
 int  orc_read_link_times(const orc_sim*, int64_t* sum_steps, int32_t* n_exits);
 int  orc_read_edge_samples(const orc_sim*, double* util, double* speed, int32_t* n_samples);
+/* vehicle types (Sec. 6.3.5): per type length, acceleration scale, maximum speed */
+int  orc_set_vehicle_types(orc_sim*, int32_t n, const float* length, const float* accel_scale,
+                           const float* max_speed, const uint8_t* trip_type);
 /* iterative decaying route equilibrium (Sec. 6.3.1) */
 int  orc_measured_costs(const orc_sim*, const int32_t* prev_cost_ds, int32_t* cost_ds, double* gap);
 int  orc_reroute(orc_sim*, const int32_t* link_cost_ds, uint32_t fraction_q16, uint32_t round);

@@ -97,6 +97,7 @@ def lib():
         L.orc_reroute.argtypes = [vp, vp, u32, u32]
         L.orc_equilibrium.argtypes = [vp, i32, vp, i32, vp, vp]
         L.orc_reroute_selected.argtypes = [C.c_uint64, i32, u32, u32]
+        L.orc_set_vehicle_types.argtypes = [vp, i32, vp, vp, vp, vp]
         L.orc_assign_static.argtypes = [vp, vp, C.c_double, i32, i32, i32, vp, vp, vp, vp, vp]
         L.orc_aon.argtypes = [vp, vp, vp]
         L.orc_co_rate.argtypes = [f32]
@@ -289,6 +290,13 @@ class OracleSim:
         gap = np.zeros(len(f), np.float64)
         _check(lib().orc_equilibrium(self.h, len(f), _p(f), int(n_steps), _p(cost), _p(gap)), "orc_equilibrium")
         return cost, gap
+
+    def set_vehicle_types(self, types, trip_type):
+        """types: list of (length_m, accel_scale, max_speed_mps); trip_type: per-trip index."""
+        n = len(types)
+        cols = [np.ascontiguousarray([t[k] for t in types], np.float32) for k in range(3)] if n else [None] * 3
+        tt = np.ascontiguousarray(trip_type, np.uint8) if n else None
+        _check(lib().orc_set_vehicle_types(self.h, n, *[_p(c) for c in cols], _p(tt)), "orc_set_vehicle_types")
 
     # ---- static user equilibrium (Sec. 5.2, Eq. 3, Eq. 6)
     def assign_static(self, capacity, alpha=0.15, beta=4, max_iter=20, bisect_iter=30):
