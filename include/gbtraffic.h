@@ -261,6 +261,28 @@ typedef struct {
  * after the n_steps.  Errors: SIM_EINVAL, SIM_ESTATE, SIM_ENOMEM. */
 int sim_adjoint(sim_handle* h, const sim_loss_spec* spec, double* grad_out, double* loss_out);
 
+/* ---------------------------------------------------------------- vehicle types
+ * Sec. 6.3.5: a second vehicle type for trucks, differing in size, acceleration and
+ * maximum speed.  With types set, every trip has a type; a vehicle's gap to its leader
+ * is measured to the leader's rear (its own length), Eq. 7 uses the link class's
+ * parameters with a multiplied by accel_scale (and 2 sqrt(ab) from that a) and v0 =
+ * min(class or link v0, max_speed_mps); a departure needs s0 + the entering vehicle's
+ * length of rear space; two changes into one lane closer than s0 + the longer of the
+ * two lengths keep only the lower trip id's.  The lane-change zone (2 * veh_len) and the
+ * edge-sample capacity keep sim_params.veh_len. */
+#define SIM_MAX_VEHICLE_TYPES 8
+typedef struct {
+  float length_m;        /* > 0 */
+  float accel_scale;     /* > 0, multiplies the class's a */
+  float max_speed_mps;   /* > 0, caps v0 */
+} sim_vehicle_type;
+
+/* types [n_types] and trip_type [n_trips] (host; each < n_types).  n_types = 0 returns
+ * to the single class of sim_params.  Takes effect from the next step; sim_set_class_params
+ * keeps applying to every type.  sim_adjoint refuses to run with types set (SIM_ESTATE).
+ * Errors: SIM_EINVAL (sizes, values, type ids), SIM_ENOMEM. */
+int sim_set_vehicle_types(sim_handle* h, int32_t n_types, const sim_vehicle_type* types, const uint8_t* trip_type);
+
 /* ---------------------------------------------------------------- measured outputs
  * Optional per-run measurements taken by the step kernels (sim_step in either
  * execution mode; sim_step_timed counts the edge-sample kernel under "own").  All

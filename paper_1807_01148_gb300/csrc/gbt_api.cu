@@ -109,6 +109,8 @@ struct sim_handle {
   // per-trip hash bases (mandatory-switch and reroute draws), measured outputs
   std::vector<unsigned long long> hseed;
   uint32_t out_flags = 0;
+  // vehicle types: per type length, acceleration scale, maximum speed
+  std::vector<float> vty_len, vty_ascale, vty_vmax;
 };
 
 namespace {
@@ -577,6 +579,23 @@ int check_device(sim_handle* h) {
     CK(cudaStreamSynchronize(h->stream));
     return fail(h, code, buf);
   }
+  return SIM_OK;
+}
+
+// Eq. 7 parameters per (class, vehicle type): the class's with a scaled by the type.
+int upload_type_params(sim_handle* h) {
+  const int nty = (int)h->vty_len.size();
+  if (!nty) return SIM_OK;
+  std::vector<ClassPar> cp((size_t)h->ncls * nty);
+  for (int c = 0; c < h->ncls; c++)
+    for (int k = 0; k < nty; k++) {
+      const float a = h->ac[c] * h->vty_ascale[k];
+      const float sab = sqrtf(a * h->bc[c]);
+      cp[(size_t)c * nty + k] = ClassPar{a, 2.0f * sab, h->Tc[c], h->s0c[c]};
+    }
+  CK(cudaMemcpyAsync(const_cast<ClassPar*>(h->d.cls_ty), cp.data(), cp.size() * sizeof(ClassPar),
+                     cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
   return SIM_OK;
 }
 
@@ -1249,7 +1268,51 @@ int sim_set_class_params(sim_handle* h, const float* v0, const float* T, const f
   CK(cudaMemcpyAsync(const_cast<LinkRec*>(h->d.links), h->recs.data(), h->recs.size() * sizeof(LinkRec),
                      cudaMemcpyHostToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  return SIM_OK;
+  return upload_type_params(h);
+}
+
+int sim_set_vehicle_types(sim_handle* h, int32_t n_types, const sim_vehicle_type* types, const uint8_t* trip_type) {
+  if (!h || n_types < 0 || n_types > SIM_MAX_VEHICLE_TYPES) return SIM_EINVAL;
+  if (n_types > 0 && (!types || (!trip_type && h->nt > 0))) return SIM_EINVAL;
+  for (int k = 0; k < n_types; k++)
+    if (!(types[k].length_m > 0.0f) || !(types[k].accel_scale > 0.0f) || !(types[k].max_speed_mps > 0.0f))
+      return fail(h, SIM_EINVAL, "vehicle types need length, accel_scale and max_speed > 0");
+  for (int i = 0; n_types > 0 && i < h->nt; i++)
+    if (trip_type[i] >= n_types) return fail(h, SIM_EINVAL, "trip type out of range");
+  Dev& d = h->d;
+  void* olds[] = {const_cast<uint8_t*>(d.vtype), const_cast<ClassPar*>(d.cls_ty), const_cast<float*>(d.vty_len),
+                  const_cast<float*>(d.vty_vmax)};
+  for (void* q : olds) dfree(h, q);
+  d.vtype = nullptr;
+  d.cls_ty = nullptr;
+  d.vty_len = d.vty_vmax = nullptr;
+  d.n_vty = 0;
+  h->vty_len.clear();
+  h->vty_ascale.clear();
+  h->vty_vmax.clear();
+  h->graph_dirty = true;
+  h->pgraph_n = -1;
+  h->tape_graph_dirty = true;
+  if (n_types == 0) return SIM_OK;
+  for (int k = 0; k < n_types; k++) {
+    h->vty_len.push_back(types[k].length_m);
+    h->vty_ascale.push_back(types[k].accel_scale);
+    h->vty_vmax.push_back(types[k].max_speed_mps);
+  }
+  uint8_t* vt;
+  ClassPar* ct;
+  float *vl, *vm;
+  int rc;
+  if ((rc = upload(h, &vt, trip_type, (size_t)h->nt)) || (rc = dalloc(h, &ct, (size_t)h->ncls * n_types)) ||
+      (rc = upload(h, &vl, h->vty_len.data(), (size_t)n_types)) ||
+      (rc = upload(h, &vm, h->vty_vmax.data(), (size_t)n_types)))
+    return rc;
+  d.vtype = vt;
+  d.cls_ty = ct;
+  d.vty_len = vl;
+  d.vty_vmax = vm;
+  d.n_vty = n_types;
+  return upload_type_params(h);
 }
 
 int sim_observe(sim_handle* h, int32_t n_steps, int32_t obs_every, double* progress) {
@@ -1322,6 +1385,7 @@ int sim_adjoint(sim_handle* h, const sim_loss_spec* spec, double* grad_out, doub
   if (!h || !spec || !grad_out || !loss_out || !spec->target) return SIM_EINVAL;
   if (!h->routed) return fail(h, SIM_ESTATE, "sim_adjoint before routes exist");
   if (h->out_flags) return fail(h, SIM_ESTATE, "sim_adjoint with measured outputs on (sim_set_outputs(h, 0, NULL))");
+  if (h->d.vtype) return fail(h, SIM_ESTATE, "sim_adjoint covers the single vehicle class (sim_set_vehicle_types(h, 0, ...))");
   const int n_steps = spec->n_steps, every = spec->obs_every;
   const int seg = spec->checkpoint_every > 0 ? spec->checkpoint_every : 64;
   if (n_steps <= 0 || every <= 0 || n_steps % every) return fail(h, SIM_EINVAL, "n_steps must be a multiple of obs_every");

@@ -159,6 +159,14 @@ struct Dev {
   double* out_s;
   int32_t* out_n;                  // [samp_max] samples in each finished window
   int samp_every, samp_per, samp_max;
+  // vehicle types (Sec. 6.3.5; vtype == nullptr: one vehicle class of length vlen):
+  // per trip a type, per (class, type) the Eq. 7 parameters, per type length and
+  // maximum speed
+  const uint8_t* vtype;
+  const ClassPar* cls_ty;          // [class * n_vty + type]
+  const float* vty_len;
+  const float* vty_vmax;
+  int n_vty;
   // departure queues
   const int32_t* qlinks;
   int n_qlinks;

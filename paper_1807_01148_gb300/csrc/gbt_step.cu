@@ -87,10 +87,16 @@ __device__ __forceinline__ void ph_scan_sum(const Dev& d) {
   for (int b = blockIdx.x; b < nb; b += gridDim.x) {
     int base = b * kScanChunk + threadIdx.x * kScanItems;
     int s = 0;
+    if (threadIdx.x < kScanThreads && base + kScanItems <= d.n_lanes) {
+      const int4 a0 = *reinterpret_cast<const int4*>(d.cnt + base);
+      const int4 a1 = *reinterpret_cast<const int4*>(d.cnt + base + 4);
+      s = ((a0.x + a0.y) + (a0.z + a0.w)) + ((a1.x + a1.y) + (a1.z + a1.w));
+    } else {
 #pragma unroll
-    for (int k = 0; k < kScanItems; k++) {
-      int i = base + k;
-      if (i < d.n_lanes && threadIdx.x < kScanThreads) s += d.cnt[i];
+      for (int k = 0; k < kScanItems; k++) {
+        int i = base + k;
+        if (i < d.n_lanes && threadIdx.x < kScanThreads) s += d.cnt[i];
+      }
     }
     int tot;
     block_excl_scan(threadIdx.x < kScanThreads ? s : 0, sw, tot);
@@ -117,22 +123,44 @@ __device__ __forceinline__ void ph_scan_fin(const Dev& d) {
     const bool lanes_of_thread = threadIdx.x < kScanThreads;
     int v[kScanItems];
     int s = 0;
+    const bool full = lanes_of_thread && base + kScanItems <= d.n_lanes;
+    if (full) {
+      const int4 a0 = *reinterpret_cast<const int4*>(d.cnt + base);
+      const int4 a1 = *reinterpret_cast<const int4*>(d.cnt + base + 4);
+      v[0] = a0.x; v[1] = a0.y; v[2] = a0.z; v[3] = a0.w;
+      v[4] = a1.x; v[5] = a1.y; v[6] = a1.z; v[7] = a1.w;
+    } else {
 #pragma unroll
-    for (int k = 0; k < kScanItems; k++) {
-      int i = base + k;
-      v[k] = (lanes_of_thread && i < d.n_lanes) ? d.cnt[i] : 0;
-      s += v[k];
+      for (int k = 0; k < kScanItems; k++) {
+        int i = base + k;
+        v[k] = (lanes_of_thread && i < d.n_lanes) ? d.cnt[i] : 0;
+      }
     }
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) s += v[k];
     int tot;
     int ex = block_excl_scan(s, sw, tot) + tot_before;
+    if (full) {
+      int o[kScanItems];
 #pragma unroll
-    for (int k = 0; k < kScanItems; k++) {
-      int i = base + k;
-      if (lanes_of_thread && i < d.n_lanes) {
-        d.lane_start[i] = ex;
-        d.cnt[i] = 0;
+      for (int k = 0; k < kScanItems; k++) {
+        o[k] = ex;
+        ex += v[k];
       }
-      ex += v[k];
+      *reinterpret_cast<int4*>(d.lane_start + base) = make_int4(o[0], o[1], o[2], o[3]);
+      *reinterpret_cast<int4*>(d.lane_start + base + 4) = make_int4(o[4], o[5], o[6], o[7]);
+      *reinterpret_cast<int4*>(d.cnt + base) = make_int4(0, 0, 0, 0);
+      *reinterpret_cast<int4*>(d.cnt + base + 4) = make_int4(0, 0, 0, 0);
+    } else {
+#pragma unroll
+      for (int k = 0; k < kScanItems; k++) {
+        int i = base + k;
+        if (lanes_of_thread && i < d.n_lanes) {
+          d.lane_start[i] = ex;
+          d.cnt[i] = 0;
+        }
+        ex += v[k];
+      }
     }
     if (b == nb - 1 && threadIdx.x == 0) {
       d.ctl->nB = tot_before + tot;
@@ -213,14 +241,38 @@ __device__ __forceinline__ bool line_closed(const Dev& d, const LinkRec& L, int 
   return false;
 }
 
+// Eq. 7 parameters and desired speed of trip vid on link L: its class's, or with vehicle
+// types (Sec. 6.3.5) the class's with a scaled by the type (a table built on the host)
+// and v0 capped at the type's maximum speed.
+template <bool TYPES>
+__device__ __forceinline__ void veh_par(const Dev& d, const LinkRec& L, int vid, ClassPar& P, float& v0) {
+  if (TYPES) {
+    const int ty = d.vtype[vid];
+    P = d.cls_ty[L.cls * d.n_vty + ty];
+    v0 = fminf(L.v0, d.vty_vmax[ty]);
+  } else {
+    P = d.cls[L.cls];
+    v0 = L.v0;
+  }
+}
+
+// length of trip vid's vehicle
+template <bool TYPES>
+__device__ __forceinline__ float veh_len(const Dev& d, int vid) {
+  return TYPES ? d.vty_len[d.vtype[vid]] : d.vlen;
+}
+
 // Acceleration of a vehicle with nothing ahead on its link e, considered in lane
 // `lane`: leader = rearmost vehicle of the mapped lane of its next link (gap across
-// the link end); a closed stop line is a standing obstacle (smaller acceleration).
-__device__ __forceinline__ float acc_front(const Dev& d, const LinkRec& L, const ClassPar& P, int vid, int nxt,
-                                           int lane, float x, float v, bool closed, TapeForm* f = nullptr) {
+// the link end, to the leader's rear); a closed stop line is a standing obstacle
+// (smaller acceleration).  P, v0: the vehicle's Eq. 7 parameters.
+template <bool TYPES>
+__device__ __forceinline__ float acc_front(const Dev& d, const LinkRec& L, const ClassPar& P, float v0, int vid,
+                                           int nxt, int lane, float x, float v, bool closed,
+                                           TapeForm* f = nullptr) {
   if (nxt < 0) {
     if (f) *f = TapeForm{-1, 0.0f, 0.0f, kFormFree, 0, 0, 0};
-    return idm_acc(P, L.v0, d.s_min, 0.0f, v, 0.0f, false);
+    return idm_acc(P, v0, d.s_min, 0.0f, v, 0.0f, false);
   }
   const LinkRec Ln = d.links[nxt];
   int m = lane < Ln.lanes - 1 ? lane : Ln.lanes - 1;
@@ -228,17 +280,18 @@ __device__ __forceinline__ float acc_front(const Dev& d, const LinkRec& L, const
   int r = d.lane_start[g];
   float a1;
   TapeForm f1;
-  if (r < d.lane_start[g + 1] && d.B.vid[r] != vid) {
-    float s = ((L.len - x) + d.B.x[r]) - d.vlen;
-    a1 = idm_acc(P, L.v0, d.s_min, s, v, d.B.v[r], true);
-    if (f) f1 = TapeForm{d.B.vid[r], s, d.B.v[r], kFormNext, 0, 0, 0};
+  const int vr = r < d.lane_start[g + 1] ? d.B.vid[r] : vid;
+  if (vr != vid) {
+    float s = ((L.len - x) + d.B.x[r]) - veh_len<TYPES>(d, vr);
+    a1 = idm_acc(P, v0, d.s_min, s, v, d.B.v[r], true);
+    if (f) f1 = TapeForm{vr, s, d.B.v[r], kFormNext, 0, 0, 0};
   } else {
-    a1 = idm_acc(P, L.v0, d.s_min, 0.0f, v, 0.0f, false);
+    a1 = idm_acc(P, v0, d.s_min, 0.0f, v, 0.0f, false);
     if (f) f1 = TapeForm{-1, 0.0f, 0.0f, kFormFree, 0, 0, 0};
   }
   if (closed) {
     const float s2 = L.len - x;
-    const float a2 = idm_acc(P, L.v0, d.s_min, s2, v, 0.0f, true);
+    const float a2 = idm_acc(P, v0, d.s_min, s2, v, 0.0f, true);
     if (a2 < a1) {
       if (f) *f = TapeForm{-1, s2, 0.0f, kFormStop, 0, 0, 0};
       return a2;
@@ -252,28 +305,30 @@ __device__ __forceinline__ TapeRec* tape_slot(const Dev& d, int t, int vid) {
   return d.tape + (size_t)(t - (int)d.ctl->tape_t0) * (size_t)d.n_trips + (size_t)vid;
 }
 
-template <bool TAPE>
+template <bool TAPE, bool TYPES>
 __device__ __forceinline__ void ph_own(const Dev& d) {
   const int nB = d.ctl->nB;
   const int t = (int)d.ctl->t;
   GRID_STRIDE(p, nB) {
     const int e = d.B.link[p];
     const LinkRec L = d.links[e];
-    const ClassPar P = d.cls[L.cls];
     const float x = d.B.x[p], v = d.B.v[p];
     const int vid = d.B.vid[p], lane = d.B.lane[p], nxt = d.B.nxt[p];
+    ClassPar P;
+    float v0;
+    veh_par<TYPES>(d, L, vid, P, v0);
     const int g = L.lane_base + lane;
     const bool front = (p + 1 == d.lane_start[g + 1]);
     const bool hold = is_holder(d, L, t, vid, lane, front);
     float a;
     TapeForm f;
     if (!front) {
-      const float sg = (d.B.x[p + 1] - x) - d.vlen;
-      a = idm_acc(P, L.v0, d.s_min, sg, v, d.B.v[p + 1], true);
+      const float sg = (d.B.x[p + 1] - x) - (TYPES ? veh_len<true>(d, d.B.vid[p + 1]) : d.vlen);
+      a = idm_acc(P, v0, d.s_min, sg, v, d.B.v[p + 1], true);
       if (TAPE) f = TapeForm{d.B.vid[p + 1], sg, d.B.v[p + 1], kFormLead, 0, 0, 0};
     } else {
       bool closed = nxt >= 0 && line_closed(d, L, t, hold);
-      a = acc_front(d, L, P, vid, nxt, lane, x, v, closed, TAPE ? &f : nullptr);
+      a = acc_front<TYPES>(d, L, P, v0, vid, nxt, lane, x, v, closed, TAPE ? &f : nullptr);
     }
     if (TAPE) {
       TapeRec* rec = tape_slot(d, t, vid);
@@ -299,9 +354,10 @@ __device__ __forceinline__ void ph_own(const Dev& d) {
       int gt = Ln.lane_base + m;
       int r = d.lane_start[gt];
       bool ok = true;
-      if (r < d.lane_start[gt + 1] && d.B.vid[r] != vid) {
+      const int vr = r < d.lane_start[gt + 1] ? d.B.vid[r] : vid;
+      if (vr != vid) {
         float land = xo - L.len;
-        float room = d.B.x[r] - d.vlen;
+        float room = d.B.x[r] - veh_len<TYPES>(d, vr);
         ok = land <= room;
       }
       if (ok) {
@@ -313,8 +369,8 @@ __device__ __forceinline__ void ph_own(const Dev& d) {
   }
 }
 
-template <bool TAPE>
-__global__ void k_own(Dev d) { ph_own<TAPE>(d); }
+template <bool TAPE, bool TYPES>
+__global__ void k_own(Dev d) { ph_own<TAPE, TYPES>(d); }
 
 // First position q in [s0, s1) whose (x, vid) exceeds (x, vid) of the probe.
 __device__ __forceinline__ int upper_pos(const Dev& d, int s0, int s1, float x, int vid) {
@@ -333,7 +389,7 @@ __device__ __forceinline__ int upper_pos(const Dev& d, int s0, int s1, float x, 
 // Helbing 2007) for discretionary changes, mandatory changes toward the lanes of
 // the next movement once within the drawn switch distance, and gap acceptance =
 // no overlap and both the changer's and the new follower's accelerations >= -b_safe.
-template <bool TAPE>
+template <bool TAPE, bool TYPES>
 __device__ __forceinline__ void ph_decide(const Dev& d) {
   const int ne = d.ctl->n_elig;
   const int t = (int)d.ctl->t;
@@ -342,9 +398,11 @@ __device__ __forceinline__ void ph_decide(const Dev& d) {
     const int e = d.B.link[p];
     const LinkRec L = d.links[e];
     const float x = d.B.x[p];
-    const ClassPar P = d.cls[L.cls];
     const float v = d.B.v[p];
     const int vid = d.B.vid[p], lane = d.B.lane[p], nxt = d.B.nxt[p], cur = d.B.cur[p];
+    ClassPar P;
+    float v0;
+    veh_par<TYPES>(d, L, vid, P, v0);
     const int M = move_mask(d, e, L.lanes, nxt);
     int dirs[2];
     int nd = 0;
@@ -367,6 +425,8 @@ __device__ __forceinline__ void ph_decide(const Dev& d) {
     const bool closed_self = nxt >= 0 && line_closed(d, L, t, hold);
     int chosen = 0;
     float chosen_inc = 0.0f, chosen_at = 0.0f;
+    float dno = 0.0f;
+    bool dno_known = false;
     for (int k = 0; k < nd; k++) {
       const int dd = dirs[k];
       const int l2 = lane + dd;
@@ -378,19 +438,22 @@ __device__ __forceinline__ void ph_decide(const Dev& d) {
       float ac;
       TapeForm cf;
       if (Ln >= 0) {
-        float sl = (d.B.x[Ln] - x) - d.vlen;
+        float sl = (d.B.x[Ln] - x) - (TYPES ? veh_len<true>(d, d.B.vid[Ln]) : d.vlen);
         if (!(sl > 0.0f)) continue;
-        ac = idm_acc(P, L.v0, d.s_min, sl, v, d.B.v[Ln], true);
+        ac = idm_acc(P, v0, d.s_min, sl, v, d.B.v[Ln], true);
         if (TAPE) cf = TapeForm{d.B.vid[Ln], sl, d.B.v[Ln], kFormLead, 0, 0, 0};
       } else {
-        ac = acc_front(d, L, P, vid, nxt, l2, x, v, closed_self, TAPE ? &cf : nullptr);
+        ac = acc_front<TYPES>(d, L, P, v0, vid, nxt, l2, x, v, closed_self, TAPE ? &cf : nullptr);
       }
       if (!(ac >= -d.mbsafe)) continue;
       float an = 0.0f;
       if (Fn >= 0) {
-        float sg = (x - d.B.x[Fn]) - d.vlen;
+        float sg = (x - d.B.x[Fn]) - veh_len<TYPES>(d, vid);
         if (!(sg > 0.0f)) continue;
-        an = idm_acc(P, L.v0, d.s_min, sg, d.B.v[Fn], v, true);
+        ClassPar PF = P;
+        float v0F = v0;
+        if (TYPES) veh_par<true>(d, L, d.B.vid[Fn], PF, v0F);
+        an = idm_acc(PF, v0F, d.s_min, sg, d.B.v[Fn], v, true);
         if (!(an >= -d.mbsafe)) continue;
       }
       if (mand) {
@@ -401,21 +464,27 @@ __device__ __forceinline__ void ph_decide(const Dev& d) {
       }
       float dc = ac - d.a_own[p];
       float dn = Fn >= 0 ? an - d.a_own[Fn] : 0.0f;
-      float dno = 0.0f;
-      const int s_own = d.lane_start[g];
-      if (p > s_own) {   // old follower F = p - 1
-        const int F = p - 1;
-        float ao;
-        if (!front) {
-          ao = idm_acc(P, L.v0, d.s_min, (d.B.x[p + 1] - d.B.x[F]) - d.vlen, d.B.v[F], d.B.v[p + 1], true);
-        } else {
-          const int vF = d.B.vid[F];
-          const int nF = d.B.nxt[F];
-          bool holdF = is_holder(d, L, t, vF, lane, false);
-          bool closedF = nF >= 0 && line_closed(d, L, t, holdF);
-          ao = acc_front(d, L, P, vF, nF, lane, d.B.x[F], d.B.v[F], closedF);
+      if (!dno_known) {   // the old follower's gain does not depend on the direction
+        dno_known = true;
+        const int s_own = d.lane_start[g];
+        if (p > s_own) {   // old follower F = p - 1
+          const int F = p - 1;
+          ClassPar PF = P;
+          float v0F = v0;
+          if (TYPES) veh_par<true>(d, L, d.B.vid[F], PF, v0F);
+          float ao;
+          if (!front) {
+            const float sF = (d.B.x[p + 1] - d.B.x[F]) - (TYPES ? veh_len<true>(d, d.B.vid[p + 1]) : d.vlen);
+            ao = idm_acc(PF, v0F, d.s_min, sF, d.B.v[F], d.B.v[p + 1], true);
+          } else {
+            const int vF = d.B.vid[F];
+            const int nF = d.B.nxt[F];
+            bool holdF = is_holder(d, L, t, vF, lane, false);
+            bool closedF = nF >= 0 && line_closed(d, L, t, holdF);
+            ao = acc_front<TYPES>(d, L, PF, v0F, vF, nF, lane, d.B.x[F], d.B.v[F], closedF);
+          }
+          dno = ao - d.a_own[F];
         }
-        dno = ao - d.a_own[F];
       }
       float inc = dc + d.mp * (dn + dno);
       if (dd < 0) inc = inc + d.mbias;
@@ -432,8 +501,8 @@ __device__ __forceinline__ void ph_decide(const Dev& d) {
   }
 }
 
-template <bool TAPE>
-__global__ void __launch_bounds__(256, 4) k_decide(Dev d) { ph_decide<TAPE>(d); }
+template <bool TAPE, bool TYPES>
+__global__ void __launch_bounds__(256, 4) k_decide(Dev d) { ph_decide<TAPE, TYPES>(d); }
 
 // ------------------------------------------------------------------ measured outputs
 // Sec. 6.3.1: trip vid leaves link e in step t; it entered it in step enter[vid]
@@ -488,8 +557,8 @@ __global__ void k_edge_sample(Dev d) { ph_edge_sample(d); }
 
 // ------------------------------------------------------------------ move
 // OUT: the measured outputs are on (a separate instantiation keeps the plain kernel's
-// register count, and so its occupancy, as it is without them)
-template <bool TAPE, bool OUT>
+// register count, and so its occupancy, as it is without them); TYPES: vehicle types.
+template <bool TAPE, bool OUT, bool TYPES>
 __device__ __forceinline__ void ph_move(const Dev& d) {
   const int nB = d.ctl->nB;
   const int t = (int)d.ctl->t;
@@ -503,8 +572,10 @@ __device__ __forceinline__ void ph_move(const Dev& d) {
     int change = d.intent[p];
     if (change != 0) {
       // cancelled by a lower-id vehicle changing into the same lane less than
-      // (vehicle length + s0) away; such vehicles sit in lanes tgt-1 and tgt+1
+      // (vehicle length + s0) away, the longer of the two lengths with vehicle types;
+      // such vehicles sit in lanes tgt-1 and tgt+1
       const int tgt = lane + change;
+      const float len_self = TYPES ? veh_len<true>(d, vid) : d.vlen;
       const float thr = d.vlen + P.s0;
       bool cancel = false;
       for (int src = tgt - 1; src <= tgt + 1 && !cancel; src += 2) {
@@ -514,7 +585,8 @@ __device__ __forceinline__ void ph_move(const Dev& d) {
         for (int q = q0; q < q1 && !cancel; q++) {
           int iq = d.intent[q];
           if (iq == 0 || src + iq != tgt || d.B.vid[q] >= vid) continue;
-          if (fabsf(d.B.x[q] - x) < thr) cancel = true;
+          const float thr_q = TYPES ? fmaxf(len_self, veh_len<true>(d, d.B.vid[q])) + P.s0 : thr;
+          if (fabsf(d.B.x[q] - x) < thr_q) cancel = true;
         }
       }
       if (cancel) change = 0;
@@ -605,7 +677,7 @@ __device__ __forceinline__ void ph_move(const Dev& d) {
 // The head of each link's queue of due trips enters at x = 0, v = 0 in the allowed
 // lane with the largest rear space (ties to the lowest lane) that received no
 // vehicle from upstream in this step, if that space is at least s0 + vehicle length.
-template <bool OUT>
+template <bool OUT, bool TYPES>
 __device__ __forceinline__ void ph_insert(const Dev& d) {
   const int nq = d.n_qlinks;
   const int t = (int)d.ctl->t;
@@ -627,14 +699,14 @@ __device__ __forceinline__ void ph_insert(const Dev& d) {
       const int g = L.lane_base + l;
       if (epoch_current(d.best[g], t)) continue;
       const int r = d.lane_start[g];
-      const float rs = r < d.lane_start[g + 1] ? d.B.x[r] - d.vlen : INFINITY;
+      const float rs = r < d.lane_start[g + 1] ? d.B.x[r] - veh_len<TYPES>(d, d.B.vid[r]) : INFINITY;
       if (bl < 0 || rs > brs) {
         bl = l;
         brs = rs;
       }
     }
     if (bl < 0) continue;
-    const float need = d.cls[L.cls].s0 + d.vlen;
+    const float need = d.cls[L.cls].s0 + veh_len<TYPES>(d, h);
     if (!(brs >= need)) continue;
     const int slot = nB + atomicAdd(&d.ctl->n_ins, 1);
     if (slot >= d.n_trips) { set_err(d, kErrSlot, slot); continue; }
@@ -657,10 +729,10 @@ __device__ __forceinline__ void ph_insert(const Dev& d) {
 
 // Move and departures touch disjoint slots of buffer A (departures append after the
 // sorted vehicles) and read only state of step t, so they share one launch.
-template <bool TAPE, bool OUT>
+template <bool TAPE, bool OUT, bool TYPES>
 __global__ void k_move_insert(Dev d) {
-  ph_move<TAPE, OUT>(d);
-  if (d.n_qlinks > 0) ph_insert<OUT>(d);
+  ph_move<TAPE, OUT, TYPES>(d);
+  if (d.n_qlinks > 0) ph_insert<OUT, TYPES>(d);
 }
 
 __host__ __device__ __forceinline__ bool outputs_on(const Dev& d) { return d.emis || d.tt_sum; }
@@ -715,17 +787,21 @@ void launch_kernel(int k, const Dev& d, int grid, cudaStream_t s) {
       // the per-edge sample (when enabled) reads the sorted state, like own; its time
       // is counted with own's
       if (d.acc_u) k_edge_sample<<<grid, 256, 0, s>>>(d);
-      if (d.tape) k_own<true><<<grid, 256, 0, s>>>(d);
-      else k_own<false><<<grid, 256, 0, s>>>(d);
+      if (d.tape) k_own<true, false><<<grid, 256, 0, s>>>(d);
+      else if (d.vtype) k_own<false, true><<<grid, 256, 0, s>>>(d);
+      else k_own<false, false><<<grid, 256, 0, s>>>(d);
       break;
     case kKDecide:
-      if (d.tape) k_decide<true><<<grid, 256, 0, s>>>(d);
-      else k_decide<false><<<grid, 256, 0, s>>>(d);
+      if (d.tape) k_decide<true, false><<<grid, 256, 0, s>>>(d);
+      else if (d.vtype) k_decide<false, true><<<grid, 256, 0, s>>>(d);
+      else k_decide<false, false><<<grid, 256, 0, s>>>(d);
       break;
     case kKMoveInsert:
-      if (d.tape) k_move_insert<true, false><<<grid, 256, 0, s>>>(d);
-      else if (outputs_on(d)) k_move_insert<false, true><<<grid, 256, 0, s>>>(d);
-      else k_move_insert<false, false><<<grid, 256, 0, s>>>(d);
+      if (d.tape) k_move_insert<true, false, false><<<grid, 256, 0, s>>>(d);
+      else if (d.vtype && outputs_on(d)) k_move_insert<false, true, true><<<grid, 256, 0, s>>>(d);
+      else if (d.vtype) k_move_insert<false, false, true><<<grid, 256, 0, s>>>(d);
+      else if (outputs_on(d)) k_move_insert<false, true, false><<<grid, 256, 0, s>>>(d);
+      else k_move_insert<false, false, false><<<grid, 256, 0, s>>>(d);
       break;
     case kKFinish: k_finish<<<1, 1, 0, s>>>(d); break;
     default: break;
@@ -820,16 +896,25 @@ __global__ void k_persistent(Dev d, GridSync* gs, int n_steps, long long limit) 
     if (!grid_barrier(gs, err, limit)) return;
     // the edge sample and own read the sorted state and write disjoint arrays
     if (d.acc_u) ph_edge_sample(d);
-    ph_own<false>(d);
+    if (d.vtype) ph_own<false, true>(d);
+    else ph_own<false, false>(d);
     if (!grid_barrier(gs, err, limit)) return;
-    ph_decide<false>(d);
+    if (d.vtype) ph_decide<false, true>(d);
+    else ph_decide<false, false>(d);
     if (!grid_barrier(gs, err, limit)) return;
-    if (outputs_on(d)) {
-      ph_move<false, true>(d);
-      if (d.n_qlinks > 0) ph_insert<true>(d);
+    if (d.vtype) {
+      if (outputs_on(d)) ph_move<false, true, true>(d);
+      else ph_move<false, false, true>(d);
+      if (d.n_qlinks > 0) {
+        if (outputs_on(d)) ph_insert<true, true>(d);
+        else ph_insert<false, true>(d);
+      }
+    } else if (outputs_on(d)) {
+      ph_move<false, true, false>(d);
+      if (d.n_qlinks > 0) ph_insert<true, false>(d);
     } else {
-      ph_move<false, false>(d);
-      if (d.n_qlinks > 0) ph_insert<false>(d);
+      ph_move<false, false, false>(d);
+      if (d.n_qlinks > 0) ph_insert<false, false>(d);
     }
     if (!grid_barrier(gs, err, limit)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) ph_finish(d);

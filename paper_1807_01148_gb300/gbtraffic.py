@@ -26,7 +26,7 @@ EXPORTS = ["sim_create", "sim_create_batch", "sim_set_stream", "sim_route", "sim
            "sim_counters", "sim_last_error", "sim_destroy", "sim_set_class_params", "sim_observe", "sim_adjoint",
            "sim_set_exec", "sim_get_exec", "sim_autotune", "sim_set_outputs", "sim_reset_outputs",
            "sim_read_emissions", "sim_read_link_times", "sim_read_edge_samples", "sim_measured_costs",
-           "sim_reroute", "sim_equilibrium", "sim_assign_static"]
+           "sim_reroute", "sim_equilibrium", "sim_assign_static", "sim_set_vehicle_types"]
 OUT_EMISSIONS, OUT_LINK_TIMES, OUT_EDGE_SAMPLES = 1, 2, 4
 SIM_EXEC_GRAPH, SIM_EXEC_PERSISTENT = 0, 1
 
@@ -73,6 +73,10 @@ class sim_loss_spec(C.Structure):
 
 class sim_sampling(C.Structure):
     _fields_ = [("every_steps", C.c_int32), ("per_window", C.c_int32), ("max_windows", C.c_int32)]
+
+
+class sim_vehicle_type(C.Structure):
+    _fields_ = [("length_m", C.c_float), ("accel_scale", C.c_float), ("max_speed_mps", C.c_float)]
 
 
 class sim_assign_spec(C.Structure):
@@ -135,6 +139,7 @@ def lib(path: str | None = None):
         L.sim_reroute.argtypes = [vp, vp, u32, u32]
         L.sim_equilibrium.argtypes = [vp, i32, vp, i32, vp, vp]
         L.sim_assign_static.argtypes = [vp, C.POINTER(sim_assign_spec), vp, vp, vp, vp, vp]
+        L.sim_set_vehicle_types.argtypes = [vp, i32, C.POINTER(sim_vehicle_type), vp]
         _lib = L
     return _lib
 
@@ -385,6 +390,14 @@ class Sim:
         gap = np.zeros(len(f), np.float64)
         self._check(lib().sim_equilibrium(self.h, len(f), _p(f), int(n_steps), _p(cost), _p(gap)))
         return cost, gap
+
+    def set_vehicle_types(self, types, trip_type):
+        """types: list of (length_m, accel_scale, max_speed_mps); trip_type: per-trip index
+        (Sec. 6.3.5 trucks).  An empty list returns to the single vehicle class."""
+        n = len(types)
+        arr = (sim_vehicle_type * max(1, n))(*[sim_vehicle_type(*map(float, t)) for t in types])
+        tt = np.ascontiguousarray(trip_type, np.uint8) if n else None
+        self._check(lib().sim_set_vehicle_types(self.h, n, arr, _p(tt)))
 
     # ---- static user equilibrium (Sec. 5.2, Eq. 3, Eq. 6)
     def assign_static(self, capacity, alpha=0.15, beta=4, max_iter=20, bisect_iter=30):
