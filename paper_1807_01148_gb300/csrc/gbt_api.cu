@@ -391,7 +391,7 @@ int create_from_flat(Flat& F, sim_handle** out) {
     TRY(dalloc(h, &d.status, nt));
     TRY(dalloc(h, &d.ins_step, nt));
     TRY(dalloc(h, &d.arr_step, nt));
-    TRY(dalloc(h, &d.dec, nt));
+    TRY(dalloc(h, &d.adec, nt));
     int32_t *roff, *rlen;
     TRY(dalloc(h, &roff, nt));
     TRY(dalloc(h, &rlen, nt));
@@ -407,6 +407,7 @@ int create_from_flat(Flat& F, sim_handle** out) {
       TRY(dalloc(h, &b->cur, nt));
       TRY(dalloc(h, &b->lane, nt));
       TRY(dalloc(h, &b->gid, nt));
+      TRY(dalloc(h, &b->mv, nt));
     }
     TRY(dalloc(h, &d.aidx, nt));
     TRY(dalloc(h, &d.tx, nt));
@@ -418,17 +419,18 @@ int create_from_flat(Flat& F, sim_handle** out) {
     TRY(dalloc(h, &d.at, nt));
     TRY(dalloc(h, &d.intent, nt));
     TRY(dalloc(h, &d.flags, nt));
-    TRY(dalloc(h, &d.elig, nt));
     TRY(dalloc(h, &d.cnt, (size_t)nlan));
     TRY(dalloc(h, &d.lane_start, (size_t)nlan + 1));
     TRY(dalloc(h, &d.bsum, (size_t)scan_blocks(nlan) + 1));
     TRY(dalloc(h, &d.best, (size_t)nlan));
+    TRY(dalloc(h, &d.rear, (size_t)nlan));
     TRY(dalloc(h, &d.holder, (size_t)F.nn));
     TRY(dalloc(h, &d.acq, (size_t)F.nn));
     TRY(dalloc(h, &d.ctl, 1));
     TRY(dalloc(h, &h->gs, 1));
     if (cudaMemset(d.cnt, 0, (size_t)nlan * 4) != cudaSuccess ||
         cudaMemset(d.best, 0xFF, (size_t)nlan * 8) != cudaSuccess ||
+        cudaMemset(d.rear, 0, (size_t)nlan * sizeof(RearRec)) != cudaSuccess ||
         cudaMemset(d.acq, 0xFF, (size_t)F.nn * 8) != cudaSuccess ||
         cudaMemset(d.holder, 0xFF, (size_t)F.nn * 4) != cudaSuccess ||
         cudaMemset(d.ctl, 0, sizeof(Ctl)) != cudaSuccess || cudaMemset(h->gs, 0, sizeof(GridSync)) != cudaSuccess ||
@@ -543,7 +545,8 @@ int reset_dynamic(sim_handle* h) {
   CK(cudaMemsetAsync(d.status, 0, nt ? nt : 1, h->stream));
   CK(cudaMemsetAsync(d.ins_step, 0xFF, (nt ? nt : 1) * 4, h->stream));
   CK(cudaMemsetAsync(d.arr_step, 0xFF, (nt ? nt : 1) * 4, h->stream));
-  CK(cudaMemsetAsync(d.dec, 0, nt ? nt : 1, h->stream));
+  CK(cudaMemsetAsync(d.adec, 0, nt ? nt : 1, h->stream));
+  CK(cudaMemsetAsync(d.rear, 0, (size_t)h->n_lanes * sizeof(RearRec), h->stream));
   CK(cudaMemsetAsync(d.holder, 0xFF, (size_t)h->nn * 4, h->stream));
   CK(cudaMemsetAsync(d.acq, 0xFF, (size_t)h->nn * 8, h->stream));
   CK(cudaMemsetAsync(d.best, 0xFF, (size_t)h->n_lanes * 8, h->stream));
@@ -1350,7 +1353,7 @@ CkptLayout ckpt_layout(const sim_handle* h) {
   L.nn = (size_t)h->nn;
   L.nl = (size_t)h->nl;
   L.nlan = (size_t)h->n_lanes;
-  L.bytes = L.nt * (8 * 4 + 1 + 4 + 4 + 1 + 4) + L.nn * 4 + L.nl * 4 + L.nlan * 4 + sizeof(Ctl) + 64;
+  L.bytes = L.nt * (8 * 4 + 1 + 1 + 4 + 4 + 1 + 4) + L.nn * 4 + L.nl * 4 + L.nlan * 4 + sizeof(Ctl) + 64;
   return L;
 }
 
@@ -1359,8 +1362,8 @@ cudaError_t ckpt_copy(sim_handle* h, unsigned char* buf, bool save) {
   Dev& d = h->d;
   struct Item { void* p; size_t n; } items[] = {
       {d.A.x, L.nt * 4}, {d.A.v, L.nt * 4}, {d.A.vid, L.nt * 4}, {d.A.link, L.nt * 4}, {d.A.nxt, L.nt * 4},
-      {d.A.cur, L.nt * 4}, {d.A.lane, L.nt * 4}, {d.A.gid, L.nt * 4}, {d.status, L.nt}, {d.ins_step, L.nt * 4}, {d.arr_step, L.nt * 4},
-      {d.dec, L.nt}, {d.aidx, L.nt * 4}, {d.holder, L.nn * 4}, {h->q_head, L.nl * 4}, {d.cnt, L.nlan * 4},
+      {d.A.cur, L.nt * 4}, {d.A.lane, L.nt * 4}, {d.A.gid, L.nt * 4}, {d.A.mv, L.nt}, {d.status, L.nt}, {d.ins_step, L.nt * 4}, {d.arr_step, L.nt * 4},
+      {d.adec, L.nt}, {d.aidx, L.nt * 4}, {d.holder, L.nn * 4}, {h->q_head, L.nl * 4}, {d.cnt, L.nlan * 4},
       {d.ctl, sizeof(Ctl)}};
   size_t off = 0;
   for (const Item& it : items) {
@@ -1374,6 +1377,7 @@ cudaError_t ckpt_copy(sim_handle* h, unsigned char* buf, bool save) {
     // epoch-tagged keys written after the checkpoint would outrank the replayed steps' keys
     cudaError_t e = cudaMemsetAsync(d.best, 0xFF, L.nlan * 8, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.acq, 0xFF, L.nn * 8, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.rear, 0, L.nlan * sizeof(RearRec), h->stream);
     return e;
   }
   return cudaSuccess;

@@ -16,7 +16,7 @@ namespace gbt {
 
 constexpr int kCtrlNone = 0, kCtrlStop = 1, kCtrlSignal = 2;
 constexpr int kPending = 0, kActive = 1, kArrived = 2;
-constexpr int kTurnThrough = 0, kTurnLeft = 1, kTurnRight = 2;
+constexpr int kTurnThrough = 0, kTurnLeft = 1, kTurnRight = 2, kTurnEnd = 3;
 
 // error word bits (device -> host)
 constexpr int kErrLane = 1, kErrLink = 2, kErrSlot = 4, kErrRoute = 8, kErrUnreach = 16,
@@ -58,22 +58,34 @@ struct VehBuf {
   int32_t* cur;    // index of the current link in the route
   int32_t* lane;
   int32_t* gid;    // global lane id (lane_base of the link + lane)
+  uint8_t* mv;     // movement class of link -> nxt (kTurn*, kTurnEnd on the last link)
+};
+
+// Rearmost vehicle of a lane, written by the occupancy rebuild for every occupied
+// lane; `tag` is the rebuild's epoch, so a lane whose tag is stale is empty.
+struct __align__(16) RearRec {
+  float x, v;
+  int32_t vid;
+  uint32_t tag;
 };
 
 struct Ctl {
   long long t;
   int nA;          // slots filled in the unsorted buffer A
   int nB;          // vehicles in the sorted buffer B (active at step start)
-  int n_ins, n_arr;
+  unsigned occ_epoch;               // occupancy rebuilds so far (tag of the rear records)
   int err, err_info;
   int active_last;
-  int n_elig;      // vehicles eligible for a lane change this step
   unsigned long long veh_steps, departed, arrived;
   unsigned long long route_cursor;  // bump allocator of the route store
   long long tape_t0;                // first step of the segment being taped
   double loss;                      // calibration loss accumulator
   long long samp_k0;                // first edge-sample index since the outputs were cleared
   unsigned long long gap_num, gap_den;  // measured-cost gap accumulators
+  // counters bumped by atomics during a step, in a cache line of their own so that the
+  // step kernels' reads of t, nB and the epoch do not queue behind them
+  alignas(128) int n_ins;
+  int n_arr;
 };
 
 // Forms of Eq. 7 an acceleration can come from (adjoint tape).
@@ -122,7 +134,7 @@ struct Dev {
   uint8_t* status;
   int32_t* ins_step;
   int32_t* arr_step;
-  int8_t* dec;
+  int8_t* adec;    // lane-change decision of the last step, per slot of buffer A
   // vehicle state: A = unsorted next state, B = sorted current state
   VehBuf A, B;
   // per-slot / per-lane scratch
@@ -140,7 +152,7 @@ struct Dev {
   float* at;
   int8_t* intent;
   uint8_t* flags;
-  int32_t* elig;              // sorted positions of lane-change candidates
+  RearRec* rear;              // per lane: rearmost vehicle (current epoch only)
   TapeRec* tape;              // adjoint tape of the current segment (nullptr: not taping)
   TapeForm* tform;            // lane-change forms of the current step (taping only)
   // per node
@@ -216,7 +228,7 @@ void launch_route(const RouteDev& R, int n_cta, cudaStream_t s);
 enum { kKScanSum, kKScanFin, kKScatter, kKRank, kKOwn, kKDecide, kKMoveInsert, kKFinish, kNumKernels };
 extern const char* const kKernelNames[kNumKernels];
 
-constexpr uint8_t kFlagFront = 1, kFlagHolder = 2, kFlagCand = 4;
+constexpr uint8_t kFlagFront = 1, kFlagHolder = 2, kFlagCand = 4, kFlagElig = 8;
 
 // ---------------------------------------------------------------- model functions
 
@@ -313,17 +325,25 @@ __host__ __device__ __forceinline__ int turn_class(long long ax, long long ay, l
   return cr < 0 ? kTurnRight : kTurnLeft;
 }
 
-// Lanes allowed for the movement e -> e2: right turns from lane 0, left turns (and
-// U-turns) from the leftmost lane, through from any; all lanes at the route's end.
-__device__ __forceinline__ int move_mask(const Dev& d, int e, int lanes, int e2) {
-  int all = (1 << lanes) - 1;
-  if (e2 < 0) return all;
+// Movement class of e -> e2 (kTurnEnd when the route ends on e).
+__device__ __forceinline__ int move_class(const Dev& d, int e, int e2) {
+  if (e2 < 0) return kTurnEnd;
   int a = d.lfrom[e], b = d.lfrom[e2];   // head of e == tail of e2
   int c = d.links[e2].to;
-  int tc = turn_class(d.node_x[a], d.node_y[a], d.node_x[b], d.node_y[b], d.node_x[c], d.node_y[c]);
-  if (tc == kTurnRight) return 1;
-  if (tc == kTurnLeft) return 1 << (lanes - 1);
-  return all;
+  return turn_class(d.node_x[a], d.node_y[a], d.node_x[b], d.node_y[b], d.node_x[c], d.node_y[c]);
+}
+
+// Lanes allowed for a movement of class mc on a link of `lanes` lanes: right turns from
+// lane 0, left turns (and U-turns) from the leftmost lane, through from any; all lanes
+// at the route's end.
+__host__ __device__ __forceinline__ int lane_mask(int mc, int lanes) {
+  if (mc == kTurnRight) return 1;
+  if (mc == kTurnLeft) return 1 << (lanes - 1);
+  return (1 << lanes) - 1;
+}
+
+__device__ __forceinline__ int move_mask(const Dev& d, int e, int lanes, int e2) {
+  return lane_mask(move_class(d, e, e2), lanes);
 }
 
 // Step time is kept below 2^31 / dt_ds (checked by sim_step), so the phase and

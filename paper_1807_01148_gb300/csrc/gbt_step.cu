@@ -20,18 +20,18 @@ namespace gbt {
 
 #define GRID_STRIDE(i, n) for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
 
-// Append `pos` to list[] (counter *n) for the lanes of the warp where `pred` holds,
-// with one atomic per warp.
-__device__ __forceinline__ void warp_append(bool pred, int pos, int* n, int32_t* list) {
+// Arrival index of this vehicle in lane g's count for the next occupancy rebuild.
+// Neighbouring threads mostly hold vehicles of the same lane (the sorted order), so
+// the threads of a warp with equal g share one atomic; the order inside the group is
+// arbitrary (the rebuild ranks by position and id).
+__device__ __forceinline__ int count_in_lane(const Dev& d, int g) {
   const unsigned act = __activemask();
-  const unsigned m = __ballot_sync(act, pred);
-  if (m) {
-    const int ln = threadIdx.x & 31, lead = __ffs(m) - 1;
-    int base = 0;
-    if (ln == lead) base = atomicAdd(n, __popc(m));
-    base = __shfl_sync(act, base, lead);
-    if (pred) list[base + __popc(m & ((1u << ln) - 1u))] = pos;
-  }
+  const unsigned peers = __match_any_sync(act, g);
+  const int ln = threadIdx.x & 31, lead = __ffs(peers) - 1;
+  int base = 0;
+  if (ln == lead) base = atomicAdd(&d.cnt[g], __popc(peers));
+  base = __shfl_sync(peers, base, lead);
+  return base + __popc(peers & ((1u << ln) - 1u));
 }
 
 // ------------------------------------------------------------------ occupancy
@@ -165,7 +165,8 @@ __device__ __forceinline__ void ph_scan_fin(const Dev& d) {
     if (b == nb - 1 && threadIdx.x == 0) {
       d.ctl->nB = tot_before + tot;
       d.lane_start[d.n_lanes] = tot_before + tot;
-      d.ctl->n_elig = 0;
+      const unsigned ep = d.ctl->occ_epoch + 1u;
+      d.ctl->occ_epoch = ep ? ep : 1u;   // tag 0 marks never-written rear records
     }
   }
 }
@@ -190,12 +191,15 @@ __global__ void k_scatter(Dev d) { ph_scatter(d); }
 
 // Rank of each vehicle inside its lane segment by (x, vid); the vehicle's state
 // moves from its slot in A to position lane_start + rank in B.  The vehicle that
-// lands last in its segment is the lane's front: if its link ends at a free stop-
+// lands first in its segment is the lane's rearmost: it writes the lane's rear record
+// (the leader seen across the link end by vehicles entering or approaching the lane).
+// The vehicle that lands last is the lane's front: if its link ends at a free stop-
 // controlled node, it bids for the node here (Sec. 6.3.2 stop signs, one vehicle at
 // a time): the bid with the smallest (round-robin rank of its link, lane) acquires it.
 __device__ __forceinline__ void ph_rank(const Dev& d) {
   const int nB = d.ctl->nB;
   const int t = (int)d.ctl->t;
+  const unsigned ep = d.ctl->occ_epoch;
   GRID_STRIDE(p, nB) {
     const int g = d.tg[p];
     const int s0 = d.lane_start[g], s1 = d.lane_start[g + 1];
@@ -209,13 +213,16 @@ __device__ __forceinline__ void ph_rank(const Dev& d) {
     const int dst = s0 + rank;
     const int src = d.tsrc[p];
     const int e = d.A.link[src], nxt = d.A.nxt[src], lane = d.A.lane[src];
+    const float vv = d.A.v[src];
     d.B.x[dst] = xp;
-    d.B.v[dst] = d.A.v[src];
+    d.B.v[dst] = vv;
     d.B.vid[dst] = vp;
     d.B.link[dst] = e;
     d.B.nxt[dst] = nxt;
     d.B.cur[dst] = d.A.cur[src];
     d.B.lane[dst] = lane;
+    d.B.mv[dst] = d.A.mv[src];
+    if (rank == 0) d.rear[g] = RearRec{xp, vv, vp, ep};
     if (dst + 1 == s1 && nxt >= 0) {
       const LinkRec& L = d.links[e];
       if (L.ctrl == kCtrlStop && d.holder[L.to] == -1 && (L.len - xp) <= d.stop_acq)
@@ -265,26 +272,34 @@ __device__ __forceinline__ float veh_len(const Dev& d, int vid) {
 // Acceleration of a vehicle with nothing ahead on its link e, considered in lane
 // `lane`: leader = rearmost vehicle of the mapped lane of its next link (gap across
 // the link end, to the leader's rear); a closed stop line is a standing obstacle
-// (smaller acceleration).  P, v0: the vehicle's Eq. 7 parameters.
+// (smaller acceleration).  P, v0: the vehicle's Eq. 7 parameters; ep: the epoch of the
+// current rear records.  Optionally returns
+// the mapped lane (*gt), whether it has a rearmost vehicle other than this one
+// (*lead) and that vehicle's rear position (*room).
 template <bool TYPES>
-__device__ __forceinline__ float acc_front(const Dev& d, const LinkRec& L, const ClassPar& P, float v0, int vid,
-                                           int nxt, int lane, float x, float v, bool closed,
-                                           TapeForm* f = nullptr) {
+__device__ __forceinline__ float acc_front(const Dev& d, unsigned ep, const LinkRec& L, const ClassPar& P, float v0,
+                                           int vid, int nxt, int lane, float x, float v, bool closed,
+                                           TapeForm* f = nullptr, int* gt = nullptr, bool* lead = nullptr,
+                                           float* room = nullptr) {
   if (nxt < 0) {
     if (f) *f = TapeForm{-1, 0.0f, 0.0f, kFormFree, 0, 0, 0};
     return idm_acc(P, v0, d.s_min, 0.0f, v, 0.0f, false);
   }
   const LinkRec Ln = d.links[nxt];
-  int m = lane < Ln.lanes - 1 ? lane : Ln.lanes - 1;
-  int g = Ln.lane_base + m;
-  int r = d.lane_start[g];
+  const int m = lane < Ln.lanes - 1 ? lane : Ln.lanes - 1;
+  const int g = Ln.lane_base + m;
+  const RearRec r = d.rear[g];
   float a1;
   TapeForm f1;
-  const int vr = r < d.lane_start[g + 1] ? d.B.vid[r] : vid;
-  if (vr != vid) {
-    float s = ((L.len - x) + d.B.x[r]) - veh_len<TYPES>(d, vr);
-    a1 = idm_acc(P, v0, d.s_min, s, v, d.B.v[r], true);
-    if (f) f1 = TapeForm{vr, s, d.B.v[r], kFormNext, 0, 0, 0};
+  const bool has = r.tag == ep && r.vid != vid;
+  if (gt) *gt = g;
+  if (lead) *lead = has;
+  if (has) {
+    const float len_r = veh_len<TYPES>(d, r.vid);
+    if (room) *room = r.x - len_r;
+    float s = ((L.len - x) + r.x) - len_r;
+    a1 = idm_acc(P, v0, d.s_min, s, v, r.v, true);
+    if (f) f1 = TapeForm{r.vid, s, r.v, kFormNext, 0, 0, 0};
   } else {
     a1 = idm_acc(P, v0, d.s_min, 0.0f, v, 0.0f, false);
     if (f) f1 = TapeForm{-1, 0.0f, 0.0f, kFormFree, 0, 0, 0};
@@ -305,72 +320,76 @@ __device__ __forceinline__ TapeRec* tape_slot(const Dev& d, int t, int vid) {
   return d.tape + (size_t)(t - (int)d.ctl->tape_t0) * (size_t)d.n_trips + (size_t)vid;
 }
 
+// Own-lane step of the vehicle at sorted position p (front: the last of its lane):
+// Eq. 7 behind the next vehicle of the lane, or for the front behind the rearmost
+// vehicle of the next link's mapped lane and the stop line; tentative ballistic move;
+// lane-change eligibility; admission candidacy of a front whose move reaches the end.
+template <bool TAPE, bool TYPES>
+__device__ __forceinline__ void own_one(const Dev& d, int p, bool front, int t, unsigned ep) {
+  const int e = d.B.link[p];
+  const LinkRec L = d.links[e];
+  const float x = d.B.x[p], v = d.B.v[p];
+  const int vid = d.B.vid[p], lane = d.B.lane[p], nxt = d.B.nxt[p];
+  ClassPar P;
+  float v0;
+  veh_par<TYPES>(d, L, vid, P, v0);
+  const bool hold = is_holder(d, L, t, vid, lane, front);
+  float a;
+  TapeForm f;
+  bool closed = false, lead = false;
+  int gt = 0;
+  float room = 0.0f;
+  if (!front) {
+    const float sg = (d.B.x[p + 1] - x) - (TYPES ? veh_len<true>(d, d.B.vid[p + 1]) : d.vlen);
+    a = idm_acc(P, v0, d.s_min, sg, v, d.B.v[p + 1], true);
+    if (TAPE) f = TapeForm{d.B.vid[p + 1], sg, d.B.v[p + 1], kFormLead, 0, 0, 0};
+  } else {
+    closed = nxt >= 0 && line_closed(d, L, t, hold);
+    a = acc_front<TYPES>(d, ep, L, P, v0, vid, nxt, lane, x, v, closed, TAPE ? &f : nullptr, &gt, &lead, &room);
+  }
+  if (TAPE) {
+    TapeRec* rec = tape_slot(d, t, vid);
+    rec->lead = f.lead;
+    rec->kind = f.kind;
+    rec->s = f.s;
+    rec->vl = f.vl;
+  }
+  float xo, vo;
+  ballistic(x, v, a, d.dt, d.hdt2, xo, vo);
+  d.a_own[p] = a;
+  d.xo[p] = xo;
+  d.intent[p] = 0;
+  // lane-change candidates: multi-lane link, away from both link ends
+  const bool elig = L.lanes >= 2 && x >= d.zone && xo < L.len - d.zone;
+  uint8_t fl = (front ? kFlagFront : 0) | (hold ? kFlagHolder : 0) | (elig ? kFlagElig : 0);
+  // admission candidate: front, route continues, stop line open, move reaches the
+  // end and lands behind the rearmost vehicle of the mapped lane
+  if (front && nxt >= 0 && !closed && xo >= L.len) {
+    const bool ok = !lead || (xo - L.len) <= room;
+    if (ok) {
+      fl |= kFlagCand;
+      atomicMin(&d.best[gt], epoch_key(t, rr_rank(L, t), lane));
+    }
+  }
+  d.flags[p] = fl;
+}
+
 template <bool TAPE, bool TYPES>
 __device__ __forceinline__ void ph_own(const Dev& d) {
   const int nB = d.ctl->nB;
   const int t = (int)d.ctl->t;
+  const unsigned ep = d.ctl->occ_epoch;
   GRID_STRIDE(p, nB) {
-    const int e = d.B.link[p];
-    const LinkRec L = d.links[e];
-    const float x = d.B.x[p], v = d.B.v[p];
-    const int vid = d.B.vid[p], lane = d.B.lane[p], nxt = d.B.nxt[p];
-    ClassPar P;
-    float v0;
-    veh_par<TYPES>(d, L, vid, P, v0);
-    const int g = L.lane_base + lane;
-    const bool front = (p + 1 == d.lane_start[g + 1]);
-    const bool hold = is_holder(d, L, t, vid, lane, front);
-    float a;
-    TapeForm f;
-    if (!front) {
-      const float sg = (d.B.x[p + 1] - x) - (TYPES ? veh_len<true>(d, d.B.vid[p + 1]) : d.vlen);
-      a = idm_acc(P, v0, d.s_min, sg, v, d.B.v[p + 1], true);
-      if (TAPE) f = TapeForm{d.B.vid[p + 1], sg, d.B.v[p + 1], kFormLead, 0, 0, 0};
-    } else {
-      bool closed = nxt >= 0 && line_closed(d, L, t, hold);
-      a = acc_front<TYPES>(d, L, P, v0, vid, nxt, lane, x, v, closed, TAPE ? &f : nullptr);
-    }
-    if (TAPE) {
-      TapeRec* rec = tape_slot(d, t, vid);
-      rec->lead = f.lead;
-      rec->kind = f.kind;
-      rec->s = f.s;
-      rec->vl = f.vl;
-    }
-    float xo, vo;
-    ballistic(x, v, a, d.dt, d.hdt2, xo, vo);
-    d.a_own[p] = a;
-    d.xo[p] = xo;
-    d.intent[p] = 0;
-    // lane-change candidates (multi-lane link, away from both link ends) go to a
-    // compact list so that the decision kernel runs full warps
-    const bool elig = L.lanes >= 2 && x >= d.zone && xo < L.len - d.zone;
-    warp_append(elig, p, &d.ctl->n_elig, d.elig);
-    uint8_t fl = (front ? kFlagFront : 0) | (hold ? kFlagHolder : 0);
-    // admission candidate: front, route continues, stop line open, move reaches the end
-    if (front && nxt >= 0 && !line_closed(d, L, t, hold) && xo >= L.len) {
-      const LinkRec Ln = d.links[nxt];
-      int m = lane < Ln.lanes - 1 ? lane : Ln.lanes - 1;
-      int gt = Ln.lane_base + m;
-      int r = d.lane_start[gt];
-      bool ok = true;
-      const int vr = r < d.lane_start[gt + 1] ? d.B.vid[r] : vid;
-      if (vr != vid) {
-        float land = xo - L.len;
-        float room = d.B.x[r] - veh_len<TYPES>(d, vr);
-        ok = land <= room;
-      }
-      if (ok) {
-        fl |= kFlagCand;
-        atomicMin(&d.best[gt], epoch_key(t, rr_rank(L, t), lane));
-      }
-    }
-    d.flags[p] = fl;
+    // the lane of sorted position p is tg[p]; p is its lane's front when the next
+    // position starts another lane
+    const int g = d.tg[p];
+    const bool front = p + 1 == nB || d.tg[p + 1] != g;
+    own_one<TAPE, TYPES>(d, p, front, t, ep);
   }
 }
 
 template <bool TAPE, bool TYPES>
-__global__ void k_own(Dev d) { ph_own<TAPE, TYPES>(d); }
+__global__ void __launch_bounds__(256, 6) k_own(Dev d) { ph_own<TAPE, TYPES>(d); }
 
 // First position q in [s0, s1) whose (x, vid) exceeds (x, vid) of the probe.
 __device__ __forceinline__ int upper_pos(const Dev& d, int s0, int s1, float x, int vid) {
@@ -390,11 +409,8 @@ __device__ __forceinline__ int upper_pos(const Dev& d, int s0, int s1, float x, 
 // the next movement once within the drawn switch distance, and gap acceptance =
 // no overlap and both the changer's and the new follower's accelerations >= -b_safe.
 template <bool TAPE, bool TYPES>
-__device__ __forceinline__ void ph_decide(const Dev& d) {
-  const int ne = d.ctl->n_elig;
-  const int t = (int)d.ctl->t;
-  GRID_STRIDE(i, ne) {
-    const int p = d.elig[i];
+__device__ __forceinline__ void decide_one(const Dev& d, int p, int t, unsigned ep) {
+  {
     const int e = d.B.link[p];
     const LinkRec L = d.links[e];
     const float x = d.B.x[p];
@@ -403,7 +419,7 @@ __device__ __forceinline__ void ph_decide(const Dev& d) {
     ClassPar P;
     float v0;
     veh_par<TYPES>(d, L, vid, P, v0);
-    const int M = move_mask(d, e, L.lanes, nxt);
+    const int M = lane_mask(d.B.mv[p], L.lanes);
     int dirs[2];
     int nd = 0;
     bool mand = false;
@@ -420,8 +436,9 @@ __device__ __forceinline__ void ph_decide(const Dev& d) {
       dirs[nd++] = dd;
     }
     const int g = L.lane_base + lane;
-    const bool front = (p + 1 == d.lane_start[g + 1]);
-    const bool hold = (d.flags[p] & kFlagHolder) != 0;
+    const uint8_t flp = d.flags[p];
+    const bool front = (flp & kFlagFront) != 0;
+    const bool hold = (flp & kFlagHolder) != 0;
     const bool closed_self = nxt >= 0 && line_closed(d, L, t, hold);
     int chosen = 0;
     float chosen_inc = 0.0f, chosen_at = 0.0f;
@@ -443,7 +460,7 @@ __device__ __forceinline__ void ph_decide(const Dev& d) {
         ac = idm_acc(P, v0, d.s_min, sl, v, d.B.v[Ln], true);
         if (TAPE) cf = TapeForm{d.B.vid[Ln], sl, d.B.v[Ln], kFormLead, 0, 0, 0};
       } else {
-        ac = acc_front<TYPES>(d, L, P, v0, vid, nxt, l2, x, v, closed_self, TAPE ? &cf : nullptr);
+        ac = acc_front<TYPES>(d, ep, L, P, v0, vid, nxt, l2, x, v, closed_self, TAPE ? &cf : nullptr);
       }
       if (!(ac >= -d.mbsafe)) continue;
       float an = 0.0f;
@@ -466,8 +483,7 @@ __device__ __forceinline__ void ph_decide(const Dev& d) {
       float dn = Fn >= 0 ? an - d.a_own[Fn] : 0.0f;
       if (!dno_known) {   // the old follower's gain does not depend on the direction
         dno_known = true;
-        const int s_own = d.lane_start[g];
-        if (p > s_own) {   // old follower F = p - 1
+        if (p > 0 && d.tg[p - 1] == g) {   // old follower F = p - 1
           const int F = p - 1;
           ClassPar PF = P;
           float v0F = v0;
@@ -481,7 +497,7 @@ __device__ __forceinline__ void ph_decide(const Dev& d) {
             const int nF = d.B.nxt[F];
             bool holdF = is_holder(d, L, t, vF, lane, false);
             bool closedF = nF >= 0 && line_closed(d, L, t, holdF);
-            ao = acc_front<TYPES>(d, L, PF, v0F, vF, nF, lane, d.B.x[F], d.B.v[F], closedF);
+            ao = acc_front<TYPES>(d, ep, L, PF, v0F, vF, nF, lane, d.B.x[F], d.B.v[F], closedF);
           }
           dno = ao - d.a_own[F];
         }
@@ -499,6 +515,42 @@ __device__ __forceinline__ void ph_decide(const Dev& d) {
     d.intent[p] = (int8_t)chosen;
     d.at[p] = chosen_at;
   }
+}
+
+// Each warp walks 32 consecutive sorted positions at a time and queues the lane-change
+// candidates flagged by the own-lane kernel in shared memory; the decisions run 32 at
+// a time, so the long decision path runs on full warps without a global list.
+constexpr int kMaxWarps = 32;   // blocks of up to 1024 threads
+
+template <bool TAPE, bool TYPES>
+__device__ __forceinline__ void ph_decide(const Dev& d) {
+  __shared__ int dq[kMaxWarps][64];
+  const int nB = d.ctl->nB;
+  const int t = (int)d.ctl->t;
+  const unsigned ep = d.ctl->occ_epoch;
+  const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+  const unsigned lt = (1u << ln) - 1u;
+  int* q = dq[w];
+  int qn = 0;   // warp-uniform queue length
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x + (w << 5); base < nB; base += stride) {
+    const int p = base + ln;
+    const bool el = p < nB && (d.flags[p] & kFlagElig) != 0;
+    const unsigned m = __ballot_sync(0xffffffffu, el);
+    if (el) q[qn + __popc(m & lt)] = p;
+    qn += __popc(m);
+    __syncwarp();
+    if (qn >= 32) {
+      const int pe = q[ln];
+      __syncwarp();
+      if (ln < qn - 32) q[ln] = q[ln + 32];
+      __syncwarp();
+      qn -= 32;
+      decide_one<TAPE, TYPES>(d, pe, t, ep);
+    }
+  }
+  if (ln < qn) decide_one<TAPE, TYPES>(d, q[ln], t, ep);
+  __syncwarp();
 }
 
 template <bool TAPE, bool TYPES>
@@ -618,9 +670,9 @@ __device__ __forceinline__ void ph_move(const Dev& d) {
       rec->crossed = 0;
       rec->valid = 1;
     }
-    d.dec[vid] = (int8_t)change;
     const bool hold = (fl & kFlagHolder) != 0;
     int nl = lane + change, nlink = e, ncur = cur, nnxt = nxt;
+    int nmv = -1;   // movement class after a crossing (else unchanged)
     float nx = x1, nv = v1;
     bool crossed = false;
     if (x1 >= L.len) {
@@ -646,6 +698,7 @@ __device__ __forceinline__ void ph_move(const Dev& d) {
         nl = m;
         nx = x1 - L.len;
         crossed = true;
+        nmv = move_class(d, nxt, nnxt);
         if (rec) rec->crossed = 1;
         if (OUT && d.tt_sum) {
           note_exit(d, vid, e, t);
@@ -660,8 +713,11 @@ __device__ __forceinline__ void ph_move(const Dev& d) {
     if (hold) d.holder[L.to] = crossed ? -1 : vid;
     // lane count for the next occupancy rebuild
     const int gb = crossed ? d.links[nlink].lane_base : L.lane_base;
-    d.A.gid[p] = gb + nl;
-    d.aidx[p] = atomicAdd(&d.cnt[gb + nl], 1);
+    const int gn = gb + nl;
+    d.A.gid[p] = gn;
+    d.aidx[p] = count_in_lane(d, gn);
+    d.A.mv[p] = nmv >= 0 ? (uint8_t)nmv : d.B.mv[p];
+    d.adec[p] = (int8_t)change;
     d.A.x[p] = nx;
     d.A.v[p] = nv;
     d.A.vid[p] = vid;
@@ -691,15 +747,17 @@ __device__ __forceinline__ void ph_insert(const Dev& d) {
     const LinkRec L = d.links[e];
     const int off = d.roff[h], len = d.rlen[h];
     const int e2 = len >= 2 ? d.routes[off + 1] : (d.loop ? d.routes[off] : -1);
-    const int M = move_mask(d, e, L.lanes, e2);
+    const int mc = move_class(d, e, e2);
+    const int M = lane_mask(mc, L.lanes);
+    const unsigned ep = d.ctl->occ_epoch;
     int bl = -1;
     float brs = 0.0f;
     for (int l = 0; l < L.lanes; l++) {
       if (!((M >> l) & 1)) continue;
       const int g = L.lane_base + l;
       if (epoch_current(d.best[g], t)) continue;
-      const int r = d.lane_start[g];
-      const float rs = r < d.lane_start[g + 1] ? d.B.x[r] - veh_len<TYPES>(d, d.B.vid[r]) : INFINITY;
+      const RearRec r = d.rear[g];
+      const float rs = r.tag == ep ? r.x - veh_len<TYPES>(d, r.vid) : INFINITY;
       if (bl < 0 || rs > brs) {
         bl = l;
         brs = rs;
@@ -717,6 +775,8 @@ __device__ __forceinline__ void ph_insert(const Dev& d) {
     d.A.nxt[slot] = e2;
     d.A.cur[slot] = 0;
     d.A.lane[slot] = bl;
+    d.A.mv[slot] = (uint8_t)mc;
+    d.adec[slot] = 0;
     d.A.gid[slot] = L.lane_base + bl;
     d.aidx[slot] = atomicAdd(&d.cnt[L.lane_base + bl], 1);
     d.status[h] = kActive;
@@ -746,7 +806,6 @@ __device__ __forceinline__ void ph_finish(const Dev& d) {
   c->nA = c->nB + c->n_ins;
   c->n_ins = 0;
   c->n_arr = 0;
-  c->n_elig = 0;
   c->t += 1;
 }
 
@@ -939,6 +998,7 @@ cudaError_t launch_persistent(const Dev& d, GridSync* gs, int blocks, int thread
 // ------------------------------------------------------------------ state I/O kernels
 __global__ void k_state_out(Dev d, uint8_t* status, int32_t* link, int32_t* lane, int32_t* cursor, float* x,
                             float* v, int32_t* ins, int32_t* arr, int8_t* dec) {
+  // decisions of trips on the road are written per slot by k_state_out_active
   GRID_STRIDE(i, d.n_trips) {
     if (status) status[i] = d.status[i];
     if (link) link[i] = -1;
@@ -948,11 +1008,12 @@ __global__ void k_state_out(Dev d, uint8_t* status, int32_t* link, int32_t* lane
     if (v) v[i] = 0.0f;
     if (ins) ins[i] = d.ins_step[i];
     if (arr) arr[i] = d.arr_step[i];
-    if (dec) dec[i] = d.status[i] == kActive ? d.dec[i] : 0;
+    if (dec) dec[i] = 0;
   }
 }
 
-__global__ void k_state_out_active(Dev d, int32_t* link, int32_t* lane, int32_t* cursor, float* x, float* v) {
+__global__ void k_state_out_active(Dev d, int32_t* link, int32_t* lane, int32_t* cursor, float* x, float* v,
+                                   int8_t* dec) {
   const int nA = d.ctl->nA;
   GRID_STRIDE(s, nA) {
     int e = d.A.link[s];
@@ -963,13 +1024,14 @@ __global__ void k_state_out_active(Dev d, int32_t* link, int32_t* lane, int32_t*
     if (cursor) cursor[i] = d.A.cur[s];
     if (x) x[i] = d.A.x[s];
     if (v) v[i] = d.A.v[s];
+    if (dec) dec[i] = d.adec[s];
   }
 }
 
 void launch_state_out(const Dev& d, int grid, cudaStream_t s, uint8_t* status, int32_t* link, int32_t* lane,
                       int32_t* cursor, float* x, float* v, int32_t* ins, int32_t* arr, int8_t* dec) {
   k_state_out<<<grid, 256, 0, s>>>(d, status, link, lane, cursor, x, v, ins, arr, dec);
-  k_state_out_active<<<grid, 256, 0, s>>>(d, link, lane, cursor, x, v);
+  k_state_out_active<<<grid, 256, 0, s>>>(d, link, lane, cursor, x, v, dec);
 }
 
 // Validate a state given by vid: every active trip sits on route[cursor], in a lane
@@ -1000,7 +1062,6 @@ __global__ void k_state_in(Dev d, const uint8_t* status, const int32_t* link, co
     d.status[i] = status[i];
     d.ins_step[i] = status[i] == kActive ? 0 : -1;
     d.arr_step[i] = -1;
-    d.dec[i] = 0;
     if (status[i] != kActive) continue;
     int slot = atomicAdd(&d.ctl->nA, 1);
     int off = d.roff[i], len = d.rlen[i];
@@ -1012,7 +1073,10 @@ __global__ void k_state_in(Dev d, const uint8_t* status, const int32_t* link, co
     d.A.link[slot] = link[i];
     d.A.lane[slot] = lane[i];
     d.A.cur[slot] = k;
-    d.A.nxt[slot] = k2 < len ? d.routes[off + k2] : (d.loop ? d.routes[off + k2 % len] : -1);
+    const int nx = k2 < len ? d.routes[off + k2] : (d.loop ? d.routes[off + k2 % len] : -1);
+    d.A.nxt[slot] = nx;
+    d.A.mv[slot] = (uint8_t)move_class(d, link[i], nx);
+    d.adec[slot] = 0;
   }
 }
 
