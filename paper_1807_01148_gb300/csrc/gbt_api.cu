@@ -48,6 +48,7 @@ void launch_fw_final_time(const double* t0, const double* x, const double* cap, 
                           int n, cudaStream_t s);
 void launch_compact_routes(const int32_t* roff, const int32_t* rlen, const int32_t* src, const int32_t* new_off,
                            int32_t* dst, int n, cudaStream_t s);
+int own_tiled_blocks_per_sm(bool types);
 int persistent_max_blocks_per_sm(int threads);
 cudaError_t launch_persistent(const Dev& d, GridSync* gs, int blocks, int threads, int n_steps, long long limit,
                               cudaStream_t s);
@@ -284,6 +285,7 @@ int create_from_flat(Flat& F, sim_handle** out) {
   cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
   if (h->sm_count <= 0) h->sm_count = 1;
   h->grid = h->sm_count * 8;
+  for (int ty = 0; ty < 2; ty++) h->d.own_grid[ty] = std::max(1, own_tiled_blocks_per_sm(ty != 0)) * h->sm_count;
 
   // in-links of every node in ascending link id -> round-robin index, in-degree
   std::vector<int> n_in(F.nn, 0), in_index(F.nl, 0);
@@ -398,22 +400,25 @@ int create_from_flat(Flat& F, sim_handle** out) {
     d.roff = roff;
     d.rlen = rlen;
     VehBuf* bufs[2] = {&d.A, &d.B};
+    // per-slot arrays carry kSlotPad spare elements: tiled bulk copies of the sorted
+    // state may read up to one tile past the last vehicle
+    const size_t ntp = nt + kSlotPad;
     for (VehBuf* b : bufs) {
-      TRY(dalloc(h, &b->x, nt));
-      TRY(dalloc(h, &b->v, nt));
-      TRY(dalloc(h, &b->vid, nt));
-      TRY(dalloc(h, &b->link, nt));
-      TRY(dalloc(h, &b->nxt, nt));
-      TRY(dalloc(h, &b->cur, nt));
-      TRY(dalloc(h, &b->lane, nt));
-      TRY(dalloc(h, &b->gid, nt));
-      TRY(dalloc(h, &b->mv, nt));
+      TRY(dalloc(h, &b->x, ntp));
+      TRY(dalloc(h, &b->v, ntp));
+      TRY(dalloc(h, &b->vid, ntp));
+      TRY(dalloc(h, &b->link, ntp));
+      TRY(dalloc(h, &b->nxt, ntp));
+      TRY(dalloc(h, &b->cur, ntp));
+      TRY(dalloc(h, &b->lane, ntp));
+      TRY(dalloc(h, &b->gid, ntp));
+      TRY(dalloc(h, &b->mv, ntp));
     }
     TRY(dalloc(h, &d.aidx, nt));
     TRY(dalloc(h, &d.tx, nt));
     TRY(dalloc(h, &d.tvid, nt));
     TRY(dalloc(h, &d.tsrc, nt));
-    TRY(dalloc(h, &d.tg, nt));
+    TRY(dalloc(h, &d.tg, ntp));
     TRY(dalloc(h, &d.a_own, nt));
     TRY(dalloc(h, &d.xo, nt));
     TRY(dalloc(h, &d.at, nt));

@@ -186,6 +186,7 @@ struct Dev {
   int32_t* q_head;
   const int32_t* q_items;
   Ctl* ctl;
+  int own_grid[2];                 // blocks of the tiled own-lane kernel (plain, vehicle types)
 };
 
 // Trip-planning work description (one shortest-path tree per distinct origin).
@@ -229,6 +230,10 @@ enum { kKScanSum, kKScanFin, kKScatter, kKRank, kKOwn, kKDecide, kKMoveInsert, k
 extern const char* const kKernelNames[kNumKernels];
 
 constexpr uint8_t kFlagFront = 1, kFlagHolder = 2, kFlagCand = 4, kFlagElig = 8;
+
+// spare elements at the end of every per-slot array (tiled bulk copies may read up to
+// one tile of 256 + 4 elements past the last vehicle)
+constexpr int kSlotPad = 512;
 
 // ---------------------------------------------------------------- model functions
 

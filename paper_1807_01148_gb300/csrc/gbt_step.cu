@@ -325,11 +325,9 @@ __device__ __forceinline__ TapeRec* tape_slot(const Dev& d, int t, int vid) {
 // vehicle of the next link's mapped lane and the stop line; tentative ballistic move;
 // lane-change eligibility; admission candidacy of a front whose move reaches the end.
 template <bool TAPE, bool TYPES>
-__device__ __forceinline__ void own_one(const Dev& d, int p, bool front, int t, unsigned ep) {
-  const int e = d.B.link[p];
+__device__ __forceinline__ void own_core(const Dev& d, int p, bool front, int t, unsigned ep, int e, float x,
+                                         float v, int vid, int lane, int nxt, float x1, float v1, int vid1) {
   const LinkRec L = d.links[e];
-  const float x = d.B.x[p], v = d.B.v[p];
-  const int vid = d.B.vid[p], lane = d.B.lane[p], nxt = d.B.nxt[p];
   ClassPar P;
   float v0;
   veh_par<TYPES>(d, L, vid, P, v0);
@@ -340,9 +338,9 @@ __device__ __forceinline__ void own_one(const Dev& d, int p, bool front, int t, 
   int gt = 0;
   float room = 0.0f;
   if (!front) {
-    const float sg = (d.B.x[p + 1] - x) - (TYPES ? veh_len<true>(d, d.B.vid[p + 1]) : d.vlen);
-    a = idm_acc(P, v0, d.s_min, sg, v, d.B.v[p + 1], true);
-    if (TAPE) f = TapeForm{d.B.vid[p + 1], sg, d.B.v[p + 1], kFormLead, 0, 0, 0};
+    const float sg = (x1 - x) - (TYPES ? veh_len<true>(d, vid1) : d.vlen);
+    a = idm_acc(P, v0, d.s_min, sg, v, v1, true);
+    if (TAPE) f = TapeForm{vid1, sg, v1, kFormLead, 0, 0, 0};
   } else {
     closed = nxt >= 0 && line_closed(d, L, t, hold);
     a = acc_front<TYPES>(d, ep, L, P, v0, vid, nxt, lane, x, v, closed, TAPE ? &f : nullptr, &gt, &lead, &room);
@@ -372,6 +370,14 @@ __device__ __forceinline__ void own_one(const Dev& d, int p, bool front, int t, 
     }
   }
   d.flags[p] = fl;
+}
+
+template <bool TAPE, bool TYPES>
+__device__ __forceinline__ void own_one(const Dev& d, int p, bool front, int t, unsigned ep) {
+  const float x1 = front ? 0.0f : d.B.x[p + 1], v1 = front ? 0.0f : d.B.v[p + 1];
+  const int vid1 = front ? 0 : d.B.vid[p + 1];
+  own_core<TAPE, TYPES>(d, p, front, t, ep, d.B.link[p], d.B.x[p], d.B.v[p], d.B.vid[p], d.B.lane[p], d.B.nxt[p],
+                        x1, v1, vid1);
 }
 
 template <bool TAPE, bool TYPES>
@@ -811,6 +817,128 @@ __device__ __forceinline__ void ph_finish(const Dev& d) {
 
 __global__ void k_finish(Dev d) { ph_finish(d); }
 
+
+// ------------------------------------------------------------------ bulk-copy staging
+// The sorted state is read in tiles of kTile consecutive positions; one thread of the
+// block copies a tile's arrays into shared memory with cp.async.bulk (completion
+// counted on an mbarrier), kStages - 1 tiles ahead of the tile being computed.
+constexpr int kTile = 256, kStages = 3;
+constexpr long long kWaitLimit = 2000000000LL;   // SM cycles (about a second)
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred P1;\n\tmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\tselp.u32 %0, 1, 0, P1;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for phase `parity` of bar: false after about a second.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > kWaitLimit) return false;
+  return true;
+}
+
+// bytes: a multiple of 16; src and dst 16-byte aligned
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+struct __align__(16) OwnTile {
+  float x[kTile + 4], v[kTile + 4];
+  int32_t vid[kTile + 4], tg[kTile + 4];
+  int32_t link[kTile], lane[kTile], nxt[kTile];
+};
+constexpr uint32_t kOwnTileBytes = 4 * (kTile + 4) * 4 + 3 * kTile * 4;
+static_assert(sizeof(OwnTile) == kOwnTileBytes, "OwnTile must be packed");
+
+__device__ __forceinline__ void own_issue(const Dev& d, OwnTile* tl, uint64_t* bar, int tile) {
+  const size_t b = (size_t)tile * kTile;
+  mbar_expect_tx(bar, kOwnTileBytes);
+  bulk_g2s(tl->x, d.B.x + b, (kTile + 4) * 4, bar);
+  bulk_g2s(tl->v, d.B.v + b, (kTile + 4) * 4, bar);
+  bulk_g2s(tl->vid, d.B.vid + b, (kTile + 4) * 4, bar);
+  bulk_g2s(tl->tg, d.tg + b, (kTile + 4) * 4, bar);
+  bulk_g2s(tl->link, d.B.link + b, kTile * 4, bar);
+  bulk_g2s(tl->lane, d.B.lane + b, kTile * 4, bar);
+  bulk_g2s(tl->nxt, d.B.nxt + b, kTile * 4, bar);
+}
+
+// Own-lane step with the sorted state staged tile by tile (blocks of kTile threads,
+// one resident wave walking the tiles).  A wait that runs out sets kErrTimeout.
+template <bool TYPES>
+__global__ void __launch_bounds__(kTile) k_own_tiled(Dev d) {
+  __shared__ OwnTile tl[kStages];
+  __shared__ __align__(8) uint64_t bar[kStages];
+  const int nB = d.ctl->nB;
+  const int t = (int)d.ctl->t;
+  const unsigned ep = d.ctl->occ_epoch;
+  const int ntiles = (nB + kTile - 1) / kTile;
+  const int n_my = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; s++) mbar_init(&bar[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int k = 0; k < kStages - 1 && k < n_my; k++) own_issue(d, &tl[k], &bar[k], blockIdx.x + k * gridDim.x);
+  }
+  __syncthreads();
+  for (int k = 0; k < n_my; k++) {
+    const int kn = k + kStages - 1;
+    if (threadIdx.x == 0 && kn < n_my) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      own_issue(d, &tl[kn % kStages], &bar[kn % kStages], blockIdx.x + kn * gridDim.x);
+    }
+    const int s = k % kStages;
+    const bool ok = mbar_wait(&bar[s], (uint32_t)(k / kStages) & 1u);
+    if (!__syncthreads_and(ok)) {
+      if (threadIdx.x == 0) {
+        set_err(d, kErrTimeout, blockIdx.x);
+        // let the copies already issued (tiles k .. k + kStages - 1) land before the
+        // block's shared memory goes away
+        for (int j = k; j < n_my && j < k + kStages; j++) mbar_wait(&bar[j % kStages], (uint32_t)(j / kStages) & 1u);
+      }
+      __syncthreads();
+      return;
+    }
+    const OwnTile& T = tl[s];
+    const int i = threadIdx.x;
+    const int p = (blockIdx.x + k * gridDim.x) * kTile + i;
+    if (p < nB) {
+      const bool front = p + 1 == nB || T.tg[i + 1] != T.tg[i];
+      own_core<false, TYPES>(d, p, front, t, ep, T.link[i], T.x[i], T.v[i], T.vid[i], T.lane[i], T.nxt[i],
+                             T.x[i + 1], T.v[i + 1], T.vid[i + 1]);
+    }
+    __syncthreads();
+  }
+}
+
+// blocks of the tiled own-lane kernel resident on one SM (plain, with vehicle types)
+int own_tiled_blocks_per_sm(bool types) {
+  int nb = 0;
+  cudaError_t e = types ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_own_tiled<true>, kTile, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_own_tiled<false>, kTile, 0);
+  return e == cudaSuccess ? nb : 0;
+}
+
 // ------------------------------------------------------------------ launch sequence
 void launch_kernel(int k, const Dev& d, int grid, cudaStream_t s);
 void launch_count(const Dev& d, int grid, cudaStream_t s);
@@ -846,9 +974,14 @@ void launch_kernel(int k, const Dev& d, int grid, cudaStream_t s) {
       // the per-edge sample (when enabled) reads the sorted state, like own; its time
       // is counted with own's
       if (d.acc_u) k_edge_sample<<<grid, 256, 0, s>>>(d);
-      if (d.tape) k_own<true, false><<<grid, 256, 0, s>>>(d);
-      else if (d.vtype) k_own<false, true><<<grid, 256, 0, s>>>(d);
-      else k_own<false, false><<<grid, 256, 0, s>>>(d);
+      if (d.tape) {
+        k_own<true, false><<<grid, 256, 0, s>>>(d);
+      } else {
+        // one resident wave of tile-walking blocks
+        const int g2 = d.vtype ? d.own_grid[1] : d.own_grid[0];
+        if (d.vtype) k_own_tiled<true><<<g2, kTile, 0, s>>>(d);
+        else k_own_tiled<false><<<g2, kTile, 0, s>>>(d);
+      }
       break;
     case kKDecide:
       if (d.tape) k_decide<true, false><<<grid, 256, 0, s>>>(d);
