@@ -28,22 +28,29 @@ sys.path.insert(0, ROOT)
 METRIC = "vehicle-steps/s"
 UNIT = "vehicle-steps/s"
 
-# Algorithmic bytes per active vehicle that each kernel must move (every array element
-# it has to read or write once; re-reads of neighbours and per-link records not counted).
+# Algorithmic bytes per unit that each kernel must move (every array element it has to
+# read or write once; re-reads of neighbours and per-link or per-lane records not
+# counted).  The unit is an active vehicle, except for the lane-change decision kernel,
+# which runs on the candidates only (vehicles on a multi-lane link away from its ends).
 ALG_BYTES = {
-    "scatter": 20 + 4 + 16,          # link, lane, x, vid, arrival index; lane start; 4 scatter words
-    "rank": 16 + 4 + 28 + 28,        # scatter words; lane start; state gather from A; state write to B
-    "own": 24 + 4 + 10,              # x, v, vid, link, nxt, lane; lane end; a_own, xo, flags, intent
-    "decide": 13,                    # link, x, xo; intent (eligible vehicles read more, not counted)
-    "move_insert": 28 + 9 + 28 + 1 + 12,  # sorted state; flags, intent, acceleration; next state; decision;
-                                          # next-lane count (read+write) and arrival index
+    "scatter": 20 + 4 + 16,          # link, lane id, arrival index, x, vid; lane start; 4 scatter words
+    "rank": 16 + 4 + 21 + 29,        # scatter words; lane starts; link, nxt, lane, v, cursor, movement
+                                     # gathered from A; sorted state written to B
+    "own": 16 + 12 + 10,             # x, v, vid, lane id; link, lane, nxt; a_own, xo, intent, flags
+    "decide": 4 + 29 + 1 + 4 + 5,    # list entry; sorted state; flags; a_own; intent and acceleration
+    "move_insert": 29 + 6 + 38 + 8,  # sorted state; flags, intent, acceleration; next state (with
+                                     # movement, decision); lane count (read + write)
 }
+ALG_UNIT = {k: "vehicle" for k in ALG_BYTES}
+ALG_UNIT["decide"] = "lane-change candidate"
 
 
-# DRAM bytes per active vehicle per launch from the ncu capture summarised in
-# profiles/step_kernels_metro_snapshot.md, valid only for the kernel source it was taken on.
-PROFILED_SRC_SHA = "57265aba677ecb3a"
-PROFILED_TRAFFIC = {"own": 48.9, "decide": 50.7, "move_insert": 70.5, "rank": 60.4}
+# DRAM bytes (read + write) per unit of ALG_UNIT per launch from the ncu capture
+# summarised in profiles/step_kernels_metro_snapshot.md (metro network, first 1,000,000
+# trips on their GPU-planned routes, 979,812 active vehicles, 489,835 candidates),
+# valid only for the kernel source it was taken on.
+PROFILED_SRC_SHA = "2b8d905340cea1bb"
+PROFILED_TRAFFIC = {"scatter": 23.6, "rank": 64.7, "own": 63.5, "decide": 130.9, "move_insert": 79.1}
 
 
 def kernel_source_sha():
@@ -70,7 +77,8 @@ def parse():
     ap.add_argument("--workload", default="metro", choices=["metro", "metro-walk"],
                     help="metro: GPU-planned shortest-path routes; metro-walk: the first --trips trips on "
                          "random-walk routes (no trip planning; smaller cases for profiling)")
-    ap.add_argument("--trips", type=int, default=0, help="metro-walk: number of trips (0 = all)")
+    ap.add_argument("--trips", type=int, default=0,
+                    help="use only the first N trips of the metro demand (0 = all; smaller cases for profiling)")
     ap.add_argument("--sample-frac", type=float, default=0.1,
                     help="fraction of trips in the CPU oracle's bounded sample")
     return ap.parse_args()
@@ -392,7 +400,7 @@ def run_cuda(args):
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
     m = S.metro()
-    if args.workload == "metro-walk" and args.trips:
+    if args.trips:
         d = m["demand"]
         k = args.trips
         m["demand"] = S._demand(d["origin"][:k], d["dest"][:k], d["depart_step"][:k])
@@ -444,9 +452,12 @@ def run_cuda(args):
     kms = g.step_timed(args.steps)
     c3 = g.counters()
     avg_active = (c3["veh_steps"] - c2["veh_steps"]) / max(1, args.steps)
+    avg_cand = (c3["lc_evals"] - c2["lc_evals"]) / max(1, args.steps)
+    units = {k: (avg_cand if ALG_UNIT[k] != "vehicle" else avg_active) for k in ALG_BYTES}
     dom = max((k for k in kms if k in ALG_BYTES), key=lambda k: kms[k])
     per_launch_ms = kms[dom] / args.steps
-    achieved = ALG_BYTES[dom] * avg_active / (per_launch_ms * 1e-3) / 1e9
+    achieved = ALG_BYTES[dom] * units[dom] / (per_launch_ms * 1e-3) / 1e9
+    per_kernel_gbs = {k: ALG_BYTES[k] * units[k] / (kms[k] / args.steps * 1e-3) / 1e9 for k in ALG_BYTES if k in kms}
 
     # -- end to end through the C ABI with host buffers: load the snapshot from pinned host
     #    memory, then every step read positions and speeds back to pinned host memory
@@ -518,20 +529,24 @@ def run_cuda(args):
         "metric": METRIC, "value": tot_vs / secs, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": ("metro (225000 nodes, 550000 links, 3000000 trips) saturated snapshot: all trips "
-                                "on their GPU-planned shortest-path routes at once") if args.workload == "metro" else
+        "config": {"workload": (f"metro (225000 nodes, 550000 links, {m['demand']['n_trips']} trips) saturated "
+                                "snapshot: all trips on their GPU-planned shortest-path routes at once")
+                               if args.workload == "metro" else
                                f"metro network, {m['demand']['n_trips']} trips on random-walk routes, saturated",
                    "dt_s": 0.5, "avg_active_vehicles": tot_vs / world / args.steps,
                    "l2": "working set > L2 (state, scratch and per-lane arrays ~0.5 GB; no flush)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
-                     "alg_bytes_per_vehicle": ALG_BYTES[dom],
-                     "traffic": (PROFILED_TRAFFIC[dom] * avg_active
+                     "alg_bytes_per_unit": ALG_BYTES[dom], "unit_of_work": ALG_UNIT[dom],
+                     "units_per_launch": units[dom],
+                     "traffic": (PROFILED_TRAFFIC[dom] * units[dom]
                                  if kernel_source_sha() == PROFILED_SRC_SHA and dom in PROFILED_TRAFFIC else None),
-                     "traffic_note": "ncu dram bytes per vehicle on a 1M-trip capture, scaled to this launch's "
-                                     "vehicles; null when the kernel source changed since"},
+                     "traffic_note": "ncu dram bytes per unit on a 1M-trip capture, scaled to this launch's "
+                                     "units; null when the kernel source changed since"},
         "per_kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+        "per_kernel_alg_gbs": per_kernel_gbs,
+        "lane_change_candidates_per_step": avg_cand,
         "routing": {"seconds": route_s, "mode": "gpu sim_route" if args.workload == "metro" else "set_routes", "origins_trees": int(len(np.unique(m["demand"]["origin"]))),
                     "trips": m["demand"]["n_trips"], "hops": int(off[-1])},
         "outputs": outputs,

@@ -102,6 +102,8 @@ typedef struct {
   int64_t veh_steps;    /* sum over steps of the vehicles advanced in that step */
   int64_t pending;      /* trips not yet due */
   int64_t active_last;  /* vehicles advanced in the last step */
+  int64_t lc_evals;     /* sum over steps of the lane-change decisions evaluated (vehicles
+                           on a multi-lane link away from both of its ends) */
 } sim_counters_t;
 
 /* Field bits for sim_read_state. */

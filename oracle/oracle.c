@@ -81,6 +81,7 @@ struct orc_sim {
   /* departure queues: trips by first link, ordered (depart_step, trip id) */
   int32_t *q_start, *q_items, *q_head;
   int64_t t, departed, arrived, veh_steps, active_last;
+  int64_t lc_evals;    /* lane-change decisions evaluated, summed over steps */
   /* adjoint tape: per step, one record per vehicle advanced (see orc_adjoint) */
   int recording;
   struct orc_rec* rec;
@@ -493,7 +494,7 @@ static void reset_state(orc_sim* S) {
     S->ins_step[i] = -1; S->arr_step[i] = -1; S->dec[i] = 0;
   }
   for (int n = 0; n < S->nn; n++) S->holder[n] = -1;
-  S->t = 0; S->departed = 0; S->arrived = 0; S->veh_steps = 0; S->active_last = 0;
+  S->t = 0; S->departed = 0; S->arrived = 0; S->veh_steps = 0; S->active_last = 0; S->lc_evals = 0;
   clear_outputs(S);
 }
 
@@ -981,6 +982,7 @@ int orc_step(orc_sim* S, int32_t n_steps) {
       if (nlan < 2) continue;
       float zone = 2.0f * S->len_v;
       if (!(S->x[i] >= zone && xo[i] < S->len[e] - zone)) continue;
+      S->lc_evals++;
       int l = S->lane[i];
       int nx = next_link(S, i, S->cur[i]);
       int M = move_mask(S, e, nx);
@@ -1212,8 +1214,9 @@ int orc_node_holder(const orc_sim* S, int32_t* holder) {
 }
 
 /* counters: t, departed, waiting (due, not on the road), active, arrived,
- * vehicle-steps, pending (not yet due), active at the last step start */
-int orc_counters(const orc_sim* S, int64_t out[8]) {
+ * vehicle-steps, pending (not yet due), active at the last step start, lane-change
+ * decisions evaluated */
+int orc_counters(const orc_sim* S, int64_t out[9]) {
   int64_t waiting = 0, pending = 0, active = 0;
   for (int i = 0; i < S->nt; i++) {
     if (S->st[i] == ST_ACTIVE) active++;
@@ -1224,6 +1227,7 @@ int orc_counters(const orc_sim* S, int64_t out[8]) {
   }
   out[0] = S->t; out[1] = S->departed; out[2] = waiting; out[3] = active;
   out[4] = S->arrived; out[5] = S->veh_steps; out[6] = pending; out[7] = S->active_last;
+  out[8] = S->lc_evals;
   return OK;
 }
 

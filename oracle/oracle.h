@@ -52,7 +52,7 @@ int  orc_read_state(const orc_sim*, uint8_t* status, int32_t* link, int32_t* lan
                     float* x, float* v, int32_t* insert_step, int32_t* arrive_step, int8_t* lane_change);
 int  orc_occupancy(const orc_sim*, int32_t* lane_start /* [n_lanes+1] */, int32_t* sorted_vid);
 int  orc_n_lanes(const orc_sim*);
-int  orc_counters(const orc_sim*, int64_t out[8]);
+int  orc_counters(const orc_sim*, int64_t out[9]);
 int  orc_node_holder(const orc_sim*, int32_t* holder);
 
 /* calibration (not in the paper): route progress every obs_every steps, and the

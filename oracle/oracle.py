@@ -217,9 +217,9 @@ class OracleSim:
         return start, vids[: start[-1]]
 
     def counters(self):
-        c = np.zeros(8, np.int64)
+        c = np.zeros(9, np.int64)
         _check(lib().orc_counters(self.h, _p(c)), "orc_counters")
-        keys = ("t", "departed", "waiting", "active", "arrived", "veh_steps", "pending", "active_last")
+        keys = ("t", "departed", "waiting", "active", "arrived", "veh_steps", "pending", "active_last", "lc_evals")
         return {k: int(v) for k, v in zip(keys, c)}
 
     def set_class_params(self, v0, T, a, b, s0):

@@ -429,6 +429,7 @@ int create_from_flat(Flat& F, sim_handle** out) {
     TRY(dalloc(h, &d.bsum, (size_t)scan_blocks(nlan) + 1));
     TRY(dalloc(h, &d.best, (size_t)nlan));
     TRY(dalloc(h, &d.rear, (size_t)nlan));
+    TRY(dalloc(h, &d.elig, nt));
     TRY(dalloc(h, &d.holder, (size_t)F.nn));
     TRY(dalloc(h, &d.acq, (size_t)F.nn));
     TRY(dalloc(h, &d.ctl, 1));
@@ -1248,6 +1249,7 @@ int sim_counters(sim_handle* h, sim_counters_t* out) {
   out->veh_steps = (int64_t)c.veh_steps;
   out->pending = pending;
   out->active_last = c.active_last;
+  out->lc_evals = (int64_t)c.lc_evals;
   return SIM_OK;
 }
 

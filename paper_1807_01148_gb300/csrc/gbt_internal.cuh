@@ -77,6 +77,7 @@ struct Ctl {
   int err, err_info;
   int active_last;
   unsigned long long veh_steps, departed, arrived;
+  unsigned long long lc_evals;      // lane-change decisions evaluated, summed over steps
   unsigned long long route_cursor;  // bump allocator of the route store
   long long tape_t0;                // first step of the segment being taped
   double loss;                      // calibration loss accumulator
@@ -86,6 +87,7 @@ struct Ctl {
   // step kernels' reads of t, nB and the epoch do not queue behind them
   alignas(128) int n_ins;
   int n_arr;
+  int n_elig;      // lane-change candidates listed this step
 };
 
 // Forms of Eq. 7 an acceleration can come from (adjoint tape).
@@ -153,6 +155,7 @@ struct Dev {
   int8_t* intent;
   uint8_t* flags;
   RearRec* rear;              // per lane: rearmost vehicle (current epoch only)
+  int32_t* elig;              // sorted positions of this step's lane-change candidates
   TapeRec* tape;              // adjoint tape of the current segment (nullptr: not taping)
   TapeForm* tform;            // lane-change forms of the current step (taping only)
   // per node
@@ -229,7 +232,7 @@ void launch_route(const RouteDev& R, int n_cta, cudaStream_t s);
 enum { kKScanSum, kKScanFin, kKScatter, kKRank, kKOwn, kKDecide, kKMoveInsert, kKFinish, kNumKernels };
 extern const char* const kKernelNames[kNumKernels];
 
-constexpr uint8_t kFlagFront = 1, kFlagHolder = 2, kFlagCand = 4, kFlagElig = 8;
+constexpr uint8_t kFlagFront = 1, kFlagHolder = 2, kFlagCand = 4;
 
 // spare elements at the end of every per-slot array (tiled bulk copies may read up to
 // one tile of 256 + 4 elements past the last vehicle)

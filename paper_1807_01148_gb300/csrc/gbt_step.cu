@@ -165,6 +165,7 @@ __device__ __forceinline__ void ph_scan_fin(const Dev& d) {
     if (b == nb - 1 && threadIdx.x == 0) {
       d.ctl->nB = tot_before + tot;
       d.lane_start[d.n_lanes] = tot_before + tot;
+      d.ctl->n_elig = 0;
       const unsigned ep = d.ctl->occ_epoch + 1u;
       d.ctl->occ_epoch = ep ? ep : 1u;   // tag 0 marks never-written rear records
     }
@@ -323,9 +324,10 @@ __device__ __forceinline__ TapeRec* tape_slot(const Dev& d, int t, int vid) {
 // Own-lane step of the vehicle at sorted position p (front: the last of its lane):
 // Eq. 7 behind the next vehicle of the lane, or for the front behind the rearmost
 // vehicle of the next link's mapped lane and the stop line; tentative ballistic move;
-// lane-change eligibility; admission candidacy of a front whose move reaches the end.
+// lane-change eligibility (returned); admission candidacy of a front whose move
+// reaches the end.
 template <bool TAPE, bool TYPES>
-__device__ __forceinline__ void own_core(const Dev& d, int p, bool front, int t, unsigned ep, int e, float x,
+__device__ __forceinline__ bool own_core(const Dev& d, int p, bool front, int t, unsigned ep, int e, float x,
                                          float v, int vid, int lane, int nxt, float x1, float v1, int vid1) {
   const LinkRec L = d.links[e];
   ClassPar P;
@@ -359,7 +361,7 @@ __device__ __forceinline__ void own_core(const Dev& d, int p, bool front, int t,
   d.intent[p] = 0;
   // lane-change candidates: multi-lane link, away from both link ends
   const bool elig = L.lanes >= 2 && x >= d.zone && xo < L.len - d.zone;
-  uint8_t fl = (front ? kFlagFront : 0) | (hold ? kFlagHolder : 0) | (elig ? kFlagElig : 0);
+  uint8_t fl = (front ? kFlagFront : 0) | (hold ? kFlagHolder : 0);
   // admission candidate: front, route continues, stop line open, move reaches the
   // end and lands behind the rearmost vehicle of the mapped lane
   if (front && nxt >= 0 && !closed && xo >= L.len) {
@@ -370,27 +372,60 @@ __device__ __forceinline__ void own_core(const Dev& d, int p, bool front, int t,
     }
   }
   d.flags[p] = fl;
+  return elig;
 }
 
 template <bool TAPE, bool TYPES>
-__device__ __forceinline__ void own_one(const Dev& d, int p, bool front, int t, unsigned ep) {
+__device__ __forceinline__ bool own_one(const Dev& d, int p, bool front, int t, unsigned ep) {
   const float x1 = front ? 0.0f : d.B.x[p + 1], v1 = front ? 0.0f : d.B.v[p + 1];
   const int vid1 = front ? 0 : d.B.vid[p + 1];
-  own_core<TAPE, TYPES>(d, p, front, t, ep, d.B.link[p], d.B.x[p], d.B.v[p], d.B.vid[p], d.B.lane[p], d.B.nxt[p],
-                        x1, v1, vid1);
+  return own_core<TAPE, TYPES>(d, p, front, t, ep, d.B.link[p], d.B.x[p], d.B.v[p], d.B.vid[p], d.B.lane[p],
+                               d.B.nxt[p], x1, v1, vid1);
 }
 
+// Append the positions of the block's threads where `pred` holds to the lane-change
+// candidate list, in thread order, with one atomic on the list counter per block.
+// Every thread of the block must call it (it holds two block barriers).
+constexpr int kMaxWarps = 32;   // blocks of up to 1024 threads
+
+__device__ __forceinline__ void block_append(const Dev& d, bool pred, int pos) {
+  __shared__ int wn[kMaxWarps + 1];
+  const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+  const unsigned m = __ballot_sync(0xffffffffu, pred);
+  if (ln == 0) wn[w] = __popc(m);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int tot = 0;
+    const int nw = (int)(blockDim.x >> 5);
+    for (int k = 0; k < nw; k++) {
+      const int c = wn[k];
+      wn[k] = tot;
+      tot += c;
+    }
+    wn[kMaxWarps] = tot ? atomicAdd(&d.ctl->n_elig, tot) : 0;
+  }
+  __syncthreads();
+  if (pred) d.elig[wn[kMaxWarps] + wn[w] + __popc(m & ((1u << ln) - 1u))] = pos;
+}
+
+// The block walks blockDim consecutive sorted positions at a time (block-uniform trip
+// count, for the candidate list's block barriers).
 template <bool TAPE, bool TYPES>
 __device__ __forceinline__ void ph_own(const Dev& d) {
   const int nB = d.ctl->nB;
   const int t = (int)d.ctl->t;
   const unsigned ep = d.ctl->occ_epoch;
-  GRID_STRIDE(p, nB) {
-    // the lane of sorted position p is tg[p]; p is its lane's front when the next
-    // position starts another lane
-    const int g = d.tg[p];
-    const bool front = p + 1 == nB || d.tg[p + 1] != g;
-    own_one<TAPE, TYPES>(d, p, front, t, ep);
+  for (int base = blockIdx.x * blockDim.x; base < nB; base += gridDim.x * blockDim.x) {
+    const int p = base + threadIdx.x;
+    bool el = false;
+    if (p < nB) {
+      // the lane of sorted position p is tg[p]; p is its lane's front when the next
+      // position starts another lane
+      const int g = d.tg[p];
+      const bool front = p + 1 == nB || d.tg[p + 1] != g;
+      el = own_one<TAPE, TYPES>(d, p, front, t, ep);
+    }
+    block_append(d, el, p);
   }
 }
 
@@ -523,40 +558,13 @@ __device__ __forceinline__ void decide_one(const Dev& d, int p, int t, unsigned 
   }
 }
 
-// Each warp walks 32 consecutive sorted positions at a time and queues the lane-change
-// candidates flagged by the own-lane kernel in shared memory; the decisions run 32 at
-// a time, so the long decision path runs on full warps without a global list.
-constexpr int kMaxWarps = 32;   // blocks of up to 1024 threads
-
+// One thread per lane-change candidate of the list built by the own-lane kernel.
 template <bool TAPE, bool TYPES>
 __device__ __forceinline__ void ph_decide(const Dev& d) {
-  __shared__ int dq[kMaxWarps][64];
-  const int nB = d.ctl->nB;
+  const int ne = d.ctl->n_elig;
   const int t = (int)d.ctl->t;
   const unsigned ep = d.ctl->occ_epoch;
-  const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
-  const unsigned lt = (1u << ln) - 1u;
-  int* q = dq[w];
-  int qn = 0;   // warp-uniform queue length
-  const int stride = gridDim.x * blockDim.x;
-  for (int base = blockIdx.x * blockDim.x + (w << 5); base < nB; base += stride) {
-    const int p = base + ln;
-    const bool el = p < nB && (d.flags[p] & kFlagElig) != 0;
-    const unsigned m = __ballot_sync(0xffffffffu, el);
-    if (el) q[qn + __popc(m & lt)] = p;
-    qn += __popc(m);
-    __syncwarp();
-    if (qn >= 32) {
-      const int pe = q[ln];
-      __syncwarp();
-      if (ln < qn - 32) q[ln] = q[ln + 32];
-      __syncwarp();
-      qn -= 32;
-      decide_one<TAPE, TYPES>(d, pe, t, ep);
-    }
-  }
-  if (ln < qn) decide_one<TAPE, TYPES>(d, q[ln], t, ep);
-  __syncwarp();
+  GRID_STRIDE(i, ne) decide_one<TAPE, TYPES>(d, d.elig[i], t, ep);
 }
 
 template <bool TAPE, bool TYPES>
@@ -806,12 +814,14 @@ __host__ __device__ __forceinline__ bool outputs_on(const Dev& d) { return d.emi
 __device__ __forceinline__ void ph_finish(const Dev& d) {
   Ctl* c = d.ctl;
   c->veh_steps += (unsigned long long)c->nB;
+  c->lc_evals += (unsigned long long)c->n_elig;
   c->departed += (unsigned long long)c->n_ins;
   c->arrived += (unsigned long long)c->n_arr;
   c->active_last = c->nB;
   c->nA = c->nB + c->n_ins;
   c->n_ins = 0;
   c->n_arr = 0;
+  c->n_elig = 0;
   c->t += 1;
 }
 
@@ -884,12 +894,38 @@ __device__ __forceinline__ void own_issue(const Dev& d, OwnTile* tl, uint64_t* b
   bulk_g2s(tl->nxt, d.B.nxt + b, kTile * 4, bar);
 }
 
+// Lane-change candidates of one warp, gathered in shared memory and appended to the
+// global list kListCap - 32 or more at a time (one atomic on the list counter per
+// flush).  Every lane of the warp takes part in each call.
+constexpr int kListCap = 256;
+
+__device__ __forceinline__ void warp_list_flush(const Dev& d, const int* buf, int& qn) {
+  __syncwarp();
+  const int ln = threadIdx.x & 31;
+  int base = 0;
+  if (ln == 0 && qn > 0) base = atomicAdd(&d.ctl->n_elig, qn);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  for (int i = ln; i < qn; i += 32) d.elig[base + i] = buf[i];
+  __syncwarp();
+  qn = 0;
+}
+
+__device__ __forceinline__ void warp_list_push(const Dev& d, int* buf, int& qn, bool pred, int pos) {
+  const unsigned m = __ballot_sync(0xffffffffu, pred);
+  if (pred) buf[qn + __popc(m & ((1u << (threadIdx.x & 31)) - 1u))] = pos;
+  qn += __popc(m);
+  if (qn > kListCap - 32) warp_list_flush(d, buf, qn);
+}
+
 // Own-lane step with the sorted state staged tile by tile (blocks of kTile threads,
 // one resident wave walking the tiles).  A wait that runs out sets kErrTimeout.
 template <bool TYPES>
 __global__ void __launch_bounds__(kTile) k_own_tiled(Dev d) {
   __shared__ OwnTile tl[kStages];
   __shared__ __align__(8) uint64_t bar[kStages];
+  __shared__ int lists[kTile / 32][kListCap];
+  int* lbuf = lists[threadIdx.x >> 5];
+  int lq = 0;   // warp-uniform
   const int nB = d.ctl->nB;
   const int t = (int)d.ctl->t;
   const unsigned ep = d.ctl->occ_epoch;
@@ -922,13 +958,16 @@ __global__ void __launch_bounds__(kTile) k_own_tiled(Dev d) {
     const OwnTile& T = tl[s];
     const int i = threadIdx.x;
     const int p = (blockIdx.x + k * gridDim.x) * kTile + i;
+    bool el = false;
     if (p < nB) {
       const bool front = p + 1 == nB || T.tg[i + 1] != T.tg[i];
-      own_core<false, TYPES>(d, p, front, t, ep, T.link[i], T.x[i], T.v[i], T.vid[i], T.lane[i], T.nxt[i],
-                             T.x[i + 1], T.v[i + 1], T.vid[i + 1]);
+      el = own_core<false, TYPES>(d, p, front, t, ep, T.link[i], T.x[i], T.v[i], T.vid[i], T.lane[i], T.nxt[i],
+                                  T.x[i + 1], T.v[i + 1], T.vid[i + 1]);
     }
-    __syncthreads();
+    warp_list_push(d, lbuf, lq, el, p);
+    __syncthreads();   // the reads of stage s end before it is refilled
   }
+  warp_list_flush(d, lbuf, lq);
 }
 
 // blocks of the tiled own-lane kernel resident on one SM (plain, with vehicle types)

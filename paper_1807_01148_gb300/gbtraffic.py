@@ -55,7 +55,8 @@ class sim_params(C.Structure):
 
 class sim_counters_t(C.Structure):
     _fields_ = [(k, C.c_int64) for k in
-                ("t", "departed", "waiting", "active", "arrived", "veh_steps", "pending", "active_last")]
+                ("t", "departed", "waiting", "active", "arrived", "veh_steps", "pending", "active_last",
+                 "lc_evals")]
 
 
 class sim_exec(C.Structure):

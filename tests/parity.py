@@ -41,7 +41,7 @@ def compare(g, o, label="", check_occ=True):
     d = diff_state(sg, so)
     assert not d, f"{label}: state differs (field, vids, gpu, oracle, count): {d}"
     cg, co = g.counters(), o.counters()
-    for k in ("t", "departed", "waiting", "active", "arrived", "veh_steps", "pending", "active_last"):
+    for k in ("t", "departed", "waiting", "active", "arrived", "veh_steps", "pending", "active_last", "lc_evals"):
         assert cg[k] == co[k], f"{label}: counter {k} gpu {cg[k]} oracle {co[k]}"
     if check_occ:
         lg, vg = g.occupancy()

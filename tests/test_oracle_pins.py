@@ -415,6 +415,21 @@ def test_simultaneous_changes_lower_id_wins():
     assert o.state()["lane_change"].tolist()[:2] == [1, -1]
 
 
+def test_lane_change_evaluation_count():
+    # decisions are evaluated for vehicles on a multi-lane link that are at least two
+    # vehicle lengths (10 m) past its start and whose own-lane move ends at least 10 m
+    # before its end: of the five vehicles below only the two in the middle of the
+    # 2-lane link qualify (x = 5 m is too close to the start, x = 995 m to the end, and
+    # the last one is on a 1-lane link)
+    net = make_net([(0.0, 0.0), (1000.0, 0.0), (2000.0, 0.0)], [(0, 1), (1, 2)], lanes=[2, 1])
+    st = dict(link=[0, 0, 0, 0, 1], lane=[0, 0, 1, 1, 0], x=[5.0, 500.0, 600.0, 995.0, 500.0],
+              v=[0.0] * 5)
+    o = _run(scenario(net, [[0, 1]] * 4 + [[1]], st), 1)
+    assert o.counters()["lc_evals"] == 2
+    o.step(1)
+    assert o.counters()["lc_evals"] == 4
+
+
 # ---------------------------------------------------------------- intersections
 def test_red_light_holds_then_releases():
     # node 1 signalised, offset 0: the east-west approach is red for steps 0..59
