@@ -213,7 +213,9 @@ int sim_autotune(sim_handle* h, int32_t trial_steps, const char* cache_path, sim
 
 /* Read the per-trip state (fields = OR of SIM_F_*).  on_device = 1: the view's
  * pointers are device pointers (e.g. from torch tensors) of n_trips elements each;
- * on_device = 0: host pointers.  The call synchronises the stream. */
+ * on_device = 0: host pointers (pinned host memory copies fastest); the first host read
+ * of a field allocates a device staging buffer of n_trips elements that the handle keeps
+ * until sim_destroy.  The call synchronises the stream. */
 int sim_read_state(sim_handle* h, const sim_state_view* out, uint32_t fields, int on_device);
 
 /* Replace the vehicle state (resume, tests).  Host arrays [n_trips]: status,

@@ -49,6 +49,7 @@ void launch_fw_final_time(const double* t0, const double* x, const double* cap, 
 void launch_compact_routes(const int32_t* roff, const int32_t* rlen, const int32_t* src, const int32_t* new_off,
                            int32_t* dst, int n, cudaStream_t s);
 int own_tiled_blocks_per_sm(bool types);
+int decide_blocks_per_sm(bool types);
 int persistent_max_blocks_per_sm(int threads);
 cudaError_t launch_persistent(const Dev& d, GridSync* gs, int blocks, int threads, int n_steps, long long limit,
                               cudaStream_t s);
@@ -60,6 +61,7 @@ static std::string g_create_error;
 
 struct sim_handle {
   std::string err;
+  void* stage[9] = {};   // device staging of sim_read_state's host reads, per field
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   int device = 0, sm_count = 0, grid = 0;
@@ -285,7 +287,10 @@ int create_from_flat(Flat& F, sim_handle** out) {
   cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
   if (h->sm_count <= 0) h->sm_count = 1;
   h->grid = h->sm_count * 8;
-  for (int ty = 0; ty < 2; ty++) h->d.own_grid[ty] = std::max(1, own_tiled_blocks_per_sm(ty != 0)) * h->sm_count;
+  for (int ty = 0; ty < 2; ty++) {
+    h->d.own_grid[ty] = std::max(1, own_tiled_blocks_per_sm(ty != 0)) * h->sm_count;
+    h->d.dec_grid[ty] = std::max(1, decide_blocks_per_sm(ty != 0)) * h->sm_count;
+  }
 
   // in-links of every node in ascending link id -> round-robin index, in-degree
   std::vector<int> n_in(F.nn, 0), in_index(F.nl, 0);
@@ -1113,21 +1118,20 @@ int sim_read_state(sim_handle* h, const sim_state_view* out, uint32_t fields, in
                   out->insert_step, out->arrive_step, out->lane_change};
   const size_t esz[9] = {1, 4, 4, 4, 4, 4, 4, 4, 1};
   void* dptr[9] = {nullptr};
-  std::vector<void*> tmp;
   for (int f = 0; f < 9; f++) {
     if (!(fields & (1u << f))) continue;
     if (!ptr[f]) return fail(h, SIM_EINVAL, "requested field has a NULL pointer");
     if (on_device) {
       dptr[f] = ptr[f];
     } else {
-      void* q;
-      cudaError_t e = cudaMalloc(&q, nt ? nt * esz[f] : 1);
-      if (e != cudaSuccess) {
-        for (void* p : tmp) cudaFree(p);
-        return cuda_fail(h, e, "read_state buffer");
+      // device staging buffer of the field, allocated at its first host read and kept
+      // for the handle's lifetime
+      if (!h->stage[f]) {
+        uint8_t* q;
+        if (int rc = dalloc(h, &q, nt ? nt * esz[f] : 1)) return rc;
+        h->stage[f] = q;
       }
-      tmp.push_back(q);
-      dptr[f] = q;
+      dptr[f] = h->stage[f];
     }
   }
   if (nt)
@@ -1139,7 +1143,6 @@ int sim_read_state(sim_handle* h, const sim_state_view* out, uint32_t fields, in
     for (int f = 0; f < 9 && e == cudaSuccess; f++)
       if (dptr[f] && nt) e = cudaMemcpyAsync(ptr[f], dptr[f], nt * esz[f], cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  for (void* p : tmp) cudaFree(p);
   if (e != cudaSuccess) return cuda_fail(h, e, "read_state");
   return SIM_OK;
 }

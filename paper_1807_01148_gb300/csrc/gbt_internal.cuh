@@ -190,6 +190,7 @@ struct Dev {
   const int32_t* q_items;
   Ctl* ctl;
   int own_grid[2];                 // blocks of the tiled own-lane kernel (plain, vehicle types)
+  int dec_grid[2];                 // blocks of the decision kernel (plain, vehicle types)
 };
 
 // Trip-planning work description (one shortest-path tree per distinct origin).

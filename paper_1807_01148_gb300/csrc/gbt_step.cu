@@ -568,7 +568,7 @@ __device__ __forceinline__ void ph_decide(const Dev& d) {
 }
 
 template <bool TAPE, bool TYPES>
-__global__ void __launch_bounds__(256, 4) k_decide(Dev d) { ph_decide<TAPE, TYPES>(d); }
+__global__ void __launch_bounds__(256, 6) k_decide(Dev d) { ph_decide<TAPE, TYPES>(d); }
 
 // ------------------------------------------------------------------ measured outputs
 // Sec. 6.3.1: trip vid leaves link e in step t; it entered it in step enter[vid]
@@ -970,6 +970,14 @@ __global__ void __launch_bounds__(kTile) k_own_tiled(Dev d) {
   warp_list_flush(d, lbuf, lq);
 }
 
+// blocks of the decision kernel resident on one SM (plain, with vehicle types)
+int decide_blocks_per_sm(bool types) {
+  int nb = 0;
+  cudaError_t e = types ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_decide<false, true>, 256, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_decide<false, false>, 256, 0);
+  return e == cudaSuccess ? nb : 0;
+}
+
 // blocks of the tiled own-lane kernel resident on one SM (plain, with vehicle types)
 int own_tiled_blocks_per_sm(bool types) {
   int nb = 0;
@@ -1023,9 +1031,10 @@ void launch_kernel(int k, const Dev& d, int grid, cudaStream_t s) {
       }
       break;
     case kKDecide:
+      // one resident wave: the candidate list's length is known on the device only
       if (d.tape) k_decide<true, false><<<grid, 256, 0, s>>>(d);
-      else if (d.vtype) k_decide<false, true><<<grid, 256, 0, s>>>(d);
-      else k_decide<false, false><<<grid, 256, 0, s>>>(d);
+      else if (d.vtype) k_decide<false, true><<<d.dec_grid[1], 256, 0, s>>>(d);
+      else k_decide<false, false><<<d.dec_grid[0], 256, 0, s>>>(d);
       break;
     case kKMoveInsert:
       if (d.tape) k_move_insert<true, false, false><<<grid, 256, 0, s>>>(d);
