@@ -442,6 +442,7 @@ int create_from_flat(Flat& F, sim_handle** out) {
     if (cudaMemset(d.cnt, 0, (size_t)nlan * 4) != cudaSuccess ||
         cudaMemset(d.best, 0xFF, (size_t)nlan * 8) != cudaSuccess ||
         cudaMemset(d.rear, 0, (size_t)nlan * sizeof(RearRec)) != cudaSuccess ||
+        cudaMemset(d.at, 0, nt ? nt * 4 : 4) != cudaSuccess ||
         cudaMemset(d.acq, 0xFF, (size_t)F.nn * 8) != cudaSuccess ||
         cudaMemset(d.holder, 0xFF, (size_t)F.nn * 4) != cudaSuccess ||
         cudaMemset(d.ctl, 0, sizeof(Ctl)) != cudaSuccess || cudaMemset(h->gs, 0, sizeof(GridSync)) != cudaSuccess ||

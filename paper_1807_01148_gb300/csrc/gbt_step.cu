@@ -177,12 +177,14 @@ __global__ void k_scan_fin(Dev d) { ph_scan_fin(d); }
 __device__ __forceinline__ void ph_scatter(const Dev& d) {
   const int nA = d.ctl->nA;
   GRID_STRIDE(s, nA) {
-    int e = d.A.link[s];
+    // every load of the slot is issued before the test (slots below nA are allocated)
+    const int e = d.A.link[s];
+    const int g = d.A.gid[s], ai = d.aidx[s], vid = d.A.vid[s];
+    const float x = d.A.x[s];
     if (e < 0) continue;
-    int g = d.A.gid[s];
-    int p = d.lane_start[g] + d.aidx[s];
-    d.tx[p] = d.A.x[s];
-    d.tvid[p] = d.A.vid[s];
+    const int p = d.lane_start[g] + ai;
+    d.tx[p] = x;
+    d.tvid[p] = vid;
     d.tsrc[p] = s;
     d.tg[p] = g;
   }
@@ -203,26 +205,28 @@ __device__ __forceinline__ void ph_rank(const Dev& d) {
   const unsigned ep = d.ctl->occ_epoch;
   GRID_STRIDE(p, nB) {
     const int g = d.tg[p];
-    const int s0 = d.lane_start[g], s1 = d.lane_start[g + 1];
+    const int src = d.tsrc[p];
     const float xp = d.tx[p];
     const int vp = d.tvid[p];
+    // the state to move does not depend on the rank: its loads overlap the count
+    const int e = d.A.link[src], nxt = d.A.nxt[src], lane = d.A.lane[src], cur = d.A.cur[src];
+    const float vv = d.A.v[src];
+    const uint8_t mv = d.A.mv[src];
+    const int s0 = d.lane_start[g], s1 = d.lane_start[g + 1];
     int rank = 0;
     for (int q = s0; q < s1; q++) {
       const float xq = d.tx[q];
       rank += (xq < xp || (xq == xp && d.tvid[q] < vp)) ? 1 : 0;
     }
     const int dst = s0 + rank;
-    const int src = d.tsrc[p];
-    const int e = d.A.link[src], nxt = d.A.nxt[src], lane = d.A.lane[src];
-    const float vv = d.A.v[src];
     d.B.x[dst] = xp;
     d.B.v[dst] = vv;
     d.B.vid[dst] = vp;
     d.B.link[dst] = e;
     d.B.nxt[dst] = nxt;
-    d.B.cur[dst] = d.A.cur[src];
+    d.B.cur[dst] = cur;
     d.B.lane[dst] = lane;
-    d.B.mv[dst] = d.A.mv[src];
+    d.B.mv[dst] = mv;
     if (rank == 0) d.rear[g] = RearRec{xp, vv, vp, ep};
     if (dst + 1 == s1 && nxt >= 0) {
       const LinkRec& L = d.links[e];
@@ -636,6 +640,9 @@ __device__ __forceinline__ void ph_move(const Dev& d) {
     const int vid = d.B.vid[p], lane = d.B.lane[p], nxt = d.B.nxt[p], cur = d.B.cur[p];
     const uint8_t fl = d.flags[p];
     int change = d.intent[p];
+    // both candidate accelerations, read before the change is settled (at[] holds an
+    // older step's value where no change was decided, and is then not used)
+    const float a_own = d.a_own[p], a_chg = d.at[p];
     if (change != 0) {
       // cancelled by a lower-id vehicle changing into the same lane less than
       // (vehicle length + s0) away, the longer of the two lengths with vehicle types;
@@ -657,7 +664,7 @@ __device__ __forceinline__ void ph_move(const Dev& d) {
       }
       if (cancel) change = 0;
     }
-    const float acc = change ? d.at[p] : d.a_own[p];
+    const float acc = change ? a_chg : a_own;
     float x1, v1;
     ballistic(x, v, acc, d.dt, d.hdt2, x1, v1);
     if (OUT && d.emis) {
