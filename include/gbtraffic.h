@@ -185,7 +185,12 @@ int sim_step_timed(sim_handle* h, int32_t n_steps, float* kernel_ms);
 const char* sim_kernel_name(int32_t k);
 
 /* How sim_step runs the steps.  SIM_EXEC_GRAPH: one CUDA graph of the step's kernels
- * per step, grid = grid_per_sm x SMs blocks of 256 threads.  SIM_EXEC_PERSISTENT: all
+ * per step, grid = grid_per_sm x SMs blocks of 256 threads for the kernels that do not
+ * size their own grid (the own-lane and decision kernels run one resident wave); the
+ * own-lane kernel's waits for its shared-memory tiles are bounded by
+ * barrier_timeout_cycles SM cycles (<= 0: 2e9), after which sim_step returns
+ * SIM_ETIMEOUT (the state is then undefined until the next sim_write_state /
+ * sim_route).  SIM_EXEC_PERSISTENT: all
  * n steps in one cooperative launch of blocks_per_sm x SMs blocks of `threads`
  * threads, the phases of a step separated by a grid barrier whose wait is bounded by
  * barrier_timeout_cycles SM cycles (<= 0: 2e9, about a second); a wait that runs out
@@ -197,7 +202,8 @@ typedef struct {
   int32_t threads;                  /* persistent: 256, 512 or 1024 */
   int32_t blocks_per_sm;            /* persistent: 1 .. co-resident limit */
   int32_t grid_per_sm;              /* graph: 1 .. 64 */
-  int64_t barrier_timeout_cycles;   /* persistent: bound of a barrier wait */
+  int64_t barrier_timeout_cycles;   /* persistent: bound of a barrier wait; graph: bound of a
+                                       tile wait of the own-lane kernel */
 } sim_exec;
 
 int sim_set_exec(sim_handle* h, const sim_exec* e);

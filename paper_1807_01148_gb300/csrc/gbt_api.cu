@@ -287,6 +287,7 @@ int create_from_flat(Flat& F, sim_handle** out) {
   cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
   if (h->sm_count <= 0) h->sm_count = 1;
   h->grid = h->sm_count * 8;
+  h->d.wait_limit = kDefaultWaitCycles;
   for (int ty = 0; ty < 2; ty++) {
     h->d.own_grid[ty] = std::max(1, own_tiled_blocks_per_sm(ty != 0)) * h->sm_count;
     h->d.dec_grid[ty] = std::max(1, decide_blocks_per_sm(ty != 0)) * h->sm_count;
@@ -1031,7 +1032,7 @@ int sim_step(sim_handle* h, int32_t n_steps) {
   }
   if (h->exec.mode == SIM_EXEC_PERSISTENT) {
     const int blocks = h->exec.blocks_per_sm * h->sm_count;
-    const long long limit = h->exec.barrier_timeout_cycles > 0 ? h->exec.barrier_timeout_cycles : 2000000000LL;
+    const long long limit = h->exec.barrier_timeout_cycles > 0 ? h->exec.barrier_timeout_cycles : kDefaultWaitCycles;
     const sim_exec& x = h->exec;
     const bool same = h->pexec && h->pgraph_n == n_steps && h->pgraph_cfg.threads == x.threads &&
                       h->pgraph_cfg.blocks_per_sm == x.blocks_per_sm &&
@@ -1079,6 +1080,7 @@ int sim_set_exec(sim_handle* h, const sim_exec* e) {
   if (x.mode == SIM_EXEC_GRAPH) {
     if (x.grid_per_sm < 1 || x.grid_per_sm > 64) return fail(h, SIM_EINVAL, "grid_per_sm must be 1..64");
     h->grid = x.grid_per_sm * h->sm_count;
+    h->d.wait_limit = x.barrier_timeout_cycles > 0 ? x.barrier_timeout_cycles : kDefaultWaitCycles;
     h->graph_dirty = true;
   h->pgraph_n = -1;
     h->tape_graph_dirty = true;

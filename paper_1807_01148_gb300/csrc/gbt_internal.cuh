@@ -18,6 +18,10 @@ constexpr int kCtrlNone = 0, kCtrlStop = 1, kCtrlSignal = 2;
 constexpr int kPending = 0, kActive = 1, kArrived = 2;
 constexpr int kTurnThrough = 0, kTurnLeft = 1, kTurnRight = 2, kTurnEnd = 3;
 
+// Default bound of a device-side wait (grid barrier, tile copy), in SM cycles: about a
+// second at GB300 clocks.
+constexpr long long kDefaultWaitCycles = 2000000000LL;
+
 // error word bits (device -> host)
 constexpr int kErrLane = 1, kErrLink = 2, kErrSlot = 4, kErrRoute = 8, kErrUnreach = 16,
               kErrRouteCap = 32, kErrQueue = 64, kErrTimeout = 128;
@@ -191,6 +195,7 @@ struct Dev {
   Ctl* ctl;
   int own_grid[2];                 // blocks of the tiled own-lane kernel (plain, vehicle types)
   int dec_grid[2];                 // blocks of the decision kernel (plain, vehicle types)
+  long long wait_limit;            // SM cycles a tile wait of the own-lane kernel may take
 };
 
 // Trip-planning work description (one shortest-path tree per distinct origin).

@@ -280,17 +280,18 @@ __device__ __forceinline__ float veh_len(const Dev& d, int vid) {
 // (smaller acceleration).  P, v0: the vehicle's Eq. 7 parameters; ep: the epoch of the
 // current rear records.  Optionally returns
 // the mapped lane (*gt), whether it has a rearmost vehicle other than this one
-// (*lead) and that vehicle's rear position (*room).
+// (*lead) and that vehicle's rear position (*room); next_rec: the next link's record
+// when the caller has loaded it already.
 template <bool TYPES>
 __device__ __forceinline__ float acc_front(const Dev& d, unsigned ep, const LinkRec& L, const ClassPar& P, float v0,
                                            int vid, int nxt, int lane, float x, float v, bool closed,
                                            TapeForm* f = nullptr, int* gt = nullptr, bool* lead = nullptr,
-                                           float* room = nullptr) {
+                                           float* room = nullptr, const LinkRec* next_rec = nullptr) {
   if (nxt < 0) {
     if (f) *f = TapeForm{-1, 0.0f, 0.0f, kFormFree, 0, 0, 0};
     return idm_acc(P, v0, d.s_min, 0.0f, v, 0.0f, false);
   }
-  const LinkRec Ln = d.links[nxt];
+  const LinkRec Ln = next_rec ? *next_rec : d.links[nxt];
   const int m = lane < Ln.lanes - 1 ? lane : Ln.lanes - 1;
   const int g = Ln.lane_base + m;
   const RearRec r = d.rear[g];
@@ -334,6 +335,9 @@ template <bool TAPE, bool TYPES>
 __device__ __forceinline__ bool own_core(const Dev& d, int p, bool front, int t, unsigned ep, int e, float x,
                                          float v, int vid, int lane, int nxt, float x1, float v1, int vid1) {
   const LinkRec L = d.links[e];
+  // a front looks across the link end: its next link's record is loaded with its own
+  LinkRec Lnx;
+  if (front && nxt >= 0) Lnx = d.links[nxt];
   ClassPar P;
   float v0;
   veh_par<TYPES>(d, L, vid, P, v0);
@@ -349,7 +353,8 @@ __device__ __forceinline__ bool own_core(const Dev& d, int p, bool front, int t,
     if (TAPE) f = TapeForm{vid1, sg, v1, kFormLead, 0, 0, 0};
   } else {
     closed = nxt >= 0 && line_closed(d, L, t, hold);
-    a = acc_front<TYPES>(d, ep, L, P, v0, vid, nxt, lane, x, v, closed, TAPE ? &f : nullptr, &gt, &lead, &room);
+    a = acc_front<TYPES>(d, ep, L, P, v0, vid, nxt, lane, x, v, closed, TAPE ? &f : nullptr, &gt, &lead, &room,
+                         &Lnx);
   }
   if (TAPE) {
     TapeRec* rec = tape_slot(d, t, vid);
@@ -840,7 +845,7 @@ __global__ void k_finish(Dev d) { ph_finish(d); }
 // block copies a tile's arrays into shared memory with cp.async.bulk (completion
 // counted on an mbarrier), kStages - 1 tiles ahead of the tile being computed.
 constexpr int kTile = 256, kStages = 3;
-constexpr long long kWaitLimit = 2000000000LL;   // SM cycles (about a second)
+constexpr long long kWaitLimit = kDefaultWaitCycles;   // drain of issued copies
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -864,13 +869,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for phase `parity` of bar: false after about a second.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred P1;\n\tmbarrier.test_wait.parity.shared::cta.b64 P1, [%1], %2;\n\tselp.u32 %0, 1, 0, P1;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for phase `parity` of bar for at most `limit` SM cycles (false when it runs out).
+// The first probe does not suspend the thread, so that a limit shorter than a copy's
+// latency runs out at once.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
   const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > kWaitLimit) return false;
-  return true;
+  if (mbar_test_wait(bar, parity)) return true;
+  while (clock64() - t0 <= limit)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
 }
 
 // bytes: a multiple of 16; src and dst 16-byte aligned
@@ -925,7 +942,9 @@ __device__ __forceinline__ void warp_list_push(const Dev& d, int* buf, int& qn, 
 }
 
 // Own-lane step with the sorted state staged tile by tile (blocks of kTile threads,
-// one resident wave walking the tiles).  A wait that runs out sets kErrTimeout.
+// one resident wave walking the tiles).  A wait for a tile that runs out (d.wait_limit
+// cycles) sets kErrTimeout; the block then lets the copies it issued land (waiting up
+// to kWaitLimit cycles for each) and returns.
 template <bool TYPES>
 __global__ void __launch_bounds__(kTile) k_own_tiled(Dev d) {
   __shared__ OwnTile tl[kStages];
@@ -951,13 +970,14 @@ __global__ void __launch_bounds__(kTile) k_own_tiled(Dev d) {
       own_issue(d, &tl[kn % kStages], &bar[kn % kStages], blockIdx.x + kn * gridDim.x);
     }
     const int s = k % kStages;
-    const bool ok = mbar_wait(&bar[s], (uint32_t)(k / kStages) & 1u);
+    const bool ok = mbar_wait(&bar[s], (uint32_t)(k / kStages) & 1u, d.wait_limit);
     if (!__syncthreads_and(ok)) {
       if (threadIdx.x == 0) {
         set_err(d, kErrTimeout, blockIdx.x);
         // let the copies already issued (tiles k .. k + kStages - 1) land before the
         // block's shared memory goes away
-        for (int j = k; j < n_my && j < k + kStages; j++) mbar_wait(&bar[j % kStages], (uint32_t)(j / kStages) & 1u);
+        for (int j = k; j < n_my && j < k + kStages; j++)
+          mbar_wait(&bar[j % kStages], (uint32_t)(j / kStages) & 1u, kWaitLimit);
       }
       __syncthreads();
       return;

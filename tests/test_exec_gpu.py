@@ -91,3 +91,24 @@ def test_barrier_timeout_returns_error_and_handle_recovers(G):
                        cursor=np.zeros(n, np.int32), x=np.zeros(n, np.float32), v=np.zeros(n, np.float32)))
     g.step(100)
     assert g.counters()["t"] == 100
+
+
+def test_tile_wait_timeout_returns_error_and_handle_recovers(G):
+    # graph execution with a one-cycle bound on the own-lane kernel's waits for its
+    # bulk-copied tiles: the first wait runs out while the copy is in flight, the kernel
+    # reports it and returns after its copies have landed; the handle is usable again
+    # after the state is reset
+    sc = S.small_grid(n=6, n_trips=400, steps=300)
+    g = G.Sim(sc)
+    g.route()
+    g.step(50)
+    g.set_exec(mode=0, grid_per_sm=8, barrier_timeout_cycles=1)
+    with pytest.raises(G.SimError) as e:
+        g.step(5)
+    assert e.value.code == G.SIM_ETIMEOUT
+    g.set_exec(mode=0, grid_per_sm=8)
+    n = sc["demand"]["n_trips"]
+    g.write_state(dict(status=np.zeros(n, np.uint8), link=np.zeros(n, np.int32), lane=np.zeros(n, np.int32),
+                       cursor=np.zeros(n, np.int32), x=np.zeros(n, np.float32), v=np.zeros(n, np.float32)))
+    g.step(100)
+    assert g.counters()["t"] == 100
