@@ -190,7 +190,7 @@ const char* sim_kernel_name(int32_t k);
  * own-lane kernel's waits for its shared-memory tiles are bounded by
  * barrier_timeout_cycles SM cycles (<= 0: 2e9), after which sim_step returns
  * SIM_ETIMEOUT (the state is then undefined until the next sim_write_state /
- * sim_route).  SIM_EXEC_PERSISTENT: all
+ * sim_route, and stepping calls return SIM_ESTATE until then).  SIM_EXEC_PERSISTENT: all
  * n steps in one cooperative launch of blocks_per_sm x SMs blocks of `threads`
  * threads, the phases of a step separated by a grid barrier whose wait is bounded by
  * barrier_timeout_cycles SM cycles (<= 0: 2e9, about a second); a wait that runs out

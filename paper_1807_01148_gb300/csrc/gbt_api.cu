@@ -62,6 +62,7 @@ static std::string g_create_error;
 struct sim_handle {
   std::string err;
   void* stage[9] = {};   // device staging of sim_read_state's host reads, per field
+  bool state_lost = false;   // a bounded device wait ran out: the state must be reset
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   int device = 0, sm_count = 0, grid = 0;
@@ -444,6 +445,8 @@ int create_from_flat(Flat& F, sim_handle** out) {
         cudaMemset(d.best, 0xFF, (size_t)nlan * 8) != cudaSuccess ||
         cudaMemset(d.rear, 0, (size_t)nlan * sizeof(RearRec)) != cudaSuccess ||
         cudaMemset(d.at, 0, nt ? nt * 4 : 4) != cudaSuccess ||
+        cudaMemset(d.a_own, 0, nt ? nt * 4 : 4) != cudaSuccess ||
+        cudaMemset(d.xo, 0, nt ? nt * 4 : 4) != cudaSuccess ||
         cudaMemset(d.acq, 0xFF, (size_t)F.nn * 8) != cudaSuccess ||
         cudaMemset(d.holder, 0xFF, (size_t)F.nn * 4) != cudaSuccess ||
         cudaMemset(d.ctl, 0, sizeof(Ctl)) != cudaSuccess || cudaMemset(h->gs, 0, sizeof(GridSync)) != cudaSuccess ||
@@ -554,6 +557,7 @@ int clear_outputs(sim_handle* h, long long t) {
 
 int reset_dynamic(sim_handle* h) {
   Dev& d = h->d;
+  h->state_lost = false;
   const size_t nt = (size_t)h->nt;
   CK(cudaMemsetAsync(d.status, 0, nt ? nt : 1, h->stream));
   CK(cudaMemsetAsync(d.ins_step, 0xFF, (nt ? nt : 1) * 4, h->stream));
@@ -590,6 +594,7 @@ int check_device(sim_handle* h) {
     char buf[160];
     snprintf(buf, sizeof buf, "device error word 0x%x (info %d) at step %lld", c.err, c.err_info, c.t);
     const int code = (c.err & kErrTimeout) ? SIM_ETIMEOUT : SIM_EDEVICE;
+    if (code == SIM_ETIMEOUT) h->state_lost = true;
     // clear the word so that the handle stays usable after the caller resets the state
     CK(cudaMemsetAsync(&h->d.ctl->err, 0, sizeof(int), h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -1005,6 +1010,7 @@ int sim_read_routes(sim_handle* h, int32_t* offsets, int32_t* links) {
 
 int sim_step(sim_handle* h, int32_t n_steps) {
   if (!h || n_steps < 0) return SIM_EINVAL;
+  if (h->state_lost) return fail(h, SIM_ESTATE, "the state is undefined after a timeout: sim_write_state or sim_route first");
   if (!h->routed) return fail(h, SIM_ESTATE, "sim_step before sim_route / sim_set_routes");
   if (n_steps == 0) return SIM_OK;
   long long t0 = 0;
@@ -1106,6 +1112,7 @@ int sim_get_exec(sim_handle* h, sim_exec* e) {
 
 int sim_step_timed(sim_handle* h, int32_t n_steps, float* kernel_ms) {
   if (!h || n_steps < 0 || !kernel_ms) return SIM_EINVAL;
+  if (h->state_lost) return fail(h, SIM_ESTATE, "the state is undefined after a timeout: sim_write_state or sim_route first");
   if (!h->routed) return fail(h, SIM_ESTATE, "sim_step_timed before sim_route / sim_set_routes");
   if (int rc = check_horizon(h, n_steps)) return rc;
   CK(launch_steps_timed(h->d, h->grid, h->has_stop, h->stream, n_steps, kernel_ms));
@@ -1333,6 +1340,7 @@ int sim_set_vehicle_types(sim_handle* h, int32_t n_types, const sim_vehicle_type
 
 int sim_observe(sim_handle* h, int32_t n_steps, int32_t obs_every, double* progress) {
   if (!h || !progress || obs_every <= 0 || n_steps < 0) return SIM_EINVAL;
+  if (h->state_lost) return fail(h, SIM_ESTATE, "the state is undefined after a timeout: sim_write_state or sim_route first");
   if (!h->routed) return fail(h, SIM_ESTATE, "sim_observe before routes exist");
   const int nobs = n_steps / obs_every;
   const size_t nt = (size_t)h->nt;
@@ -1400,6 +1408,7 @@ cudaError_t ckpt_copy(sim_handle* h, unsigned char* buf, bool save) {
 
 int sim_adjoint(sim_handle* h, const sim_loss_spec* spec, double* grad_out, double* loss_out) {
   if (!h || !spec || !grad_out || !loss_out || !spec->target) return SIM_EINVAL;
+  if (h->state_lost) return fail(h, SIM_ESTATE, "the state is undefined after a timeout: sim_write_state or sim_route first");
   if (!h->routed) return fail(h, SIM_ESTATE, "sim_adjoint before routes exist");
   if (h->out_flags) return fail(h, SIM_ESTATE, "sim_adjoint with measured outputs on (sim_set_outputs(h, 0, NULL))");
   if (h->d.vtype) return fail(h, SIM_ESTATE, "sim_adjoint covers the single vehicle class (sim_set_vehicle_types(h, 0, ...))");
@@ -1569,6 +1578,7 @@ void tune_cache_store(const char* path, const std::string& key, const sim_exec& 
 
 int sim_autotune(sim_handle* h, int32_t trial_steps, const char* cache_path, sim_exec* chosen) {
   if (!h || trial_steps < 1) return SIM_EINVAL;
+  if (h->state_lost) return fail(h, SIM_ESTATE, "the state is undefined after a timeout: sim_write_state or sim_route first");
   if (!h->routed) return fail(h, SIM_ESTATE, "sim_autotune before routes exist");
   if (h->out_flags) return fail(h, SIM_ESTATE, "sim_autotune with measured outputs on (its trial steps would count)");
   const std::string key = tune_key(h);
@@ -1757,6 +1767,7 @@ int sim_measured_costs(sim_handle* h, const int32_t* prev_cost_ds, int32_t* cost
 int sim_equilibrium(sim_handle* h, int32_t n_iter, const uint32_t* fractions_q16, int32_t n_steps, int32_t* cost_out,
                     double* gap_out) {
   if (!h || !fractions_q16 || !cost_out || !gap_out) return SIM_EINVAL;
+  if (h->state_lost) return fail(h, SIM_ESTATE, "the state is undefined after a timeout: sim_write_state or sim_route first");
   if (!h->d.tt_sum) return fail(h, SIM_ESTATE, "sim_equilibrium needs the link-time output");
   if (n_iter < 1 || n_steps < 1) return fail(h, SIM_EINVAL, "n_iter and n_steps must be >= 1");
   for (int k = 1; k < n_iter; k++)

@@ -737,6 +737,14 @@ __device__ __forceinline__ void ph_move(const Dev& d) {
       }
     }
     if (hold) d.holder[L.to] = crossed ? -1 : vid;
+    // a lane outside the link can only come from a step whose own-lane pass was cut
+    // short by a wait that ran out (stale decisions): the vehicle is dropped and the
+    // step reports it
+    if (!crossed && (unsigned)nl >= L.lanes) {
+      set_err(d, kErrLane, vid);
+      d.A.link[p] = -1;
+      continue;
+    }
     // lane count for the next occupancy rebuild
     const int gb = crossed ? d.links[nlink].lane_base : L.lane_base;
     const int gn = gb + nl;

@@ -84,8 +84,11 @@ def test_barrier_timeout_returns_error_and_handle_recovers(G):
     with pytest.raises(G.SimError) as e:
         g.step(5)
     assert e.value.code == G.SIM_ETIMEOUT
-    # back to a sane configuration: reset the state and step again
+    # back to a sane configuration: the handle refuses to step until the state is reset
     g.set_exec(mode=0, grid_per_sm=8)
+    with pytest.raises(G.SimError) as e:
+        g.step(1)
+    assert e.value.code == G.SIM_ESTATE
     n = sc["demand"]["n_trips"]
     g.write_state(dict(status=np.zeros(n, np.uint8), link=np.zeros(n, np.int32), lane=np.zeros(n, np.int32),
                        cursor=np.zeros(n, np.int32), x=np.zeros(n, np.float32), v=np.zeros(n, np.float32)))
@@ -107,6 +110,9 @@ def test_tile_wait_timeout_returns_error_and_handle_recovers(G):
         g.step(5)
     assert e.value.code == G.SIM_ETIMEOUT
     g.set_exec(mode=0, grid_per_sm=8)
+    with pytest.raises(G.SimError) as e:
+        g.step(1)
+    assert e.value.code == G.SIM_ESTATE
     n = sc["demand"]["n_trips"]
     g.write_state(dict(status=np.zeros(n, np.uint8), link=np.zeros(n, np.int32), lane=np.zeros(n, np.int32),
                        cursor=np.zeros(n, np.int32), x=np.zeros(n, np.float32), v=np.zeros(n, np.float32)))
