@@ -49,8 +49,8 @@ ALG_UNIT["decide"] = "lane-change candidate"
 # summarised in profiles/step_kernels_metro_snapshot.md (metro network, first 1,000,000
 # trips on their GPU-planned routes, 979,812 active vehicles, 489,835 candidates),
 # valid only for the kernel source it was taken on.
-PROFILED_SRC_SHA = "2b8d905340cea1bb"
-PROFILED_TRAFFIC = {"scatter": 23.6, "rank": 64.7, "own": 63.5, "decide": 130.9, "move_insert": 79.1}
+PROFILED_SRC_SHA = "120fbf894801061e"
+PROFILED_TRAFFIC = {"scatter": 23.6, "rank": 64.6, "own": 63.6, "decide": 137.0, "move_insert": 81.4}
 
 
 def kernel_source_sha():
