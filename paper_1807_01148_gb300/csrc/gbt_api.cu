@@ -447,6 +447,8 @@ int create_from_flat(Flat& F, sim_handle** out) {
         cudaMemset(d.at, 0, nt ? nt * 4 : 4) != cudaSuccess ||
         cudaMemset(d.a_own, 0, nt ? nt * 4 : 4) != cudaSuccess ||
         cudaMemset(d.xo, 0, nt ? nt * 4 : 4) != cudaSuccess ||
+        cudaMemset(d.intent, 0, nt ? nt : 1) != cudaSuccess ||
+        cudaMemset(d.flags, 0, nt ? nt : 1) != cudaSuccess ||
         cudaMemset(d.acq, 0xFF, (size_t)F.nn * 8) != cudaSuccess ||
         cudaMemset(d.holder, 0xFF, (size_t)F.nn * 4) != cudaSuccess ||
         cudaMemset(d.ctl, 0, sizeof(Ctl)) != cudaSuccess || cudaMemset(h->gs, 0, sizeof(GridSync)) != cudaSuccess ||
