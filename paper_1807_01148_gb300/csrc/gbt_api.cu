@@ -63,6 +63,10 @@ struct sim_handle {
   std::string err;
   void* stage[9] = {};   // device staging of sim_read_state's host reads, per field
   bool state_lost = false;   // a bounded device wait ran out: the state must be reset
+  // host copy of the device step counter, valid while only sim_step (and reads) ran
+  // since it was taken: sim_step then checks the horizon without a device round trip
+  long long t_host = 0;
+  bool t_known = false;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   int device = 0, sm_count = 0, grid = 0;
@@ -560,6 +564,7 @@ int clear_outputs(sim_handle* h, long long t) {
 int reset_dynamic(sim_handle* h) {
   Dev& d = h->d;
   h->state_lost = false;
+  h->t_known = false;
   const size_t nt = (size_t)h->nt;
   CK(cudaMemsetAsync(d.status, 0, nt ? nt : 1, h->stream));
   CK(cudaMemsetAsync(d.ins_step, 0xFF, (nt ? nt : 1) * 4, h->stream));
@@ -576,14 +581,19 @@ int reset_dynamic(sim_handle* h) {
 
 // Step times stay below 2^31 / dt_ds so that the device's 32-bit phase arithmetic is exact.
 int check_horizon(sim_handle* h, int n_steps, long long* t_now = nullptr) {
-  Ctl c;
-  CK(cudaMemcpyAsync(&c, h->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
-  if (t_now) *t_now = c.t;
+  if (!h->t_known) {
+    Ctl c;
+    CK(cudaMemcpyAsync(&c, h->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->t_host = c.t;
+    h->t_known = true;
+  }
+  const long long t = h->t_host;
+  if (t_now) *t_now = t;
   const long long limit = 2147483647LL / (h->d.dt_ds + 1);
-  if (c.t + (long long)n_steps > limit) return fail(h, SIM_EINVAL, "simulation horizon beyond 2^31 deciseconds");
+  if (t + (long long)n_steps > limit) return fail(h, SIM_EINVAL, "simulation horizon beyond 2^31 deciseconds");
   const Dev& d = h->d;
-  if (d.acc_u && n_steps > 0 && (c.t + n_steps - 1) / d.samp_every / d.samp_per >= d.samp_max)
+  if (d.acc_u && n_steps > 0 && (t + n_steps - 1) / d.samp_every / d.samp_per >= d.samp_max)
     return fail(h, SIM_EINVAL, "edge-sample windows would run past max_windows");
   return SIM_OK;
 }
@@ -592,6 +602,8 @@ int check_device(sim_handle* h) {
   Ctl c;
   CK(cudaMemcpyAsync(&c, h->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  h->t_host = c.t;
+  h->t_known = true;
   if (c.err) {
     char buf[160];
     snprintf(buf, sizeof buf, "device error word 0x%x (info %d) at step %lld", c.err, c.err_info, c.t);
@@ -922,17 +934,20 @@ int sim_create_batch(int32_t n, const sim_network* const* nets, const sim_demand
 
 int sim_set_stream(sim_handle* h, void* stream) {
   if (!h) return SIM_EINVAL;
+  h->t_known = false;
   h->stream = (cudaStream_t)stream;
   return SIM_OK;
 }
 
 int sim_route(sim_handle* h, const int32_t* link_cost_ds) {
   if (!h) return SIM_EINVAL;
+  h->t_known = false;
   return route_impl(h, link_cost_ds, nullptr);
 }
 
 int sim_reroute(sim_handle* h, const int32_t* link_cost_ds, uint32_t fraction_q16, uint32_t round) {
   if (!h || !link_cost_ds) return SIM_EINVAL;
+  h->t_known = false;
   if (!h->routed) return fail(h, SIM_ESTATE, "sim_reroute before routes exist");
   if (fraction_q16 > 65536u) return fail(h, SIM_EINVAL, "fraction_q16 must be 0..65536");
   std::vector<uint8_t> sel(h->nt);
@@ -942,6 +957,7 @@ int sim_reroute(sim_handle* h, const int32_t* link_cost_ds, uint32_t fraction_q1
 
 int sim_set_routes(sim_handle* h, const int32_t* offsets, const int32_t* links) {
   if (!h || !offsets || !links) return SIM_EINVAL;
+  h->t_known = false;
   const int nt = h->nt;
   if (offsets[0] != 0) return fail(h, SIM_EINVAL, "offsets[0] must be 0");
   for (int i = 0; i < nt; i++) {
@@ -1084,6 +1100,7 @@ int sim_step(sim_handle* h, int32_t n_steps) {
 
 int sim_set_exec(sim_handle* h, const sim_exec* e) {
   if (!h || !e) return SIM_EINVAL;
+  h->t_known = false;
   sim_exec x = *e;
   if (x.mode == SIM_EXEC_GRAPH) {
     if (x.grid_per_sm < 1 || x.grid_per_sm > 64) return fail(h, SIM_EINVAL, "grid_per_sm must be 1..64");
@@ -1114,6 +1131,7 @@ int sim_get_exec(sim_handle* h, sim_exec* e) {
 
 int sim_step_timed(sim_handle* h, int32_t n_steps, float* kernel_ms) {
   if (!h || n_steps < 0 || !kernel_ms) return SIM_EINVAL;
+  h->t_known = false;
   if (h->state_lost) return fail(h, SIM_ESTATE, "the state is undefined after a timeout: sim_write_state or sim_route first");
   if (!h->routed) return fail(h, SIM_ESTATE, "sim_step_timed before sim_route / sim_set_routes");
   if (int rc = check_horizon(h, n_steps)) return rc;
@@ -1162,6 +1180,7 @@ int sim_read_state(sim_handle* h, const sim_state_view* out, uint32_t fields, in
 int sim_write_state(sim_handle* h, const uint8_t* status, const int32_t* link, const int32_t* lane,
                     const int32_t* cursor, const float* x, const float* v) {
   if (!h || !status || !link || !lane || !cursor || !x || !v) return SIM_EINVAL;
+  h->t_known = false;
   if (!h->routed) return fail(h, SIM_ESTATE, "sim_write_state before routes exist");
   const int nt = h->nt;
   uint8_t* ds;
@@ -1219,6 +1238,7 @@ int sim_write_state(sim_handle* h, const uint8_t* status, const int32_t* link, c
 
 int sim_occupancy(sim_handle* h, int32_t* lane_start, int32_t* sorted_vid) {
   if (!h || !lane_start || !sorted_vid) return SIM_EINVAL;
+  h->t_known = false;
   if (!h->routed) return fail(h, SIM_ESTATE, "no routes");
   launch_occupancy(h->d, h->grid, h->stream);
   int32_t* dv;
@@ -1271,6 +1291,7 @@ int sim_counters(sim_handle* h, sim_counters_t* out) {
 int sim_set_class_params(sim_handle* h, const float* v0, const float* T, const float* a, const float* b,
                          const float* s0) {
   if (!h || !v0 || !T || !a || !b || !s0) return SIM_EINVAL;
+  h->t_known = false;
   for (int c = 0; c < h->ncls; c++)
     if (!(a[c] > 0.0f) || !(b[c] > 0.0f) || !(T[c] >= 0.0f) || !(s0[c] >= 0.0f) ||
         ((h->v0c[c] > 0.0f) != (v0[c] > 0.0f)))
@@ -1298,6 +1319,7 @@ int sim_set_class_params(sim_handle* h, const float* v0, const float* T, const f
 
 int sim_set_vehicle_types(sim_handle* h, int32_t n_types, const sim_vehicle_type* types, const uint8_t* trip_type) {
   if (!h || n_types < 0 || n_types > SIM_MAX_VEHICLE_TYPES) return SIM_EINVAL;
+  h->t_known = false;
   if (n_types > 0 && (!types || (!trip_type && h->nt > 0))) return SIM_EINVAL;
   for (int k = 0; k < n_types; k++)
     if (!(types[k].length_m > 0.0f) || !(types[k].accel_scale > 0.0f) || !(types[k].max_speed_mps > 0.0f))
@@ -1342,6 +1364,7 @@ int sim_set_vehicle_types(sim_handle* h, int32_t n_types, const sim_vehicle_type
 
 int sim_observe(sim_handle* h, int32_t n_steps, int32_t obs_every, double* progress) {
   if (!h || !progress || obs_every <= 0 || n_steps < 0) return SIM_EINVAL;
+  h->t_known = false;
   if (h->state_lost) return fail(h, SIM_ESTATE, "the state is undefined after a timeout: sim_write_state or sim_route first");
   if (!h->routed) return fail(h, SIM_ESTATE, "sim_observe before routes exist");
   const int nobs = n_steps / obs_every;
@@ -1397,6 +1420,7 @@ cudaError_t ckpt_copy(sim_handle* h, unsigned char* buf, bool save) {
     off += it.n;
   }
   if (!save) {
+    h->t_known = false;   // the restored step counter
     // epoch-tagged keys written after the checkpoint would outrank the replayed steps' keys
     cudaError_t e = cudaMemsetAsync(d.best, 0xFF, L.nlan * 8, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.acq, 0xFF, L.nn * 8, h->stream);
@@ -1410,6 +1434,7 @@ cudaError_t ckpt_copy(sim_handle* h, unsigned char* buf, bool save) {
 
 int sim_adjoint(sim_handle* h, const sim_loss_spec* spec, double* grad_out, double* loss_out) {
   if (!h || !spec || !grad_out || !loss_out || !spec->target) return SIM_EINVAL;
+  h->t_known = false;
   if (h->state_lost) return fail(h, SIM_ESTATE, "the state is undefined after a timeout: sim_write_state or sim_route first");
   if (!h->routed) return fail(h, SIM_ESTATE, "sim_adjoint before routes exist");
   if (h->out_flags) return fail(h, SIM_ESTATE, "sim_adjoint with measured outputs on (sim_set_outputs(h, 0, NULL))");
@@ -1418,6 +1443,7 @@ int sim_adjoint(sim_handle* h, const sim_loss_spec* spec, double* grad_out, doub
   const int seg = spec->checkpoint_every > 0 ? spec->checkpoint_every : 64;
   if (n_steps <= 0 || every <= 0 || n_steps % every) return fail(h, SIM_EINVAL, "n_steps must be a multiple of obs_every");
   if (int rc = check_horizon(h, n_steps)) return rc;
+  h->t_known = false;   // the passes below advance and restore the step counter
   const int nobs = n_steps / every, nseg = (n_steps + seg - 1) / seg;
   const size_t nt = (size_t)std::max(1, h->nt);
   // sim_step's graph
@@ -1580,6 +1606,7 @@ void tune_cache_store(const char* path, const std::string& key, const sim_exec& 
 
 int sim_autotune(sim_handle* h, int32_t trial_steps, const char* cache_path, sim_exec* chosen) {
   if (!h || trial_steps < 1) return SIM_EINVAL;
+  h->t_known = false;
   if (h->state_lost) return fail(h, SIM_ESTATE, "the state is undefined after a timeout: sim_write_state or sim_route first");
   if (!h->routed) return fail(h, SIM_ESTATE, "sim_autotune before routes exist");
   if (h->out_flags) return fail(h, SIM_ESTATE, "sim_autotune with measured outputs on (its trial steps would count)");
@@ -1647,6 +1674,7 @@ int sim_autotune(sim_handle* h, int32_t trial_steps, const char* cache_path, sim
 // ------------------------------------------------------------------ measured outputs
 int sim_set_outputs(sim_handle* h, uint32_t flags, const sim_sampling* sampling) {
   if (!h) return SIM_EINVAL;
+  h->t_known = false;
   if (flags & ~(uint32_t)(SIM_OUT_EMISSIONS | SIM_OUT_LINK_TIMES | SIM_OUT_EDGE_SAMPLES))
     return fail(h, SIM_EINVAL, "unknown output flag");
   int every = 0, per = 0, maxw = 0;
@@ -1696,6 +1724,7 @@ int sim_set_outputs(sim_handle* h, uint32_t flags, const sim_sampling* sampling)
 
 int sim_reset_outputs(sim_handle* h) {
   if (!h) return SIM_EINVAL;
+  h->t_known = false;
   return clear_outputs(h, -1);
 }
 
@@ -1739,6 +1768,7 @@ int sim_read_edge_samples(sim_handle* h, double* util, double* speed, int32_t* n
 
 int sim_measured_costs(sim_handle* h, const int32_t* prev_cost_ds, int32_t* cost_ds, double* gap) {
   if (!h || !prev_cost_ds || !cost_ds) return SIM_EINVAL;
+  h->t_known = false;
   const Dev& d = h->d;
   if (!d.tt_sum) return fail(h, SIM_ESTATE, "link-time output is off");
   const int nl = h->nl;
@@ -1769,6 +1799,7 @@ int sim_measured_costs(sim_handle* h, const int32_t* prev_cost_ds, int32_t* cost
 int sim_equilibrium(sim_handle* h, int32_t n_iter, const uint32_t* fractions_q16, int32_t n_steps, int32_t* cost_out,
                     double* gap_out) {
   if (!h || !fractions_q16 || !cost_out || !gap_out) return SIM_EINVAL;
+  h->t_known = false;
   if (h->state_lost) return fail(h, SIM_ESTATE, "the state is undefined after a timeout: sim_write_state or sim_route first");
   if (!h->d.tt_sum) return fail(h, SIM_ESTATE, "sim_equilibrium needs the link-time output");
   if (n_iter < 1 || n_steps < 1) return fail(h, SIM_EINVAL, "n_iter and n_steps must be >= 1");
@@ -1802,6 +1833,7 @@ double fixed_scale(double bound, int n) {
 int sim_assign_static(sim_handle* h, const sim_assign_spec* spec, double* flow_out, double* time_out, double* gap_out,
                       double* step_out, double* objective_out) {
   if (!h || !spec || !spec->capacity || !flow_out || !time_out || !objective_out) return SIM_EINVAL;
+  h->t_known = false;
   const int nl = h->nl, nn = h->nn, K = spec->max_iter, beta = spec->beta;
   const double alpha = spec->alpha;
   if (beta < 1 || beta > 8 || !(alpha >= 0.0) || K < 0 || spec->bisect_iter < 0 || spec->bisect_iter > 60)
