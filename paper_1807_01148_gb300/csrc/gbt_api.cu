@@ -21,6 +21,7 @@ void launch_state_out(const Dev& d, int grid, cudaStream_t s, uint8_t* status, i
 void launch_state_in(const Dev& d, int grid, cudaStream_t s, const uint8_t* status, const int32_t* link,
                      const int32_t* lane, const int32_t* cursor, const float* x, const float* v);
 void launch_occ_out(const Dev& d, int grid, cudaStream_t s, int32_t* sorted_vid);
+void launch_status_counts(const Dev& d, int grid, cudaStream_t s, unsigned long long* counts);
 void launch_state_check(const Dev& d, int grid, cudaStream_t s, const uint8_t* status, const int32_t* link,
                         const int32_t* lane, const int32_t* cursor, const float* x, const float* v, int* bad);
 cudaError_t launch_steps_timed(const Dev& d, int grid, bool has_stop, cudaStream_t s, int n, float* kernel_ms);
@@ -59,6 +60,11 @@ using namespace gbt;
 
 static std::string g_create_error;
 
+struct HostMirror {
+  Ctl c;
+  unsigned long long counts[3];   // active, waiting (due, not on the road), pending (not yet due)
+};
+
 struct sim_handle {
   std::string err;
   void* stage[9] = {};   // device staging of sim_read_state's host reads, per field
@@ -67,6 +73,10 @@ struct sim_handle {
   // since it was taken: sim_step then checks the horizon without a device round trip
   long long t_host = 0;
   bool t_known = false;
+  // pinned host copy of the control block and of the trip-status counts (read back by
+  // every sim_step and sim_counters) and their device source for the counts
+  HostMirror* mirror = nullptr;
+  unsigned long long* d_counts = nullptr;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   int device = 0, sm_count = 0, grid = 0;
@@ -465,6 +475,12 @@ int create_from_flat(Flat& F, sim_handle** out) {
       rc = fail(h, SIM_ECUDA, "cudaStreamCreate failed");
       goto fail_rc;
     }
+    TRY(dalloc(h, &h->d_counts, 3));
+    if (cudaMallocHost(&h->mirror, sizeof(HostMirror)) != cudaSuccess) {
+      h->mirror = nullptr;
+      rc = fail(h, SIM_ENOMEM, "cudaMallocHost of the control-block mirror failed");
+      goto fail_rc;
+    }
     if (cudaDeviceSynchronize() != cudaSuccess) {
       rc = fail(h, SIM_ECUDA, "device synchronize after create failed");
       goto fail_rc;
@@ -582,10 +598,9 @@ int reset_dynamic(sim_handle* h) {
 // Step times stay below 2^31 / dt_ds so that the device's 32-bit phase arithmetic is exact.
 int check_horizon(sim_handle* h, int n_steps, long long* t_now = nullptr) {
   if (!h->t_known) {
-    Ctl c;
-    CK(cudaMemcpyAsync(&c, h->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&h->mirror->c, h->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    h->t_host = c.t;
+    h->t_host = h->mirror->c.t;
     h->t_known = true;
   }
   const long long t = h->t_host;
@@ -599,9 +614,9 @@ int check_horizon(sim_handle* h, int n_steps, long long* t_now = nullptr) {
 }
 
 int check_device(sim_handle* h) {
-  Ctl c;
-  CK(cudaMemcpyAsync(&c, h->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(&h->mirror->c, h->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  const Ctl c = h->mirror->c;
   h->t_host = c.t;
   h->t_known = true;
   if (c.err) {
@@ -1263,19 +1278,16 @@ int sim_n_lanes(sim_handle* h, int64_t* n) {
 
 int sim_counters(sim_handle* h, sim_counters_t* out) {
   if (!h || !out) return SIM_EINVAL;
-  Ctl c;
-  CK(cudaMemcpyAsync(&c, h->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
-  std::vector<uint8_t> st(h->nt);
-  if (h->nt) CK(cudaMemcpyAsync(st.data(), h->d.status, (size_t)h->nt, cudaMemcpyDeviceToHost, h->stream));
+  // trip statuses counted on the device against the step counter there
+  CK(cudaMemsetAsync(h->d_counts, 0, 3 * sizeof(unsigned long long), h->stream));
+  launch_status_counts(h->d, h->grid, h->stream, h->d_counts);
+  CK(cudaMemcpyAsync(&h->mirror->c, h->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h->mirror->counts, h->d_counts, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                     h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  int64_t waiting = 0, pending = 0, active = 0;
-  for (int i = 0; i < h->nt; i++) {
-    if (st[i] == SIM_ACTIVE) active++;
-    else if (st[i] == SIM_PENDING) {
-      if ((long long)h->depart[i] < c.t) waiting++;
-      else pending++;
-    }
-  }
+  const Ctl c = h->mirror->c;
+  const int64_t active = (int64_t)h->mirror->counts[0], waiting = (int64_t)h->mirror->counts[1],
+                pending = (int64_t)h->mirror->counts[2];
   out->t = c.t;
   out->departed = (int64_t)c.departed;
   out->waiting = waiting;
@@ -1984,6 +1996,7 @@ void sim_destroy(sim_handle* h) {
   if (h->pexec) cudaGraphExecDestroy(h->pexec);
   if (h->pgraph) cudaGraphDestroy(h->pgraph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->mirror) cudaFreeHost(h->mirror);
   for (void* p : h->allocs) cudaFree(p);
   delete h;
 }

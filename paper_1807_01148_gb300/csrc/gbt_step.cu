@@ -1301,6 +1301,31 @@ void launch_state_in(const Dev& d, int grid, cudaStream_t s, const uint8_t* stat
   k_state_in<<<grid, 256, 0, s>>>(d, status, link, lane, cursor, x, v);
 }
 
+// Trips by status at the current step: active, waiting (pending and due: departure step
+// < t) and pending (not yet due), reduced per warp, one atomic per warp and class.
+__global__ void k_status_counts(Dev d, unsigned long long* counts) {
+  const long long t = d.ctl->t;
+  const int n = d.n_trips;
+  for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += gridDim.x * blockDim.x) {
+    const int i = base + (threadIdx.x & 31);
+    int cls = -1;
+    if (i < n) {
+      const uint8_t s = d.status[i];
+      if (s == kActive) cls = 0;
+      else if (s == kPending) cls = (long long)d.depart[i] < t ? 1 : 2;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      const unsigned m = __ballot_sync(0xffffffffu, cls == k);
+      if ((threadIdx.x & 31) == 0 && m) atomicAdd(&counts[k], (unsigned long long)__popc(m));
+    }
+  }
+}
+
+void launch_status_counts(const Dev& d, int grid, cudaStream_t s, unsigned long long* counts) {
+  k_status_counts<<<grid, 256, 0, s>>>(d, counts);
+}
+
 __global__ void k_occ_out(Dev d, int32_t* sorted_vid) {
   const int nB = d.ctl->nB;
   GRID_STRIDE(p, nB) sorted_vid[p] = d.B.vid[p];
