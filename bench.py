@@ -2,12 +2,14 @@
 
 Workload (default): the metropolitan network (225,000 nodes, 550,000 links, 3,000,000
 gravity-OD trips; dt = 0.5 s) with every trip on its GPU-planned shortest-path route
-and all of them on the road at once (the saturated snapshot).  One
+and all of them on the road at once (the saturated snapshot: every trip placed on a
+random hop of its route, evenly spaced in its lane, at half the speed limit).  One
 bench step = one simulation step of the whole hot path (occupancy rebuild,
 neighbours, lane changes, IDM, admission and transitions, departures, counters).
 
 Prints one JSON line.  ``--impl reference`` times the CPU oracle instead (the
-reference arm of this build), on a bounded sample of the same workload.
+reference arm: the plain single-threaded C implementation of the same model), on a
+bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -46,7 +48,7 @@ ALG_UNIT["decide"] = "lane-change candidate"
 
 
 # DRAM bytes (read + write) per unit of ALG_UNIT per launch from the ncu capture
-# summarised in profiles/step_kernels_metro_snapshot.md (metro network, first 1,000,000
+# summarised under profiles/ (metro network, first 1,000,000
 # trips on their GPU-planned routes, 979,812 active vehicles, 489,835 candidates),
 # valid only for the kernel source it was taken on.
 PROFILED_SRC_SHA = "120fbf894801061e"

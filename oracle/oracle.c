@@ -14,8 +14,8 @@
  *   - mandatory / discretionary lane changes with an exponential switch toward
  *     mandatory near the exit, plus lead/lag gap acceptance (Sec. 6.3.2);
  *   - stop signs (one vehicle at a time) and fixed-time traffic lights (Sec. 6.3.2).
- * Where the paper is silent the readings used here are listed in the design doc
- * ("Readings of the paper"); each is repeated at the function that applies it.
+ * Where the paper is silent a reading is taken; each reading is stated at the
+ * function that applies it.
  *
  * Floating point: every kinematic quantity is IEEE binary32 evaluated in the
  * written operation order; build with -ffp-contract=off (no fused multiply-add).
@@ -1232,7 +1232,7 @@ int orc_counters(const orc_sim* S, int64_t out[9]) {
 }
 
 /* ------------------------------------------------------------------ calibration adjoint
- * Not in the paper (the calibration workload of this build): loss
+ * Not in the paper (a calibration workload of the simulator): loss
  *   L = sum over observations k and trips v of (p_v(t_k) - target_{k,v})^2,
  * t_k = k * obs_every steps after the start, p_v = route progress (length of the
  * completed links of the route plus x; 0 before departure; the whole route length
