@@ -151,6 +151,20 @@ def dist_env():
     return world, rank, local
 
 
+def reduce_over_ranks(secs, veh_steps, world, device):
+    """Replicas (one per GPU, no exchange): the job takes the slowest rank's time and
+    advances the vehicle-steps of all ranks."""
+    if world <= 1:
+        return secs, veh_steps
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(secs)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    v = torch.tensor([float(veh_steps)], dtype=torch.float64, device=device)
+    dist.all_reduce(v, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(v.item())
+
+
 def lscpu_model():
     try:
         for line in open("/proc/cpuinfo"):
@@ -502,15 +516,7 @@ def run_cuda(args):
         assignment = measure_assignment(G, S, torch)
 
     # -- aggregate over ranks (replicas only: each rank runs its own copy)
-    secs = ms / 1e3
-    tot_vs = veh_steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([secs], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        v = torch.tensor([float(veh_steps)], device="cuda")
-        dist.all_reduce(v, op=dist.ReduceOp.SUM)
-        secs, tot_vs = float(t.item()), float(v.item())
+    secs, tot_vs = reduce_over_ranks(ms / 1e3, veh_steps, world, "cuda")
     adjoint = None
     if not args.no_adjoint:
         adjoint = measure_adjoint(G, S, torch)
