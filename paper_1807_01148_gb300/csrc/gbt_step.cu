@@ -20,6 +20,14 @@ namespace gbt {
 
 #define GRID_STRIDE(i, n) for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
 
+// The step kernels are launched with programmatic stream serialization: a kernel's
+// launch is prepared while the one before it in the stream runs, and the kernel waits
+// here, before its first read, until that grid has completed and its writes are
+// visible.  (Without such a launch the wait returns at once.)  No kernel triggers its
+// dependents early: waiting blocks would hold registers and shared memory that the
+// running kernel's blocks use (measured slower).
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Arrival index of this vehicle in lane g's count for the next occupancy rebuild.
 // Neighbouring threads mostly hold vehicles of the same lane (the sorted order), so
 // the threads of a warp with equal g share one atomic; the order inside the group is
@@ -36,6 +44,7 @@ __device__ __forceinline__ int count_in_lane(const Dev& d, int g) {
 
 // ------------------------------------------------------------------ occupancy
 __global__ void k_count(Dev d) {
+  griddep_wait();
   const int nA = d.ctl->nA;
   GRID_STRIDE(s, nA) {
     int e = d.A.link[s];
@@ -104,7 +113,10 @@ __device__ __forceinline__ void ph_scan_sum(const Dev& d) {
   }
 }
 
-__global__ void k_scan_sum(Dev d) { ph_scan_sum(d); }
+__global__ void k_scan_sum(Dev d) {
+  griddep_wait();
+  ph_scan_sum(d);
+}
 
 
 // Lane starts = chunk offset + exclusive scan inside the chunk; counts reset to zero.
@@ -172,7 +184,10 @@ __device__ __forceinline__ void ph_scan_fin(const Dev& d) {
   }
 }
 
-__global__ void k_scan_fin(Dev d) { ph_scan_fin(d); }
+__global__ void k_scan_fin(Dev d) {
+  griddep_wait();
+  ph_scan_fin(d);
+}
 
 __device__ __forceinline__ void ph_scatter(const Dev& d) {
   const int nA = d.ctl->nA;
@@ -190,7 +205,10 @@ __device__ __forceinline__ void ph_scatter(const Dev& d) {
   }
 }
 
-__global__ void k_scatter(Dev d) { ph_scatter(d); }
+__global__ void k_scatter(Dev d) {
+  griddep_wait();
+  ph_scatter(d);
+}
 
 // Rank of each vehicle inside its lane segment by (x, vid); the vehicle's state
 // moves from its slot in A to position lane_start + rank in B.  The vehicle that
@@ -236,7 +254,10 @@ __device__ __forceinline__ void ph_rank(const Dev& d) {
   }
 }
 
-__global__ void __launch_bounds__(256, 8) k_rank(Dev d) { ph_rank(d); }
+__global__ void __launch_bounds__(256, 8) k_rank(Dev d) {
+  griddep_wait();
+  ph_rank(d);
+}
 
 // ------------------------------------------------------------------ neighbours / IDM
 __device__ __forceinline__ bool is_holder(const Dev& d, const LinkRec& L, int t, int vid, int lane,
@@ -439,7 +460,10 @@ __device__ __forceinline__ void ph_own(const Dev& d) {
 }
 
 template <bool TAPE, bool TYPES>
-__global__ void __launch_bounds__(256, 6) k_own(Dev d) { ph_own<TAPE, TYPES>(d); }
+__global__ void __launch_bounds__(256, 6) k_own(Dev d) {
+  griddep_wait();
+  ph_own<TAPE, TYPES>(d);
+}
 
 // First position q in [s0, s1) whose (x, vid) exceeds (x, vid) of the probe.
 __device__ __forceinline__ int upper_pos(const Dev& d, int s0, int s1, float x, int vid) {
@@ -577,7 +601,10 @@ __device__ __forceinline__ void ph_decide(const Dev& d) {
 }
 
 template <bool TAPE, bool TYPES>
-__global__ void __launch_bounds__(256, 6) k_decide(Dev d) { ph_decide<TAPE, TYPES>(d); }
+__global__ void __launch_bounds__(256, 6) k_decide(Dev d) {
+  griddep_wait();
+  ph_decide<TAPE, TYPES>(d);
+}
 
 // ------------------------------------------------------------------ measured outputs
 // Sec. 6.3.1: trip vid leaves link e in step t; it entered it in step enter[vid]
@@ -628,7 +655,10 @@ __device__ __forceinline__ void ph_edge_sample(const Dev& d) {
   if (closes && blockIdx.x == 0 && threadIdx.x == 0) d.out_n[w] = (int32_t)(k - from + 1);
 }
 
-__global__ void k_edge_sample(Dev d) { ph_edge_sample(d); }
+__global__ void k_edge_sample(Dev d) {
+  griddep_wait();
+  ph_edge_sample(d);
+}
 
 // ------------------------------------------------------------------ move
 // OUT: the measured outputs are on (a separate instantiation keeps the plain kernel's
@@ -825,6 +855,7 @@ __device__ __forceinline__ void ph_insert(const Dev& d) {
 // sorted vehicles) and read only state of step t, so they share one launch.
 template <bool TAPE, bool OUT, bool TYPES>
 __global__ void k_move_insert(Dev d) {
+  griddep_wait();
   ph_move<TAPE, OUT, TYPES>(d);
   if (d.n_qlinks > 0) ph_insert<OUT, TYPES>(d);
 }
@@ -845,7 +876,10 @@ __device__ __forceinline__ void ph_finish(const Dev& d) {
   c->t += 1;
 }
 
-__global__ void k_finish(Dev d) { ph_finish(d); }
+__global__ void k_finish(Dev d) {
+  griddep_wait();
+  ph_finish(d);
+}
 
 
 // ------------------------------------------------------------------ bulk-copy staging
@@ -955,6 +989,7 @@ __device__ __forceinline__ void warp_list_push(const Dev& d, int* buf, int& qn, 
 // to kWaitLimit cycles for each) and returns.
 template <bool TYPES>
 __global__ void __launch_bounds__(kTile) k_own_tiled(Dev d) {
+  griddep_wait();
   __shared__ OwnTile tl[kStages];
   __shared__ __align__(8) uint64_t bar[kStages];
   __shared__ int lists[kTile / 32][kListCap];
@@ -1022,6 +1057,23 @@ int own_tiled_blocks_per_sm(bool types) {
 }
 
 // ------------------------------------------------------------------ launch sequence
+// Launch with programmatic stream serialization (the kernel starts with griddep_wait),
+// which hides part of the launch gap between the kernels of a step.
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kern)(KArgs...), int grid, int block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 void launch_kernel(int k, const Dev& d, int grid, cudaStream_t s);
 void launch_count(const Dev& d, int grid, cudaStream_t s);
 
@@ -1049,42 +1101,42 @@ void launch_kernel(int k, const Dev& d, int grid, cudaStream_t s) {
   const int nb = scan_blocks(d.n_lanes);
   switch (k) {
     case kKScanSum: k_scan_sum<<<nb, kScanThreads, 0, s>>>(d); break;
-    case kKScanFin: k_scan_fin<<<nb, kScanThreads, 0, s>>>(d); break;
-    case kKScatter: k_scatter<<<grid, 256, 0, s>>>(d); break;
-    case kKRank: k_rank<<<grid, 256, 0, s>>>(d); break;
+    case kKScanFin: launch_pdl(k_scan_fin, nb, kScanThreads, s, d); break;
+    case kKScatter: launch_pdl(k_scatter, grid, 256, s, d); break;
+    case kKRank: launch_pdl(k_rank, grid, 256, s, d); break;
     case kKOwn:
       // the per-edge sample (when enabled) reads the sorted state, like own; its time
       // is counted with own's
-      if (d.acc_u) k_edge_sample<<<grid, 256, 0, s>>>(d);
+      if (d.acc_u) launch_pdl(k_edge_sample, grid, 256, s, d);
       if (d.tape) {
-        k_own<true, false><<<grid, 256, 0, s>>>(d);
+        launch_pdl(k_own<true, false>, grid, 256, s, d);
       } else {
         // one resident wave of tile-walking blocks
         const int g2 = d.vtype ? d.own_grid[1] : d.own_grid[0];
-        if (d.vtype) k_own_tiled<true><<<g2, kTile, 0, s>>>(d);
-        else k_own_tiled<false><<<g2, kTile, 0, s>>>(d);
+        if (d.vtype) launch_pdl(k_own_tiled<true>, g2, kTile, s, d);
+        else launch_pdl(k_own_tiled<false>, g2, kTile, s, d);
       }
       break;
     case kKDecide:
       // one resident wave: the candidate list's length is known on the device only
-      if (d.tape) k_decide<true, false><<<grid, 256, 0, s>>>(d);
-      else if (d.vtype) k_decide<false, true><<<d.dec_grid[1], 256, 0, s>>>(d);
-      else k_decide<false, false><<<d.dec_grid[0], 256, 0, s>>>(d);
+      if (d.tape) launch_pdl(k_decide<true, false>, grid, 256, s, d);
+      else if (d.vtype) launch_pdl(k_decide<false, true>, d.dec_grid[1], 256, s, d);
+      else launch_pdl(k_decide<false, false>, d.dec_grid[0], 256, s, d);
       break;
     case kKMoveInsert:
-      if (d.tape) k_move_insert<true, false, false><<<grid, 256, 0, s>>>(d);
-      else if (d.vtype && outputs_on(d)) k_move_insert<false, true, true><<<grid, 256, 0, s>>>(d);
-      else if (d.vtype) k_move_insert<false, false, true><<<grid, 256, 0, s>>>(d);
-      else if (outputs_on(d)) k_move_insert<false, true, false><<<grid, 256, 0, s>>>(d);
-      else k_move_insert<false, false, false><<<grid, 256, 0, s>>>(d);
+      if (d.tape) launch_pdl(k_move_insert<true, false, false>, grid, 256, s, d);
+      else if (d.vtype && outputs_on(d)) launch_pdl(k_move_insert<false, true, true>, grid, 256, s, d);
+      else if (d.vtype) launch_pdl(k_move_insert<false, false, true>, grid, 256, s, d);
+      else if (outputs_on(d)) launch_pdl(k_move_insert<false, true, false>, grid, 256, s, d);
+      else launch_pdl(k_move_insert<false, false, false>, grid, 256, s, d);
       break;
-    case kKFinish: k_finish<<<1, 1, 0, s>>>(d); break;
+    case kKFinish: launch_pdl(k_finish, 1, 1, s, d); break;
     default: break;
   }
 }
 
 // lane counts of buffer A (after a state is loaded, or to restore them)
-void launch_count(const Dev& d, int grid, cudaStream_t s) { k_count<<<grid, 256, 0, s>>>(d); }
+void launch_count(const Dev& d, int grid, cudaStream_t s) { launch_pdl(k_count, grid, 256, s, d); }
 
 void launch_step(const Dev& d, int grid, bool has_stop, cudaStream_t s) {
   for (int k = 0; k < kNumKernels; k++)
