@@ -738,7 +738,9 @@ int route_impl(sim_handle* h, const int32_t* link_cost_ds, const std::vector<uin
   for (int e = 0; e < nl; e++) csum += cost[e];
   const int delta = (int)std::max<long long>(1, csum / std::max(1, nl));
 
-  const int n_cta = std::max(1, std::min<int>((int)origins.size(), h->sm_count * 2));
+  // four trees in flight per SM (one per 256-thread block): a tree's rounds are short and
+  // synchronous, so more trees hide more of their latency
+  const int n_cta = std::max(1, std::min<int>((int)origins.size(), h->sm_count * 4));
   std::vector<void*> tmp;
   auto talloc = [&](auto** p, size_t n) -> int {
     int rc = dalloc(h, p, n);

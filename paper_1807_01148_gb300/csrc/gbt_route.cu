@@ -30,7 +30,7 @@ __device__ __forceinline__ int dval(const unsigned long long* dist, int v, unsig
   return (unsigned)(k >> 32) == hi ? (int)(unsigned)k : INT_MAX;
 }
 
-__global__ void __launch_bounds__(512) k_sssp_route(RouteDev R) {
+__global__ void __launch_bounds__(256) k_sssp_route(RouteDev R) {
   __shared__ int sh_oi, sh_round, sh_nq, sh_nf, sh_min;
   __shared__ unsigned sh_epoch;
   const int tid = threadIdx.x, bd = blockDim.x;
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(512) k_sssp_route(RouteDev R) {
 }
 
 void launch_route(const RouteDev& R, int n_cta, cudaStream_t s) {
-  k_sssp_route<<<n_cta, 512, 0, s>>>(R);
+  k_sssp_route<<<n_cta, 256, 0, s>>>(R);
 }
 
 // first link of every trip's route (departure-queue keys)
