@@ -51,8 +51,8 @@ ALG_UNIT["decide"] = "lane-change candidate"
 # summarised under profiles/ (metro network, first 1,000,000
 # trips on their GPU-planned routes, 979,812 active vehicles, 489,835 candidates),
 # valid only for the kernel source it was taken on.
-PROFILED_SRC_SHA = "120fbf894801061e"
-PROFILED_TRAFFIC = {"scatter": 23.6, "rank": 64.6, "own": 63.6, "decide": 137.0, "move_insert": 81.4}
+PROFILED_SRC_SHA = "275e79e74f650b75"
+PROFILED_TRAFFIC = {"scatter": 23.6, "rank": 64.8, "own": 63.7, "decide": 137.1, "move_insert": 81.1}
 
 
 def kernel_source_sha():
