@@ -736,7 +736,11 @@ int route_impl(sim_handle* h, const int32_t* link_cost_ds, const std::vector<uin
     if (ts[v + 1] > ts[v]) origins.push_back(v);
   long long csum = 0;
   for (int e = 0; e < nl; e++) csum += cost[e];
-  const int delta = (int)std::max<long long>(1, csum / std::max(1, nl));
+  // bucket width of the near-far search: eight mean link costs (fewer far-pile splits
+  // for a few more re-relaxations inside a bucket; measured fastest on the metro; the
+  // distances, and so the routes, do not depend on it).  Below INT_MAX - 2e9 since a
+  // link costs at most 1e6.
+  const int delta = (int)std::max<long long>(1, 8 * csum / std::max(1, nl));
 
   // four trees in flight per SM (one per 256-thread block): a tree's rounds are short and
   // synchronous, so more trees hide more of their latency
