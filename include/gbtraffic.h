@@ -88,6 +88,9 @@ typedef struct {
   uint64_t seed;                     /* draws of the mandatory-switch distance */
   int32_t cost_mode;                 /* 0: free-flow length/speed; 1: sqrt(lanes)*length/speed */
   int32_t loop_routes;               /* 1: routes repeat forever (ring roads) */
+  uint64_t max_device_bytes;         /* cap on the device memory the handle allocates, 0: none;
+                                        a call that would pass it returns SIM_ENOMEM (all
+                                        scenarios of a batch must give the same value) */
 } sim_params;
 
 typedef struct sim_handle sim_handle;

@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gbt_internal.cuh"
 #include "gbtraffic.h"
 
@@ -60,6 +62,15 @@ using namespace gbt;
 
 static std::string g_create_error;
 
+// An NVTX range over one call of the C ABI (visible in Nsight timelines; header-only
+// NVTX3, inactive unless a tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 struct HostMirror {
   Ctl c;
   unsigned long long counts[3];   // active, waiting (due, not on the road), pending (not yet due)
@@ -91,6 +102,8 @@ struct sim_handle {
   int cost_mode = 0, loop = 0;
   // device
   std::vector<void*> allocs;
+  std::vector<size_t> alloc_sizes;   // bytes of each entry of allocs
+  size_t bytes = 0, max_bytes = 0;   // device bytes held; cap (0: none)
   Dev d{};
   int32_t* routes = nullptr;
   unsigned long long route_cap = 0;
@@ -152,10 +165,15 @@ int cuda_fail(sim_handle* h, cudaError_t e, const char* what) {
 
 template <class T>
 int dalloc(sim_handle* h, T** p, size_t n) {
+  const size_t nb = (n ? n : 1) * sizeof(T);
+  if (h->max_bytes && h->bytes + nb > h->max_bytes)
+    return fail(h, SIM_ENOMEM, "device memory cap (sim_params.max_device_bytes) reached");
   void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, (n ? n : 1) * sizeof(T));
+  cudaError_t e = cudaMalloc(&q, nb);
   if (e != cudaSuccess) return cuda_fail(h, e, "cudaMalloc");
   h->allocs.push_back(q);
+  h->alloc_sizes.push_back(nb);
+  h->bytes += nb;
   *p = static_cast<T*>(q);
   return SIM_OK;
 }
@@ -163,7 +181,12 @@ int dalloc(sim_handle* h, T** p, size_t n) {
 void dfree(sim_handle* h, void* p) {
   if (!p) return;
   auto it = std::find(h->allocs.begin(), h->allocs.end(), p);
-  if (it != h->allocs.end()) h->allocs.erase(it);
+  if (it != h->allocs.end()) {
+    const size_t k = (size_t)(it - h->allocs.begin());
+    h->bytes -= h->alloc_sizes[k];
+    h->alloc_sizes.erase(h->alloc_sizes.begin() + (long)k);
+    h->allocs.erase(it);
+  }
   cudaFree(p);
 }
 
@@ -210,7 +233,8 @@ int flatten(int n, const sim_network* const* nets, const sim_demand* const* dems
       if (P->dt != Q.dt || P->veh_len != Q.veh_len || P->s_min != Q.s_min || P->mobil_p != Q.mobil_p ||
           P->mobil_athr != Q.mobil_athr || P->mobil_bsafe != Q.mobil_bsafe ||
           P->mobil_bias_right != Q.mobil_bias_right || P->lambda_mand != Q.lambda_mand ||
-          P->stop_acquire_m != Q.stop_acquire_m || P->cost_mode != Q.cost_mode || P->loop_routes != Q.loop_routes)
+          P->stop_acquire_m != Q.stop_acquire_m || P->cost_mode != Q.cost_mode || P->loop_routes != Q.loop_routes ||
+          P->max_device_bytes != Q.max_device_bytes)
         return fail(nullptr, SIM_EINVAL, "batched scenarios must share dt and all scalar parameters");
     }
     const int nb = F.nn, lb = F.nl, cb = F.ncls;
@@ -283,6 +307,7 @@ int create_from_flat(Flat& F, sim_handle** out) {
   }
 
   sim_handle* h = new sim_handle();
+  h->max_bytes = (size_t)P.max_device_bytes;
   h->nn = F.nn;
   h->nl = F.nl;
   h->nt = F.nt;
@@ -935,6 +960,7 @@ int route_impl(sim_handle* h, const int32_t* link_cost_ds, const std::vector<uin
 extern "C" {
 
 int sim_create(const sim_network* net, const sim_demand* dem, const sim_params* par, sim_handle** out) {
+  NvtxRange nvtx_("sim_create");
   if (!out) return fail(nullptr, SIM_EINVAL, "out is NULL");
   *out = nullptr;
   Flat F;
@@ -945,6 +971,7 @@ int sim_create(const sim_network* net, const sim_demand* dem, const sim_params* 
 
 int sim_create_batch(int32_t n, const sim_network* const* nets, const sim_demand* const* dems,
                      const sim_params* const* pars, sim_handle** out) {
+  NvtxRange nvtx_("sim_create_batch");
   if (!out) return fail(nullptr, SIM_EINVAL, "out is NULL");
   *out = nullptr;
   Flat F;
@@ -961,12 +988,14 @@ int sim_set_stream(sim_handle* h, void* stream) {
 }
 
 int sim_route(sim_handle* h, const int32_t* link_cost_ds) {
+  NvtxRange nvtx_("sim_route");
   if (!h) return SIM_EINVAL;
   h->t_known = false;
   return route_impl(h, link_cost_ds, nullptr);
 }
 
 int sim_reroute(sim_handle* h, const int32_t* link_cost_ds, uint32_t fraction_q16, uint32_t round) {
+  NvtxRange nvtx_("sim_reroute");
   if (!h || !link_cost_ds) return SIM_EINVAL;
   h->t_known = false;
   if (!h->routed) return fail(h, SIM_ESTATE, "sim_reroute before routes exist");
@@ -977,6 +1006,7 @@ int sim_reroute(sim_handle* h, const int32_t* link_cost_ds, uint32_t fraction_q1
 }
 
 int sim_set_routes(sim_handle* h, const int32_t* offsets, const int32_t* links) {
+  NvtxRange nvtx_("sim_set_routes");
   if (!h || !offsets || !links) return SIM_EINVAL;
   h->t_known = false;
   const int nt = h->nt;
@@ -1048,6 +1078,7 @@ int sim_read_routes(sim_handle* h, int32_t* offsets, int32_t* links) {
 }
 
 int sim_step(sim_handle* h, int32_t n_steps) {
+  NvtxRange nvtx_("sim_step");
   if (!h || n_steps < 0) return SIM_EINVAL;
   if (h->state_lost) return fail(h, SIM_ESTATE, "the state is undefined after a timeout: sim_write_state or sim_route first");
   if (!h->routed) return fail(h, SIM_ESTATE, "sim_step before sim_route / sim_set_routes");
@@ -1151,6 +1182,7 @@ int sim_get_exec(sim_handle* h, sim_exec* e) {
 }
 
 int sim_step_timed(sim_handle* h, int32_t n_steps, float* kernel_ms) {
+  NvtxRange nvtx_("sim_step_timed");
   if (!h || n_steps < 0 || !kernel_ms) return SIM_EINVAL;
   h->t_known = false;
   if (h->state_lost) return fail(h, SIM_ESTATE, "the state is undefined after a timeout: sim_write_state or sim_route first");
@@ -1163,6 +1195,7 @@ int sim_step_timed(sim_handle* h, int32_t n_steps, float* kernel_ms) {
 const char* sim_kernel_name(int32_t k) { return (k >= 0 && k < kNumKernels) ? kKernelNames[k] : ""; }
 
 int sim_read_state(sim_handle* h, const sim_state_view* out, uint32_t fields, int on_device) {
+  NvtxRange nvtx_("sim_read_state");
   if (!h || !out) return SIM_EINVAL;
   const size_t nt = (size_t)h->nt;
   void* ptr[9] = {out->status, out->link, out->lane, out->cursor, out->x, out->v,
@@ -1200,6 +1233,7 @@ int sim_read_state(sim_handle* h, const sim_state_view* out, uint32_t fields, in
 
 int sim_write_state(sim_handle* h, const uint8_t* status, const int32_t* link, const int32_t* lane,
                     const int32_t* cursor, const float* x, const float* v) {
+  NvtxRange nvtx_("sim_write_state");
   if (!h || !status || !link || !lane || !cursor || !x || !v) return SIM_EINVAL;
   h->t_known = false;
   if (!h->routed) return fail(h, SIM_ESTATE, "sim_write_state before routes exist");
@@ -1283,6 +1317,7 @@ int sim_n_lanes(sim_handle* h, int64_t* n) {
 }
 
 int sim_counters(sim_handle* h, sim_counters_t* out) {
+  NvtxRange nvtx_("sim_counters");
   if (!h || !out) return SIM_EINVAL;
   // trip statuses counted on the device against the step counter there
   CK(cudaMemsetAsync(h->d_counts, 0, 3 * sizeof(unsigned long long), h->stream));
@@ -1381,6 +1416,7 @@ int sim_set_vehicle_types(sim_handle* h, int32_t n_types, const sim_vehicle_type
 }
 
 int sim_observe(sim_handle* h, int32_t n_steps, int32_t obs_every, double* progress) {
+  NvtxRange nvtx_("sim_observe");
   if (!h || !progress || obs_every <= 0 || n_steps < 0) return SIM_EINVAL;
   h->t_known = false;
   if (h->state_lost) return fail(h, SIM_ESTATE, "the state is undefined after a timeout: sim_write_state or sim_route first");
@@ -1451,6 +1487,7 @@ cudaError_t ckpt_copy(sim_handle* h, unsigned char* buf, bool save) {
 }  // namespace
 
 int sim_adjoint(sim_handle* h, const sim_loss_spec* spec, double* grad_out, double* loss_out) {
+  NvtxRange nvtx_("sim_adjoint");
   if (!h || !spec || !grad_out || !loss_out || !spec->target) return SIM_EINVAL;
   h->t_known = false;
   if (h->state_lost) return fail(h, SIM_ESTATE, "the state is undefined after a timeout: sim_write_state or sim_route first");
@@ -1581,7 +1618,7 @@ std::string tune_key(const sim_handle* h) {
   mix((unsigned long long)h->nt);
   mix((unsigned long long)h->n_lanes);
   mix((unsigned long long)h->has_stop);
-  char buf[256];
+  char buf[sizeof(prop.name) + 48];
   snprintf(buf, sizeof buf, "%s|sm%d|%016llx", prop.name, h->sm_count, hsh);
   return buf;
 }
@@ -1623,6 +1660,7 @@ void tune_cache_store(const char* path, const std::string& key, const sim_exec& 
 }  // namespace
 
 int sim_autotune(sim_handle* h, int32_t trial_steps, const char* cache_path, sim_exec* chosen) {
+  NvtxRange nvtx_("sim_autotune");
   if (!h || trial_steps < 1) return SIM_EINVAL;
   h->t_known = false;
   if (h->state_lost) return fail(h, SIM_ESTATE, "the state is undefined after a timeout: sim_write_state or sim_route first");
@@ -1785,6 +1823,7 @@ int sim_read_edge_samples(sim_handle* h, double* util, double* speed, int32_t* n
 }
 
 int sim_measured_costs(sim_handle* h, const int32_t* prev_cost_ds, int32_t* cost_ds, double* gap) {
+  NvtxRange nvtx_("sim_measured_costs");
   if (!h || !prev_cost_ds || !cost_ds) return SIM_EINVAL;
   h->t_known = false;
   const Dev& d = h->d;
@@ -1816,6 +1855,7 @@ int sim_measured_costs(sim_handle* h, const int32_t* prev_cost_ds, int32_t* cost
 
 int sim_equilibrium(sim_handle* h, int32_t n_iter, const uint32_t* fractions_q16, int32_t n_steps, int32_t* cost_out,
                     double* gap_out) {
+  NvtxRange nvtx_("sim_equilibrium");
   if (!h || !fractions_q16 || !cost_out || !gap_out) return SIM_EINVAL;
   h->t_known = false;
   if (h->state_lost) return fail(h, SIM_ESTATE, "the state is undefined after a timeout: sim_write_state or sim_route first");
@@ -1850,6 +1890,7 @@ double fixed_scale(double bound, int n) {
 
 int sim_assign_static(sim_handle* h, const sim_assign_spec* spec, double* flow_out, double* time_out, double* gap_out,
                       double* step_out, double* objective_out) {
+  NvtxRange nvtx_("sim_assign_static");
   if (!h || !spec || !spec->capacity || !flow_out || !time_out || !objective_out) return SIM_EINVAL;
   h->t_known = false;
   const int nl = h->nl, nn = h->nn, K = spec->max_iter, beta = spec->beta;

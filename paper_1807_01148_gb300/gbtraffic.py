@@ -50,7 +50,8 @@ class sim_params(C.Structure):
                 ("v0", C.c_void_p), ("T", C.c_void_p), ("a", C.c_void_p), ("b", C.c_void_p), ("s0", C.c_void_p),
                 ("mobil_p", C.c_float), ("mobil_athr", C.c_float), ("mobil_bsafe", C.c_float),
                 ("mobil_bias_right", C.c_float), ("lambda_mand", C.c_float), ("stop_acquire_m", C.c_float),
-                ("seed", C.c_uint64), ("cost_mode", C.c_int32), ("loop_routes", C.c_int32)]
+                ("seed", C.c_uint64), ("cost_mode", C.c_int32), ("loop_routes", C.c_int32),
+                ("max_device_bytes", C.c_uint64)]
 
 
 class sim_counters_t(C.Structure):
@@ -185,7 +186,7 @@ def _structs(sc, keep):
                    keep(par["b"], np.float32), keep(par["s0"], np.float32),
                    par["mobil_p"], par["mobil_athr"], par["mobil_bsafe"], par["mobil_bias_right"],
                    par["lambda_mand"], par["stop_acquire_m"], par["seed"] & (2**64 - 1),
-                   par["cost_mode"], par["loop_routes"])
+                   par["cost_mode"], par["loop_routes"], int(par.get("max_device_bytes", 0)))
     return n, d, p
 
 

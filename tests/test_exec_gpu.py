@@ -118,3 +118,23 @@ def test_tile_wait_timeout_returns_error_and_handle_recovers(G):
                        cursor=np.zeros(n, np.int32), x=np.zeros(n, np.float32), v=np.zeros(n, np.float32)))
     g.step(100)
     assert g.counters()["t"] == 100
+
+
+def test_device_memory_cap_returns_enomem(G):
+    # sim_params.max_device_bytes caps what a handle allocates: a creation that would pass
+    # it fails with SIM_ENOMEM (nothing is left allocated), a generous cap changes nothing
+    sc = S.small_grid(n=5, n_trips=200, steps=100)
+    tiny = dict(sc, params=dict(sc["params"], max_device_bytes=4096))
+    with pytest.raises(G.SimError) as e:
+        G.Sim(tiny)
+    assert e.value.code == G.SIM_ENOMEM
+    roomy = dict(sc, params=dict(sc["params"], max_device_bytes=1 << 30))
+    g = G.Sim(roomy)
+    g.route()
+    g.step(20)
+    ref = G.Sim(sc)
+    ref.route()
+    ref.step(20)
+    a, b = g.state(), ref.state()
+    assert all(np.array_equal(a[k], b[k]) for k in a)
+
