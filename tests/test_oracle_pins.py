@@ -430,6 +430,100 @@ def test_lane_change_evaluation_count():
     assert o.counters()["lc_evals"] == 4
 
 
+# ---------------------------------------------------------------- departures, look-ahead, arrival
+def _idm64(s, v, vl, has=True, a=A, b=B, T_=T, s0=S0, v0=V0, smin=SMIN):
+    """Eq. 7 as read (quotient v dv / (2 sqrt(ab)), dynamic part floored at 0, gap floored
+    at s_min), in binary64 and written out here, independent of the oracle's code."""
+    acc_free = a * (1.0 - (v / v0) ** 4)
+    if not has:
+        return acc_free
+    ss = s0 + max(0.0, v * T_ + v * (v - vl) / (2.0 * np.sqrt(a * b)))
+    return acc_free - a * (ss / max(s, smin)) ** 2
+
+
+def test_departures_fifo_lane_choice_and_space():
+    # four trips on one 2-lane first link: the queue releases them in (departure step, id)
+    # order, one per step at most; the first goes to lane 0 (both empty: tie to the lowest),
+    # the second to the other, still empty lane; the next waits until a lane's rearmost
+    # vehicle is s0 + vehicle length (7 m) clear of the link start
+    net = make_net([(0.0, 0.0), (1000.0, 0.0), (2000.0, 0.0)], [(0, 1), (1, 2)], lanes=2)
+    o = _run(scenario(net, [[0, 1]] * 4, depart=[1, 0, 0, 0]), 0)
+    ins, lanes, space_at_entry = {}, {}, {}
+    for t in range(200):
+        before = o.state()
+        o.step(1)
+        s = o.state()
+        new = np.flatnonzero((before["status"] == S.ST_PENDING) & (s["status"] == S.ST_ACTIVE))
+        assert len(new) <= 1                                   # one departure per first link and step
+        for i in new:
+            ins[int(i)] = t
+            lanes[int(i)] = int(s["lane"][i])
+            on = (before["status"] == S.ST_ACTIVE) & (before["link"] == 0) & (before["lane"] == s["lane"][i])
+            space_at_entry[int(i)] = float(before["x"][on].min()) - 5.0 if on.any() else np.inf
+        if len(ins) == 4:
+            break
+    assert sorted(ins, key=ins.get) == [1, 2, 3, 0]
+    assert lanes[1] == 0 and lanes[2] == 1 and ins[2] == ins[1] + 1
+    assert all(space_at_entry[i] >= S0 + 5.0 for i in ins)
+    assert ins[3] > ins[2] + 1                                  # waited for space
+
+
+def test_look_ahead_gap_across_the_link_end():
+    # A (vid 0) 10 m before the end of link 0; B (vid 1) 5 m into link 1, the next link of
+    # A's route: A follows B across the link end with gap (L - x_A) + x_B - len = 10 m
+    net = make_net([(0.0, 0.0), (500.0, 0.0), (1000.0, 0.0)], [(0, 1), (1, 2)], lanes=1)
+    st = dict(link=[0, 1], cursor=[0, 0], x=[490.0, 5.0], v=[10.0, 8.0])
+    o = _run(scenario(net, [[0, 1], [1]], st), 1)
+    a = (float(o.state()["v"][0]) - 10.0) / 0.5
+    assert abs(a - _idm64(10.0, 10.0, 8.0)) < 1e-4
+    # B farther into link 1 is still the rearmost vehicle there: gap 10 + 400 - 5 = 405 m
+    o = _run(scenario(net, [[0, 1], [1]], dict(link=[0, 1], cursor=[0, 0], x=[490.0, 400.0],
+                                              v=[10.0, 8.0])), 1)
+    a = (float(o.state()["v"][0]) - 10.0) / 0.5
+    assert abs(a - _idm64(405.0, 10.0, 8.0)) < 1e-4
+    # A alone: free road
+    o = _run(scenario(net, [[0, 1]], dict(link=[0], cursor=[0], x=[490.0], v=[10.0])), 1)
+    a = (float(o.state()["v"][0]) - 10.0) / 0.5
+    assert abs(a - _idm64(0.0, 10.0, 0.0, has=False)) < 1e-5
+
+
+def test_arrival_at_the_end_of_the_last_link():
+    net = make_net([(0.0, 0.0), (500.0, 0.0), (1000.0, 0.0)], [(0, 1), (1, 2)], lanes=1)
+    o = _run(scenario(net, [[0, 1]], dict(link=[1], cursor=[1], x=[499.0], v=[10.0])), 1)
+    s, c = o.state(), o.counters()
+    assert s["status"][0] == S.ST_ARRIVED and s["arrive_step"][0] == 0
+    assert c["arrived"] == 1 and c["active"] == 0
+
+
+def test_merge_admits_one_per_step_by_rotating_rank():
+    # three equal approaches (links 0, 2, 3: the in-links of node 1 in id order, round-robin
+    # indices 0, 1, 2) reach the end of their links in the same step; one crosses into
+    # link 1, the others stop at the line: the winner is the approach whose rank
+    # (in_index - t) mod 3 is 0, i.e. in_index = t mod 3
+    xy = [(0.0, 0.0), (300.0, 0.0), (600.0, 0.0), (300.0, -300.0), (300.0, 300.0)]
+    net = make_net(xy, [(0, 1), (1, 2), (3, 1), (4, 1)], lanes=1)
+    seen = set()
+    for x0 in (250.0, 245.0, 240.0, 235.0, 230.0, 225.0):
+        st = dict(link=[0, 2, 3], x=[x0, x0, x0], v=[10.0, 10.0, 10.0])
+        o = _run(scenario(net, [[0, 1], [2, 1], [3, 1]], st), 0)
+        for _ in range(100):
+            t = o.counters()["t"]
+            o.step(1)
+            s = o.state()
+            crossed = np.flatnonzero(s["link"] == 1)
+            if len(crossed):
+                assert len(crossed) == 1
+                assert int(crossed[0]) == t % 3
+                seen.add(t % 3)
+                for j in range(3):
+                    if j != crossed[0]:
+                        assert s["x"][j] == 300.0 and s["v"][j] == 0.0
+                break
+        else:
+            raise AssertionError("no crossing")
+    assert len(seen) >= 2          # the start positions give crossings at different t mod 3
+
+
 # ---------------------------------------------------------------- intersections
 def test_red_light_holds_then_releases():
     # node 1 signalised, offset 0: the east-west approach is red for steps 0..59
