@@ -524,6 +524,28 @@ def test_merge_admits_one_per_step_by_rotating_rank():
     assert len(seen) >= 2          # the start positions give crossings at different t mod 3
 
 
+def test_transition_maps_the_lane_and_carries_the_overshoot():
+    # a vehicle in lane 1 of a 2-lane link crossing into a 1-lane link: x <- x - L,
+    # lane <- min(lane, lanes_next - 1), route cursor + 1
+    net = make_net([(0.0, 0.0), (500.0, 0.0), (1000.0, 0.0)], [(0, 1), (1, 2)], lanes=[2, 1])
+    o = _run(scenario(net, [[0, 1]], dict(link=[0], lane=[1], x=[498.0], v=[10.0])), 1)
+    s = o.state()
+    a = _idm64(0.0, 10.0, 0.0, has=False)
+    assert s["link"][0] == 1 and s["lane"][0] == 0 and s["cursor"][0] == 1
+    assert abs(float(s["x"][0]) - (498.0 + 10.0 * 0.5 + a * 0.125 - 500.0)) < 1e-4
+
+
+def test_red_light_is_a_standing_obstacle_at_the_line():
+    # alone 50 m before a red light: Eq. 7 behind a standing obstacle at the stop line
+    # (gap L - x), smaller than the free-road value
+    xy = [(0.0, 0.0), (500.0, 0.0), (1000.0, 0.0)]
+    net = make_net(xy, [(0, 1), (1, 2)], ctrl=[0, S.CTRL_SIGNAL, 0], lanes=1)
+    o = _run(scenario(net, [[0, 1]], dict(lane=[0], x=[450.0], v=[10.0])), 1)
+    a = (float(o.state()["v"][0]) - 10.0) / 0.5
+    want = min(_idm64(0.0, 10.0, 0.0, has=False), _idm64(50.0, 10.0, 0.0))
+    assert abs(a - want) < 1e-4 and want < 0.0
+
+
 # ---------------------------------------------------------------- intersections
 def test_red_light_holds_then_releases():
     # node 1 signalised, offset 0: the east-west approach is red for steps 0..59
