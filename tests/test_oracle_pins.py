@@ -546,6 +546,17 @@ def test_red_light_is_a_standing_obstacle_at_the_line():
     assert abs(a - want) < 1e-4 and want < 0.0
 
 
+@pytest.mark.parametrize("d,both", [(6.9, False), (7.1, True)])
+def test_simultaneous_change_conflict_distance(d, both):
+    # two changers into lane 1 from both sides, d metres apart: closer than vehicle length
+    # + s0 = 7 m only the lower id moves, farther both move
+    net = _corridor(lanes=3)
+    st = dict(lane=[0, 2, 0, 2, 1], x=[100.0, 100.0 + d, 125.0, 125.0 + d, 128.0],
+              v=[20.0, 20.0, 5.0, 5.0, 20.0])
+    o = _run(scenario(net, [[0, 1]] * 5, st), 1)
+    assert o.state()["lane_change"].tolist()[:2] == ([1, -1] if both else [1, 0])
+
+
 # ---------------------------------------------------------------- intersections
 def test_red_light_holds_then_releases():
     # node 1 signalised, offset 0: the east-west approach is red for steps 0..59
