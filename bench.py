@@ -217,6 +217,25 @@ def time_oracle(frac, steps, warmup, budget_s=None):
     return dict(value=vs / dt, steps=n, seconds=dt, veh_steps=vs, trips=m["demand"]["n_trips"])
 
 
+def time_oracle_routing(n_trips=100):
+    """The oracle's trip planning (one Dijkstra tree per distinct origin, canonical
+    routes) for the first n_trips trips of the metro demand on the full network:
+    trees per second on one core."""
+    import oracle
+    from paper_1807_01148_gb300 import scenarios as S
+    m = S.metro()
+    d = m["demand"]
+    m["demand"] = S._demand(d["origin"][:n_trips], d["dest"][:n_trips], d["depart_step"][:n_trips])
+    n_orig = int(len(np.unique(m["demand"]["origin"])))
+    o = oracle.OracleSim(m)
+    t0 = time.perf_counter()
+    o.route()
+    dt = time.perf_counter() - t0
+    return {"trees_per_s": n_orig / dt, "seconds": dt, "cores": 1,
+            "sample": f"{n_orig} origin trees (the first {n_trips} trips of the metro demand) on the full "
+                      f"225000-node network, single-threaded"}
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -532,7 +551,8 @@ def run_cuda(args):
                "sample": f"{r['trips']} trips ({args.sample_frac:.0%} of the metro demand) in the saturated "
                          f"snapshot recipe on the full network, random-walk routes; {r['steps']} steps, "
                          f"{r['seconds']:.1f} s single-threaded",
-               "cpu": lscpu_model()}
+               "cpu": lscpu_model(),
+               "routing": time_oracle_routing()}
     line = {
         "metric": METRIC, "value": tot_vs / secs, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -555,7 +575,9 @@ def run_cuda(args):
         "per_kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
         "per_kernel_alg_gbs": per_kernel_gbs,
         "lane_change_candidates_per_step": avg_cand,
-        "routing": {"seconds": route_s, "mode": "gpu sim_route" if args.workload == "metro" else "set_routes", "origins_trees": int(len(np.unique(m["demand"]["origin"]))),
+        "routing": {"seconds": route_s, "mode": "gpu sim_route" if args.workload == "metro" else "set_routes",
+                    "origins_trees": int(len(np.unique(m["demand"]["origin"]))),
+                    "trees_per_s": int(len(np.unique(m["demand"]["origin"]))) / route_s,
                     "trips": m["demand"]["n_trips"], "hops": int(off[-1])},
         "outputs": outputs,
         "equilibrium": equilibrium,
