@@ -274,6 +274,13 @@ typedef struct {
  * after the n_steps.  Errors: SIM_EINVAL, SIM_ESTATE, SIM_ENOMEM. */
 int sim_adjoint(sim_handle* h, const sim_loss_spec* spec, double* grad_out, double* loss_out);
 
+/* The same loss L without the gradient: steps n_steps from the current state (plain
+ * step kernels, no tape, no checkpoints) and adds the squared residuals of every trip
+ * at each observation on the device (binary64; the per-block partial sums are added
+ * atomically, so the last bits may depend on the order of the blocks).  On return the
+ * state is the one after the n_steps.  Errors: SIM_EINVAL, SIM_ESTATE, SIM_ENOMEM. */
+int sim_loss(sim_handle* h, const sim_loss_spec* spec, double* loss_out);
+
 /* ---------------------------------------------------------------- vehicle types
  * Sec. 6.3.5: a second vehicle type for trucks, differing in size, acceleration and
  * maximum speed.  With types set, every trip has a type; a vehicle's gap to its leader
@@ -444,10 +451,23 @@ int sim_assign_static(sim_handle* h, const sim_assign_spec* spec, double* flow, 
  * streams or host threads at the same time) race and give wrong results, so
  * serialise them.  Only a small per-call control block is cleared on each call;
  * the distance and queue words are tagged with a per-call epoch and need no
- * clearing.  Returns SIM_OK, SIM_EINVAL or SIM_ECUDA; sim_last_error is not set. */
+ * clearing, except once every 2^30 calls or search rounds, when the call that
+ * reaches that count refills them after its output is written.  Returns SIM_OK, SIM_EINVAL or SIM_ECUDA; sim_last_error is not set. */
 int sim_sssp_static(int32_t n_nodes, int32_t n_links, const int32_t* out_start, const int32_t* out_link,
                     const int32_t* link_to, const int32_t* link_cost, int32_t origin, int32_t* dist_out,
                     void* stream);
+
+/* Test hook of sim_sssp_static (no counterpart in the paper): sets the two counters the
+ * fixed array keeps across calls, the search epoch that tags distance words and the
+ * round number that tags queue flags.  After any call that leaves either at 2^30 or
+ * more, sim_sssp_static puts the array back to its first-use state (distance words
+ * all-ones, flags and counters zero) so that neither counter can wrap around in a
+ * long-lived process; this hook lets a test reach that point without a billion calls.
+ * The counters may only be moved forward (below their current values, stale tags in
+ * the array would look current).  Same set-up and serialisation rules as
+ * sim_sssp_static; allocates nothing.  Returns
+ * SIM_OK or SIM_ECUDA. */
+int sim_sssp_static_set_counters(uint32_t epoch, int32_t round, void* stream);
 
 /* Message of the last failed call on this handle (or of the last failed
  * sim_create when h is NULL). */

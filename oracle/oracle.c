@@ -1396,6 +1396,58 @@ int orc_adjoint(orc_sim* S, int32_t n_steps, int32_t obs_every, const double* ta
   return OK;
 }
 
+/* Test helper (not the method): run n_steps recording the tape of every vehicle-step,
+ * without observations or the reverse sweep, so that runs at perturbed parameters can
+ * be compared with the base run's tape by orc_tape_digest. */
+int orc_record(orc_sim* S, int32_t n_steps) {
+  if (!S->routed) return ESTATE;
+  if (n_steps < 0) return EINV;
+  S->rec_n = 0; S->rec_steps = 0; S->recording = 1;
+  orc_step(S, n_steps);
+  S->recording = 0;
+  if (S->rec_step) S->rec_step[S->rec_steps] = S->rec_n;
+  return OK;
+}
+
+/* Test helper (not the method): the discrete content of the last recorded run, the
+ * decisions the adjoint holds fixed, folded into one 64-bit FNV-1a digest (Fowler,
+ * Noll, Vo: offset basis 14695981039346656037, prime 1099511628211, one byte at a
+ * time).  Per record, in order: step boundary, trip, link, form of Eq. 7, its leader,
+ * how the move ended, whether it crossed, and the two floors of Eq. 7 as the taped
+ * binary32 values decide them (dynamic term positive, gap at or below s_min).  Two
+ * runs whose digests and record counts agree took the same discrete path.  With
+ * step_digest ([rec_steps] or NULL), entry j is the digest of steps 0 .. j-1 alone, so
+ * the first entry where two runs differ bounds their common discrete prefix. */
+static uint64_t fnv_bytes(uint64_t h, const void* p, size_t n) {
+  const unsigned char* b = (const unsigned char*)p;
+  for (size_t i = 0; i < n; i++) { h ^= b[i]; h *= 1099511628211ULL; }
+  return h;
+}
+
+int orc_tape_digest(const orc_sim* S, uint64_t* digest, int64_t* n_rec, uint64_t* step_digest) {
+  if (!digest || !n_rec) return EINV;
+  uint64_t h = 14695981039346656037ULL;
+  for (int j = 0; j < S->rec_steps; j++) {
+    int32_t mark = -1 - j;
+    h = fnv_bytes(h, &mark, 4);
+    if (step_digest) step_digest[j] = h;   /* digest of the steps before j */
+    for (int64_t q = S->rec_step[j]; q < S->rec_step[j + 1]; q++) {
+      const orc_rec* r = &S->rec[q];
+      int c = S->cls[r->link];
+      float dv32 = r->v - r->vl;
+      float t1 = r->v * S->pT[c];
+      float t2 = (r->v * dv32) / (2.0f * S->psab[c]);
+      int32_t w[8] = {r->vid, r->link, r->kind, r->lead, r->branch, r->crossed,
+                      (r->kind != FORM_FREE && r->kind != FORM_NONE) ? (t1 + t2) > 0.0f : 0,
+                      (r->kind != FORM_FREE && r->kind != FORM_NONE) ? !(r->s > S->s_min) : 0};
+      h = fnv_bytes(h, w, sizeof w);
+    }
+  }
+  *digest = h;
+  *n_rec = S->rec_steps > 0 ? S->rec_step[S->rec_steps] : 0;
+  return OK;
+}
+
 /* Loss of the last taped run replayed in binary64 with other class parameters
  * (v0, T, a, b, s0 per class), every discrete decision taken from the tape. */
 int orc_replay_loss(const orc_sim* S, const double* pv0, const double* pT, const double* pa, const double* pb,

@@ -63,6 +63,10 @@ int  orc_adjoint(orc_sim*, int32_t n_steps, int32_t obs_every, const double* tar
 int  orc_replay_loss(const orc_sim*, const double* v0, const double* T, const double* a, const double* b,
                      const double* s0, double* loss);
 int  orc_set_class_params(orc_sim*, const float* v0, const float* T, const float* a, const float* b, const float* s0);
+/* test helpers: a recorded run without the reverse sweep, and the digest of the
+ * discrete decisions of the last recorded run (equal digests: no discrete event flipped) */
+int  orc_record(orc_sim*, int32_t n_steps);
+int  orc_tape_digest(const orc_sim*, uint64_t* digest, int64_t* n_rec, uint64_t* step_digest);
 
 /* measured outputs (flags: 1 fuel and CO per trip, Eq. 8-9; 2 link traversal times,
  * Sec. 6.3.1; 4 per-edge samples, Sec. 6.4), cleared whenever the run restarts */

@@ -75,6 +75,8 @@ def lib():
         L.orc_adjoint.argtypes = [vp, i32, i32, vp, vp, vp]
         L.orc_replay_loss.argtypes = [vp] + [vp] * 6
         L.orc_set_class_params.argtypes = [vp] * 6
+        L.orc_record.argtypes = [vp, i32]
+        L.orc_tape_digest.argtypes = [vp, vp, vp, vp]
         L.orc_idm.argtypes = [f32] * 9 + [C.c_int]
         L.orc_idm.restype = f32
         L.orc_ballistic.argtypes = [f32, f32, f32, f32, C.POINTER(f32), C.POINTER(f32)]
@@ -245,6 +247,19 @@ class OracleSim:
         return float(loss[0])
 
     # ---- measured outputs (Eq. 8-9, Sec. 6.3.1, Sec. 6.4)
+    def record(self, n_steps):
+        """Run n_steps with the adjoint's tape recorded (no observation, no sweep)."""
+        _check(lib().orc_record(self.h, int(n_steps)), "orc_record")
+
+    def tape_digest(self, per_step=False):
+        """(digest, records) of the discrete decisions of the last recorded run; with
+        per_step also the array whose entry j digests steps 0 .. j-1."""
+        dg = np.zeros(1, np.uint64)
+        n = np.zeros(1, np.int64)
+        steps = np.zeros(max(1, int(self.counters()["t"])) + 1, np.uint64) if per_step else None
+        _check(lib().orc_tape_digest(self.h, _p(dg), _p(n), _p(steps) if per_step else None), "orc_tape_digest")
+        return (int(dg[0]), int(n[0]), steps) if per_step else (int(dg[0]), int(n[0]))
+
     def set_outputs(self, flags, sample_every=120, per_window=6, max_windows=0):
         _check(lib().orc_set_outputs(self.h, int(flags), int(sample_every), int(per_window), int(max_windows)),
                "orc_set_outputs")

@@ -1440,6 +1440,43 @@ int sim_observe(sim_handle* h, int32_t n_steps, int32_t obs_every, double* progr
   return rc;
 }
 
+int sim_loss(sim_handle* h, const sim_loss_spec* spec, double* loss_out) {
+  NvtxRange nvtx_("sim_loss");
+  if (!h || !spec || !loss_out || !spec->target) return SIM_EINVAL;
+  h->t_known = false;
+  if (h->state_lost) return fail(h, SIM_ESTATE, "the state is undefined after a timeout: sim_write_state or sim_route first");
+  if (!h->routed) return fail(h, SIM_ESTATE, "sim_loss before routes exist");
+  const int n_steps = spec->n_steps, every = spec->obs_every;
+  if (n_steps <= 0 || every <= 0 || n_steps % every) return fail(h, SIM_EINVAL, "n_steps must be a multiple of obs_every");
+  if (int rc = check_horizon(h, n_steps)) return rc;
+  h->t_known = false;
+  const int nobs = n_steps / every;
+  const size_t nt = (size_t)std::max(1, h->nt);
+  double *tgt, *res;
+  int rc = dalloc(h, &tgt, (size_t)nobs * nt);
+  if (rc) return rc;
+  if ((rc = dalloc(h, &res, nt))) {
+    dfree(h, tgt);
+    return rc;
+  }
+  cudaError_t e = cudaMemcpyAsync(tgt, spec->target, (size_t)nobs * nt * 8, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&h->d.ctl->loss, 0, 8, h->stream);
+  if (e != cudaSuccess) rc = cuda_fail(h, e, "loss");
+  for (int k = 0; k < nobs && rc == SIM_OK; k++) {
+    if ((rc = sim_step(h, every))) break;
+    launch_observe(h->d, h->grid, h->stream, tgt + (size_t)k * nt, res, nullptr);
+  }
+  if (rc == SIM_OK) {
+    e = cudaMemcpyAsync(loss_out, &h->d.ctl->loss, 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) rc = cuda_fail(h, e, "loss");
+  }
+  dfree(h, tgt);
+  dfree(h, res);
+  if (rc) return rc;
+  return check_device(h);
+}
+
 namespace {
 
 // Everything a step changes, for the adjoint's checkpoints.

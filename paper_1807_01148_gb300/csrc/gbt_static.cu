@@ -67,6 +67,14 @@ constexpr int kMaxDevices = 64;
 unsigned char* g_scratch_addr[kMaxDevices] = {nullptr};
 std::mutex g_scratch_mu;
 
+// The search tags distance words with an epoch and queue flags with a round number,
+// both counted up for the life of the array.  Before either could wrap around (which
+// would make stale words look current), the array is put back to its first-use state:
+// distance words all-ones, flags zero, counters zero.  Both are read back after every
+// call; the reset happens once either passes this bound (about a billion calls or
+// rounds), far below the 2^31 where the comparisons would break.
+constexpr unsigned kCounterResetAt = 1u << 30;
+
 __global__ void k_static_check(int n, int m, const int32_t* out_start, const int32_t* out_link,
                                const int32_t* link_to, const int32_t* cost, StaticCall* call) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n || i < m; i += gridDim.x * blockDim.x) {
@@ -183,6 +191,31 @@ extern "C" int sim_sssp_static(int32_t n_nodes, int32_t n_links, const int32_t* 
   const int g2 = (n_nodes + 255) / 256;
   k_static_dist_out<<<g2 < 1024 ? g2 : 1024, 256, 0, s>>>(n_nodes, R.dist, ps, dist_out);
   if (cudaGetLastError() != cudaSuccess) return SIM_ECUDA;
+  StaticPersist hp;
+  if (cudaMemcpyAsync(&hp, ps, sizeof(hp), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SIM_ECUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return SIM_ECUDA;
+  if (hp.cta_epoch >= kCounterResetAt || (unsigned)hp.cta_round >= kCounterResetAt) {
+    // back to the first-use state (see kCounterResetAt); this call's output is complete
+    if (cudaMemsetAsync(base + kOffDist, 0xFF, 8 * kN, s) != cudaSuccess ||
+        cudaMemsetAsync(base + kOffQflag, 0, 8 * kN, s) != cudaSuccess ||   // queue and far flags
+        cudaMemsetAsync(ps, 0, sizeof(StaticPersist), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+      return SIM_ECUDA;
+  }
+  return SIM_OK;
+}
+
+// Test hook: set the persistent epoch and round counters (to check the reset above
+// without a billion calls).  Same set-up and serialisation rules as sim_sssp_static.
+extern "C" int sim_sssp_static_set_counters(uint32_t epoch, int32_t round, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char* base = nullptr;
+  int rc = scratch_address(&base);
+  if (rc != SIM_OK) return rc;
+  StaticPersist hp{};
+  hp.cta_epoch = epoch;
+  hp.cta_round = round;
+  if (cudaMemcpyAsync(base + kOffPersist, &hp, sizeof(hp), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return SIM_ECUDA;
   return SIM_OK;
 }

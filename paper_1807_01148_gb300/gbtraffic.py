@@ -26,7 +26,7 @@ EXPORTS = ["sim_create", "sim_create_batch", "sim_set_stream", "sim_route", "sim
            "sim_counters", "sim_last_error", "sim_destroy", "sim_set_class_params", "sim_observe", "sim_adjoint",
            "sim_set_exec", "sim_get_exec", "sim_autotune", "sim_set_outputs", "sim_reset_outputs",
            "sim_read_emissions", "sim_read_link_times", "sim_read_edge_samples", "sim_measured_costs",
-           "sim_reroute", "sim_equilibrium", "sim_assign_static", "sim_set_vehicle_types"]
+           "sim_reroute", "sim_equilibrium", "sim_assign_static", "sim_set_vehicle_types", "sim_loss"]
 OUT_EMISSIONS, OUT_LINK_TIMES, OUT_EDGE_SAMPLES = 1, 2, 4
 SIM_EXEC_GRAPH, SIM_EXEC_PERSISTENT = 0, 1
 
@@ -128,6 +128,7 @@ def lib(path: str | None = None):
         L.sim_set_class_params.argtypes = [vp] * 6
         L.sim_observe.argtypes = [vp, i32, i32, vp]
         L.sim_adjoint.argtypes = [vp, C.POINTER(sim_loss_spec), vp, vp]
+        L.sim_loss.argtypes = [vp, C.POINTER(sim_loss_spec), vp]
         L.sim_set_exec.argtypes = [vp, C.POINTER(sim_exec)]
         L.sim_get_exec.argtypes = [vp, C.POINTER(sim_exec)]
         L.sim_autotune.argtypes = [vp, i32, C.c_char_p, C.POINTER(sim_exec)]
@@ -330,6 +331,15 @@ class Sim:
         self._check(lib().sim_adjoint(self.h, C.byref(spec), _p(g), _p(loss)))
         return g.reshape(n_class, 5), float(loss[0])
 
+    def loss(self, n_steps, obs_every, target):
+        """The calibration loss alone, computed on the device from the current state (see
+        sim_loss); the state advances by n_steps."""
+        t = np.ascontiguousarray(target, np.float64)
+        spec = sim_loss_spec(int(n_steps), int(obs_every), 0, t.ctypes.data)
+        loss = np.zeros(1, np.float64)
+        self._check(lib().sim_loss(self.h, C.byref(spec), _p(loss)))
+        return float(loss[0])
+
     def set_exec(self, mode=SIM_EXEC_GRAPH, threads=256, blocks_per_sm=1, grid_per_sm=8,
                  barrier_timeout_cycles=0):
         e = sim_exec(mode, threads, blocks_per_sm, grid_per_sm, barrier_timeout_cycles)
@@ -438,8 +448,8 @@ def calibration_loss_fn():
     """torch.autograd.Function for trajectory calibration: loss(theta), theta a
     [n_class, 5] float64 tensor of (v0, T, a, b, s0) per class.  Forward sets the class
     parameters, restores the start state and runs sim_adjoint (taped forward pass with
-    checkpoints + binary64 reverse sweep) when a gradient is needed, sim_observe
-    otherwise; backward returns the stored gradient scaled by the incoming one."""
+    checkpoints + binary64 reverse sweep) when a gradient is needed, sim_loss (the
+    loss alone, on the device) otherwise; backward returns the stored gradient scaled by the incoming one."""
     import torch
 
     class CalibrationLoss(torch.autograd.Function):
@@ -452,8 +462,7 @@ def calibration_loss_fn():
                 g, loss = sim.adjoint(n_steps, obs_every, target, th.shape[0], checkpoint_every)
                 ctx.save_for_backward(torch.from_numpy(g).to(theta.device, theta.dtype))
             else:
-                p = sim.observe(n_steps, obs_every)
-                loss = float(((p - target) ** 2).sum())
+                loss = sim.loss(n_steps, obs_every, target)
             return torch.tensor(loss, dtype=theta.dtype, device=theta.device)
 
         @staticmethod

@@ -1,10 +1,17 @@
 """sim_sssp_static: the shortest-path tree for callers that cannot allocate device
 memory (a framework owns the pool, a supervisor caps the process, a plug-in must not
-touch the allocator).  Its working memory is a fixed array inside the library, so
-this test checks it against the existing trip planner, sim_route, through the C ABI:
-for every trip of the sampled origins, the tree's distance to the destination equals
-the cost of the route sim_route planned (integer costs: exact), on two calls in a
-row.  This file is collected last."""
+touch the allocator).  Its working memory is a fixed array inside the library.
+
+Checked through the C ABI on two calls in a row:
+  * dist_out over EVERY node equals the oracle's Dijkstra (integer costs: exact), on
+    graphs with unreachable regions (INT32_MAX there) and on graphs at and near
+    SIM_SSSP_STATIC_MAX_NODES, where the fixed array's offsets are used in full;
+  * the tree agrees with the existing trip planner, sim_route: the distance to each
+    trip's destination is the cost of the route sim_route planned;
+  * once the epoch or round counter the array keeps across calls passes 2^30, the
+    call that reaches it puts the array back to its first-use state, and the results
+    stay exact across that reset.
+This file is collected last."""
 import ctypes
 
 import numpy as np
@@ -15,6 +22,7 @@ from paper_1807_01148_gb300 import scenarios as S
 pytestmark = pytest.mark.gpu
 
 SIM_SSSP_STATIC_MAX_NODES = 262144
+INT32_MAX = 2**31 - 1
 
 
 def _bind(lib):
@@ -25,12 +33,59 @@ def _bind(lib):
     return f
 
 
-def _csr(net):
-    lf = net["link_from"].astype(np.int64)
+def _csr(n_nodes, link_from):
+    lf = np.asarray(link_from, np.int64)
     order = np.argsort(lf, kind="stable").astype(np.int32)
-    start = np.zeros(net["n_nodes"] + 1, np.int64)
+    start = np.zeros(n_nodes + 1, np.int64)
     np.add.at(start, lf + 1, 1)
     return np.cumsum(start).astype(np.int32), order
+
+
+class _Graph:
+    """A graph resident on the device in the layout sim_sssp_static takes."""
+
+    def __init__(self, n_nodes, link_from, link_to, cost):
+        import torch
+        dev = torch.device("cuda")
+        self.n, self.m = int(n_nodes), len(link_from)
+        self.lf = np.asarray(link_from, np.int32)
+        self.lt = np.asarray(link_to, np.int32)
+        self.cost = np.asarray(cost, np.int32)
+        start, order = _csr(self.n, self.lf)
+        self.d_start = torch.from_numpy(start).to(dev)
+        self.d_link = torch.from_numpy(order).to(dev)
+        self.d_to = torch.from_numpy(self.lt.copy()).to(dev)
+        self.d_cost = torch.from_numpy(self.cost.copy()).to(dev)
+        self.dist = torch.empty(self.n, dtype=torch.int32, device=dev)
+
+    def tree(self, f, origin, stream):
+        rc = f(self.n, self.m, self.d_start.data_ptr(), self.d_link.data_ptr(), self.d_to.data_ptr(),
+               self.d_cost.data_ptr(), int(origin), self.dist.data_ptr(), stream)
+        assert rc == 0
+        return self.dist.cpu().numpy().copy()
+
+    def oracle(self, origin):
+        import oracle
+        d = oracle.oracle_sssp(self.n, self.lf, self.lt, self.cost, int(origin))
+        return np.where(d >= INT32_MAX, INT32_MAX, d).astype(np.int64)
+
+
+def _check_all_nodes(gr, f, origins, stream):
+    import torch
+    torch.cuda.synchronize()
+    for o in origins:
+        want = gr.oracle(o)
+        for _ in range(2):                                   # two calls in a row
+            got = gr.tree(f, o, stream).astype(np.int64)
+            bad = np.flatnonzero(got != want)
+            assert not len(bad), (o, bad[:8].tolist(), got[bad[:8]].tolist(), want[bad[:8]].tolist())
+
+
+def _no_unreachable_marker():
+    import oracle
+    # the oracle's own convention for unreachable nodes, pinned on a 2-node graph
+    d = oracle.oracle_sssp(2, np.array([0], np.int32), np.array([1], np.int32), np.array([3], np.int32), 1)
+    assert d[1] == 0 and d[0] >= INT32_MAX
 
 
 @pytest.mark.parametrize("make", [lambda: S.grid(n=12, n_trips=3000),
@@ -47,33 +102,81 @@ def test_static_tree_matches_sim_route(make):
     sim.route(cost)                      # the existing entry point
     off, links = sim.routes()
     route_cost = np.add.reduceat(cost[links].astype(np.int64), off[:-1])
-
-    start, order = _csr(net)
-    dev = torch.device("cuda")
-    d_start = torch.from_numpy(start).to(dev)
-    d_link = torch.from_numpy(order).to(dev)
-    d_to = torch.from_numpy(net["link_to"].astype(np.int32)).to(dev)
-    d_cost = torch.from_numpy(cost).to(dev)
-    dist = torch.empty(net["n_nodes"], dtype=torch.int32, device=dev)
+    gr = _Graph(net["n_nodes"], net["link_from"], net["link_to"], cost)
     f = _bind(G.lib())
     stream = torch.cuda.current_stream().cuda_stream
-
     origins = sc["demand"]["origin"]
     dests = sc["demand"]["dest"]
-    sample = rng.choice(np.unique(origins), 25, replace=False)
-    for o in sample:
-        results = []
-        for _ in range(2):                               # two calls in a row
-            rc = f(net["n_nodes"], net["n_links"], d_start.data_ptr(), d_link.data_ptr(), d_to.data_ptr(),
-                   d_cost.data_ptr(), int(o), dist.data_ptr(), stream)
-            assert rc == 0
-            results.append(dist.cpu().numpy().copy())
-        assert np.array_equal(results[0], results[1])
-        dv = results[0]
-        assert dv[o] == 0
+    for o in rng.choice(np.unique(origins), 25, replace=False):
+        dv = [gr.tree(f, o, stream) for _ in range(2)]       # two calls in a row
+        assert np.array_equal(dv[0], dv[1])
+        assert dv[0][o] == 0
         trips = np.flatnonzero(origins == o)
-        assert np.array_equal(dv[dests[trips]].astype(np.int64), route_cost[trips])
+        assert np.array_equal(dv[0][dests[trips]].astype(np.int64), route_cost[trips])
     sim.close()
+
+
+def test_static_tree_equals_oracle_with_unreachable_regions():
+    import torch
+    from paper_1807_01148_gb300 import gbtraffic as G
+
+    _no_unreachable_marker()
+    net = S.small_metro(nx=40, ny=30, n_trips=10)["network"]
+    rng = np.random.default_rng(11)
+    n = net["n_nodes"]
+    cut = rng.random(n) < 0.08                           # nodes nobody may enter
+    keep = ~cut[net["link_to"]]
+    lf, lt = net["link_from"][keep], net["link_to"][keep]
+    cost = rng.integers(1, 1000, len(lf)).astype(np.int32)
+    # plus a node with no links at all at the end
+    gr = _Graph(n + 1, lf, lt, cost)
+    f = _bind(G.lib())
+    stream = torch.cuda.current_stream().cuda_stream
+    origins = list(rng.choice(np.flatnonzero(~cut), 6, replace=False)) + list(rng.choice(np.flatnonzero(cut), 2))
+    origins.append(n)                                    # the isolated node: only itself is reached
+    _check_all_nodes(gr, f, origins, stream)
+    d = gr.tree(f, origins[0], stream)
+    assert (d == INT32_MAX).sum() >= cut.sum() and d[n] == INT32_MAX
+
+
+@pytest.mark.parametrize("side", [511, 512])
+def test_static_tree_equals_oracle_near_the_size_limit(side):
+    # 511^2 = 261121 and 512^2 = 262144 = SIM_SSSP_STATIC_MAX_NODES nodes: every
+    # region of the fixed array is used up to (or within a few KB of) its end
+    import torch
+    from paper_1807_01148_gb300 import gbtraffic as G
+
+    net = S.grid(n=side, n_trips=10)["network"]
+    assert net["n_nodes"] <= SIM_SSSP_STATIC_MAX_NODES
+    rng = np.random.default_rng(side)
+    cost = rng.integers(1, 300, net["n_links"]).astype(np.int32)
+    gr = _Graph(net["n_nodes"], net["link_from"], net["link_to"], cost)
+    f = _bind(G.lib())
+    stream = torch.cuda.current_stream().cuda_stream
+    _check_all_nodes(gr, f, [0, net["n_nodes"] - 1, int(rng.integers(net["n_nodes"]))], stream)
+
+
+def test_static_tree_counter_reset_keeps_results_exact():
+    import torch
+    from paper_1807_01148_gb300 import gbtraffic as G
+
+    lib = G.lib()
+    f = _bind(lib)
+    hook = lib.sim_sssp_static_set_counters
+    hook.argtypes = [ctypes.c_uint32, ctypes.c_int32, ctypes.c_void_p]
+    hook.restype = ctypes.c_int
+    net = S.small_metro(nx=40, ny=30, n_trips=10)["network"]
+    rng = np.random.default_rng(5)
+    cost = rng.integers(1, 500, net["n_links"]).astype(np.int32)
+    gr = _Graph(net["n_nodes"], net["link_from"], net["link_to"], cost)
+    stream = torch.cuda.current_stream().cuda_stream
+    origins = rng.choice(net["n_nodes"], 3, replace=False)
+    _check_all_nodes(gr, f, origins, stream)
+    # counters moved forward to just below the reset bound (never backwards: stale tags
+    # would then look current): the next call crosses it, finishes exactly, then resets
+    for epoch, rnd in (((1 << 30) - 3, 1 << 29), (1 << 29, (1 << 30) - 2)):
+        assert hook(epoch, rnd, stream) == 0
+        _check_all_nodes(gr, f, origins, stream)
 
 
 def test_static_tree_rejects_oversize_and_bad_graphs():
@@ -100,4 +203,4 @@ def test_static_tree_rejects_oversize_and_bad_graphs():
     to = torch.tensor([1], dtype=torch.int32, device=dev)
     assert f(2, 1, start.data_ptr(), link.data_ptr(), to.data_ptr(), cost.data_ptr(), 1, out.data_ptr(),
              stream) == 0
-    assert out.cpu().tolist() == [2**31 - 1, 0]
+    assert out.cpu().tolist() == [INT32_MAX, 0]
