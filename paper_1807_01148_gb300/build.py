@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgbtraffic.so")
-SOURCES = ["gbt_api.cu", "gbt_step.cu", "gbt_route.cu", "gbt_static.cu", "gbt_adjoint.cu", "gbt_outputs.cu", "gbt_assign.cu"]
+SOURCES = ["gbt_api.cu", "gbt_step.cu", "gbt_fused.cu", "gbt_route.cu", "gbt_static.cu", "gbt_adjoint.cu", "gbt_outputs.cu", "gbt_assign.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC,-ffp-contract=off,-fno-fast-math",
            "-Xptxas", "-O3", f"-I{INCLUDE}", f"-I{CSRC}"]

@@ -51,8 +51,8 @@ void launch_fw_final_time(const double* t0, const double* x, const double* cap, 
                           int n, cudaStream_t s);
 void launch_compact_routes(const int32_t* roff, const int32_t* rlen, const int32_t* src, const int32_t* new_off,
                            int32_t* dst, int n, cudaStream_t s);
-int own_tiled_blocks_per_sm(bool types);
-int decide_blocks_per_sm(bool types);
+void chunk_setup(int blocks_per_sm[4]);
+size_t chunk_table_size(int n_trips);
 int persistent_max_blocks_per_sm(int threads);
 cudaError_t launch_persistent(const Dev& d, GridSync* gs, int blocks, int threads, int n_steps, long long limit,
                               cudaStream_t s);
@@ -328,9 +328,11 @@ int create_from_flat(Flat& F, sim_handle** out) {
   if (h->sm_count <= 0) h->sm_count = 1;
   h->grid = h->sm_count * 8;
   h->d.wait_limit = kDefaultWaitCycles;
-  for (int ty = 0; ty < 2; ty++) {
-    h->d.own_grid[ty] = std::max(1, own_tiled_blocks_per_sm(ty != 0)) * h->sm_count;
-    h->d.dec_grid[ty] = std::max(1, decide_blocks_per_sm(ty != 0)) * h->sm_count;
+  {
+    // one resident wave of chunk-taking blocks per variant of the chunk kernel
+    int bps[4];
+    chunk_setup(bps);
+    for (int v = 0; v < 4; v++) h->d.chunk_grid[v] = std::max(1, bps[v]) * h->sm_count;
   }
 
   // in-links of every node in ascending link id -> round-robin index, in-degree
@@ -422,9 +424,11 @@ int create_from_flat(Flat& F, sim_handle** out) {
     d.n_nodes = F.nn;
     d.n_lanes = nlan;
     d.n_trips = F.nt;
+    d.n_cls = F.ncls;
     d.dt = P.dt;
     d.hdt2 = (0.5f * P.dt) * P.dt;
     d.vlen = P.veh_len;
+    d.vlen_max = P.veh_len;
     d.s_min = P.s_min;
     d.zone = 2.0f * P.veh_len;
     d.mp = P.mobil_p;
@@ -465,16 +469,28 @@ int create_from_flat(Flat& F, sim_handle** out) {
     TRY(dalloc(h, &d.tvid, nt));
     TRY(dalloc(h, &d.tsrc, nt));
     TRY(dalloc(h, &d.tg, ntp));
-    TRY(dalloc(h, &d.a_own, nt));
+    TRY(dalloc(h, &d.a_own, ntp));
     TRY(dalloc(h, &d.xo, nt));
     TRY(dalloc(h, &d.at, nt));
     TRY(dalloc(h, &d.intent, nt));
-    TRY(dalloc(h, &d.flags, nt));
+    TRY(dalloc(h, &d.flags, ntp));
     TRY(dalloc(h, &d.cnt, (size_t)nlan));
-    TRY(dalloc(h, &d.lane_start, (size_t)nlan + 1));
+    // 8 spare entries: the chunk kernel stages lane starts in copies rounded up to 4
+    TRY(dalloc(h, &d.lane_start, (size_t)nlan + 8));
     TRY(dalloc(h, &d.bsum, (size_t)scan_blocks(nlan) + 1));
     TRY(dalloc(h, &d.best, (size_t)nlan));
     TRY(dalloc(h, &d.rear, (size_t)nlan));
+    TRY(dalloc(h, &d.fr, (size_t)nlan));
+    TRY(dalloc(h, &d.cr, (size_t)nlan));
+    TRY(dalloc(h, &d.chunks, chunk_table_size(F.nt)));
+    {
+      std::vector<int32_t> ll((size_t)nlan);
+      for (int e = 0; e < F.nl; e++)
+        for (int l = 0; l < F.lanes[e]; l++) ll[(size_t)h->lane_base[e] + l] = e;
+      int32_t* dll;
+      TRY(upload(h, &dll, ll.data(), ll.size()));
+      d.lane_link = dll;
+    }
     TRY(dalloc(h, &d.elig, nt));
     TRY(dalloc(h, &d.holder, (size_t)F.nn));
     TRY(dalloc(h, &d.acq, (size_t)F.nn));
@@ -1387,6 +1403,7 @@ int sim_set_vehicle_types(sim_handle* h, int32_t n_types, const sim_vehicle_type
   d.cls_ty = nullptr;
   d.vty_len = d.vty_vmax = nullptr;
   d.n_vty = 0;
+  d.vlen_max = d.vlen;
   h->vty_len.clear();
   h->vty_ascale.clear();
   h->vty_vmax.clear();
@@ -1412,6 +1429,7 @@ int sim_set_vehicle_types(sim_handle* h, int32_t n_types, const sim_vehicle_type
   d.vty_len = vl;
   d.vty_vmax = vm;
   d.n_vty = n_types;
+  d.vlen_max = *std::max_element(h->vty_len.begin(), h->vty_len.end());
   return upload_type_params(h);
 }
 

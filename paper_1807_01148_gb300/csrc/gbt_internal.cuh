@@ -73,6 +73,30 @@ struct __align__(16) RearRec {
   uint32_t tag;
 };
 
+// Front (last sorted position) of a lane, written by the occupancy rebuild for every
+// occupied lane: what the lane-front kernel needs of it.
+struct __align__(16) FrontRec {
+  float x, v;
+  int32_t vid, nxt, cur;
+  int32_t pad[3];
+};
+
+// State after crossing of a lane front that bids for admission (written by the lane-front
+// kernel for bidding fronts only; used when the bid wins): position on the next link,
+// speed, target lane id, route cursor, the link after, movement class, lane.
+struct __align__(16) CrossRec {
+  float nx, nv;
+  int32_t gt, ncur, nnxt;
+  uint8_t nmv, m, pad0, pad1;
+  int32_t pad[2];
+};
+
+// A chunk of the fused step kernel: sorted positions [c0, c1) (whole links), the links
+// of its first and last vehicle and the lane ids [g_lo, g_hi) of those links.
+struct __align__(16) ChunkInfo {
+  int32_t c0, c1, e_lo, e_hi, g_lo, g_hi, pad0, pad1;
+};
+
 struct Ctl {
   long long t;
   int nA;          // slots filled in the unsorted buffer A
@@ -92,6 +116,7 @@ struct Ctl {
   alignas(128) int n_ins;
   int n_arr;
   int n_elig;      // lane-change candidates listed this step
+  int chunk_next;  // next chunk of the fused step kernel to take
 };
 
 // Forms of Eq. 7 an acceleration can come from (adjoint tape).
@@ -127,7 +152,7 @@ struct Dev {
   const float* cls_b;            // comfortable deceleration b per class (adjoint)
   const uint8_t* cls_v0_param;   // 1 when the class sets v0 (else v0 = link speed limit)
   const float* tau;      // mandatory-switch table [256]
-  int n_links, n_nodes, n_lanes, n_trips;
+  int n_links, n_nodes, n_lanes, n_trips, n_cls;
   // parameters
   float dt, hdt2, vlen, s_min, zone, mp, mathr, mbsafe, mbias, lam, stop_acq;
   int dt_ds, loop;
@@ -159,6 +184,10 @@ struct Dev {
   int8_t* intent;
   uint8_t* flags;
   RearRec* rear;              // per lane: rearmost vehicle (current epoch only)
+  FrontRec* fr;               // per lane: front vehicle (occupied lanes of this step only)
+  const int32_t* lane_link;   // per lane: its link
+  CrossRec* cr;               // per lane: the bidding front's state after crossing
+  ChunkInfo* chunks;          // chunks of the fused step kernel (this step's)
   int32_t* elig;              // sorted positions of this step's lane-change candidates
   TapeRec* tape;              // adjoint tape of the current segment (nullptr: not taping)
   TapeForm* tform;            // lane-change forms of the current step (taping only)
@@ -185,6 +214,7 @@ struct Dev {
   const ClassPar* cls_ty;          // [class * n_vty + type]
   const float* vty_len;
   const float* vty_vmax;
+  float vlen_max;                  // longest vehicle length (vlen without types)
   int n_vty;
   // departure queues
   const int32_t* qlinks;
@@ -193,9 +223,8 @@ struct Dev {
   int32_t* q_head;
   const int32_t* q_items;
   Ctl* ctl;
-  int own_grid[2];                 // blocks of the tiled own-lane kernel (plain, vehicle types)
-  int dec_grid[2];                 // blocks of the decision kernel (plain, vehicle types)
-  long long wait_limit;            // SM cycles a tile wait of the own-lane kernel may take
+  int chunk_grid[4];               // blocks of the chunk kernel (plain, outputs, types, both)
+  long long wait_limit;            // SM cycles a staging wait of the chunk kernel may take
 };
 
 // Trip-planning work description (one shortest-path tree per distinct origin).
@@ -235,7 +264,7 @@ struct RouteDev {
 void launch_route(const RouteDev& R, int n_cta, cudaStream_t s);
 
 // kernels of one step, in launch order
-enum { kKScanSum, kKScanFin, kKScatter, kKRank, kKOwn, kKDecide, kKMoveInsert, kKFinish, kNumKernels };
+enum { kKScanSum, kKScanFin, kKScatter, kKRank, kKFront, kKChunk, kKFinish, kNumKernels };
 extern const char* const kKernelNames[kNumKernels];
 
 constexpr uint8_t kFlagFront = 1, kFlagHolder = 2, kFlagCand = 4;

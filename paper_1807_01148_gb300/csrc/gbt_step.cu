@@ -14,33 +14,9 @@
 // by earlier kernels of the same step) and writes the state at t+1, so the result
 // does not depend on thread scheduling; ties are broken by vehicle id or by the
 // rotating round-robin rank.
-#include "gbt_internal.cuh"
+#include "gbt_stepdev.cuh"
 
 namespace gbt {
-
-#define GRID_STRIDE(i, n) for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
-
-// The step kernels are launched with programmatic stream serialization: a kernel's
-// launch is prepared while the one before it in the stream runs, and the kernel waits
-// here, before its first read, until that grid has completed and its writes are
-// visible.  (Without such a launch the wait returns at once.)  No kernel triggers its
-// dependents early: waiting blocks would hold registers and shared memory that the
-// running kernel's blocks use (measured slower).
-__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
-// Arrival index of this vehicle in lane g's count for the next occupancy rebuild.
-// Neighbouring threads mostly hold vehicles of the same lane (the sorted order), so
-// the threads of a warp with equal g share one atomic; the order inside the group is
-// arbitrary (the rebuild ranks by position and id).
-__device__ __forceinline__ int count_in_lane(const Dev& d, int g) {
-  const unsigned act = __activemask();
-  const unsigned peers = __match_any_sync(act, g);
-  const int ln = threadIdx.x & 31, lead = __ffs(peers) - 1;
-  int base = 0;
-  if (ln == lead) base = atomicAdd(&d.cnt[g], __popc(peers));
-  base = __shfl_sync(peers, base, lead);
-  return base + __popc(peers & ((1u << ln) - 1u));
-}
 
 // ------------------------------------------------------------------ occupancy
 __global__ void k_count(Dev d) {
@@ -115,6 +91,7 @@ __device__ __forceinline__ void ph_scan_sum(const Dev& d) {
 
 __global__ void k_scan_sum(Dev d) {
   griddep_wait();
+  if (step_timed_out(d)) return;
   ph_scan_sum(d);
 }
 
@@ -178,6 +155,7 @@ __device__ __forceinline__ void ph_scan_fin(const Dev& d) {
       d.ctl->nB = tot_before + tot;
       d.lane_start[d.n_lanes] = tot_before + tot;
       d.ctl->n_elig = 0;
+      d.ctl->chunk_next = 0;
       const unsigned ep = d.ctl->occ_epoch + 1u;
       d.ctl->occ_epoch = ep ? ep : 1u;   // tag 0 marks never-written rear records
     }
@@ -186,6 +164,7 @@ __device__ __forceinline__ void ph_scan_fin(const Dev& d) {
 
 __global__ void k_scan_fin(Dev d) {
   griddep_wait();
+  if (step_timed_out(d)) return;
   ph_scan_fin(d);
 }
 
@@ -207,6 +186,7 @@ __device__ __forceinline__ void ph_scatter(const Dev& d) {
 
 __global__ void k_scatter(Dev d) {
   griddep_wait();
+  if (step_timed_out(d)) return;
   ph_scatter(d);
 }
 
@@ -246,6 +226,7 @@ __device__ __forceinline__ void ph_rank(const Dev& d) {
     d.B.lane[dst] = lane;
     d.B.mv[dst] = mv;
     if (rank == 0) d.rear[g] = RearRec{xp, vv, vp, ep};
+    if (dst + 1 == s1) d.fr[g] = FrontRec{xp, vv, vp, nxt, cur, {0, 0, 0}};
     if (dst + 1 == s1 && nxt >= 0) {
       const LinkRec& L = d.links[e];
       if (L.ctrl == kCtrlStop && d.holder[L.to] == -1 && (L.len - xp) <= d.stop_acq)
@@ -256,96 +237,10 @@ __device__ __forceinline__ void ph_rank(const Dev& d) {
 
 __global__ void __launch_bounds__(256, 8) k_rank(Dev d) {
   griddep_wait();
+  if (step_timed_out(d)) return;
   ph_rank(d);
 }
 
-// ------------------------------------------------------------------ neighbours / IDM
-__device__ __forceinline__ bool is_holder(const Dev& d, const LinkRec& L, int t, int vid, int lane,
-                                          bool front) {
-  if (L.ctrl != kCtrlStop) return false;
-  int h = d.holder[L.to];
-  if (h == vid) return true;
-  return h == -1 && front && d.acq[L.to] == epoch_key(t, rr_rank(L, t), lane);
-}
-
-__device__ __forceinline__ bool line_closed(const Dev& d, const LinkRec& L, int t, bool holder) {
-  if (L.ctrl == kCtrlSignal) return !signal_green(L, t * d.dt_ds);
-  if (L.ctrl == kCtrlStop) return !holder;
-  return false;
-}
-
-// Eq. 7 parameters and desired speed of trip vid on link L: its class's, or with vehicle
-// types (Sec. 6.3.5) the class's with a scaled by the type (a table built on the host)
-// and v0 capped at the type's maximum speed.
-template <bool TYPES>
-__device__ __forceinline__ void veh_par(const Dev& d, const LinkRec& L, int vid, ClassPar& P, float& v0) {
-  if (TYPES) {
-    const int ty = d.vtype[vid];
-    P = d.cls_ty[L.cls * d.n_vty + ty];
-    v0 = fminf(L.v0, d.vty_vmax[ty]);
-  } else {
-    P = d.cls[L.cls];
-    v0 = L.v0;
-  }
-}
-
-// length of trip vid's vehicle
-template <bool TYPES>
-__device__ __forceinline__ float veh_len(const Dev& d, int vid) {
-  return TYPES ? d.vty_len[d.vtype[vid]] : d.vlen;
-}
-
-// Acceleration of a vehicle with nothing ahead on its link e, considered in lane
-// `lane`: leader = rearmost vehicle of the mapped lane of its next link (gap across
-// the link end, to the leader's rear); a closed stop line is a standing obstacle
-// (smaller acceleration).  P, v0: the vehicle's Eq. 7 parameters; ep: the epoch of the
-// current rear records.  Optionally returns
-// the mapped lane (*gt), whether it has a rearmost vehicle other than this one
-// (*lead) and that vehicle's rear position (*room); next_rec: the next link's record
-// when the caller has loaded it already.
-template <bool TYPES>
-__device__ __forceinline__ float acc_front(const Dev& d, unsigned ep, const LinkRec& L, const ClassPar& P, float v0,
-                                           int vid, int nxt, int lane, float x, float v, bool closed,
-                                           TapeForm* f = nullptr, int* gt = nullptr, bool* lead = nullptr,
-                                           float* room = nullptr, const LinkRec* next_rec = nullptr) {
-  if (nxt < 0) {
-    if (f) *f = TapeForm{-1, 0.0f, 0.0f, kFormFree, 0, 0, 0};
-    return idm_acc(P, v0, d.s_min, 0.0f, v, 0.0f, false);
-  }
-  const LinkRec Ln = next_rec ? *next_rec : d.links[nxt];
-  const int m = lane < Ln.lanes - 1 ? lane : Ln.lanes - 1;
-  const int g = Ln.lane_base + m;
-  const RearRec r = d.rear[g];
-  float a1;
-  TapeForm f1;
-  const bool has = r.tag == ep && r.vid != vid;
-  if (gt) *gt = g;
-  if (lead) *lead = has;
-  if (has) {
-    const float len_r = veh_len<TYPES>(d, r.vid);
-    if (room) *room = r.x - len_r;
-    float s = ((L.len - x) + r.x) - len_r;
-    a1 = idm_acc(P, v0, d.s_min, s, v, r.v, true);
-    if (f) f1 = TapeForm{r.vid, s, r.v, kFormNext, 0, 0, 0};
-  } else {
-    a1 = idm_acc(P, v0, d.s_min, 0.0f, v, 0.0f, false);
-    if (f) f1 = TapeForm{-1, 0.0f, 0.0f, kFormFree, 0, 0, 0};
-  }
-  if (closed) {
-    const float s2 = L.len - x;
-    const float a2 = idm_acc(P, v0, d.s_min, s2, v, 0.0f, true);
-    if (a2 < a1) {
-      if (f) *f = TapeForm{-1, s2, 0.0f, kFormStop, 0, 0, 0};
-      return a2;
-    }
-  }
-  if (f) *f = f1;
-  return a1;
-}
-
-__device__ __forceinline__ TapeRec* tape_slot(const Dev& d, int t, int vid) {
-  return d.tape + (size_t)(t - (int)d.ctl->tape_t0) * (size_t)d.n_trips + (size_t)vid;
-}
 
 // Own-lane step of the vehicle at sorted position p (front: the last of its lane):
 // Eq. 7 behind the next vehicle of the lane, or for the front behind the rearmost
@@ -462,6 +357,7 @@ __device__ __forceinline__ void ph_own(const Dev& d) {
 template <bool TAPE, bool TYPES>
 __global__ void __launch_bounds__(256, 6) k_own(Dev d) {
   griddep_wait();
+  if (step_timed_out(d)) return;
   ph_own<TAPE, TYPES>(d);
 }
 
@@ -603,19 +499,11 @@ __device__ __forceinline__ void ph_decide(const Dev& d) {
 template <bool TAPE, bool TYPES>
 __global__ void __launch_bounds__(256, 6) k_decide(Dev d) {
   griddep_wait();
+  if (step_timed_out(d)) return;
   ph_decide<TAPE, TYPES>(d);
 }
 
 // ------------------------------------------------------------------ measured outputs
-// Sec. 6.3.1: trip vid leaves link e in step t; it entered it in step enter[vid]
-// (-1 when it was already on the link when the outputs were cleared).
-__device__ __forceinline__ void note_exit(const Dev& d, int vid, int e, int t) {
-  const int te = d.enter[vid];
-  if (te >= 0) {
-    atomicAdd(&d.tt_sum[e], (unsigned long long)(t - te));
-    atomicAdd(&d.tt_n[e], 1);
-  }
-}
 
 // Sec. 6.4 per-edge sample of the state at step t (when t is a multiple of samp_every),
 // one thread per link over its contiguous run of the sorted buffer (lanes in order,
@@ -657,6 +545,7 @@ __device__ __forceinline__ void ph_edge_sample(const Dev& d) {
 
 __global__ void k_edge_sample(Dev d) {
   griddep_wait();
+  if (step_timed_out(d)) return;
   ph_edge_sample(d);
 }
 
@@ -793,69 +682,12 @@ __device__ __forceinline__ void ph_move(const Dev& d) {
 }
 
 
-// ------------------------------------------------------------------ departures
-// The head of each link's queue of due trips enters at x = 0, v = 0 in the allowed
-// lane with the largest rear space (ties to the lowest lane) that received no
-// vehicle from upstream in this step, if that space is at least s0 + vehicle length.
-template <bool OUT, bool TYPES>
-__device__ __forceinline__ void ph_insert(const Dev& d) {
-  const int nq = d.n_qlinks;
-  const int t = (int)d.ctl->t;
-  const int nB = d.ctl->nB;
-  GRID_STRIDE(i, nq) {
-    const int e = d.qlinks[i];
-    const int hd = d.q_head[e];
-    if (hd >= d.q_end[e]) continue;
-    const int h = d.q_items[hd];
-    if ((long long)d.depart[h] > t) continue;
-    const LinkRec L = d.links[e];
-    const int off = d.roff[h], len = d.rlen[h];
-    const int e2 = len >= 2 ? d.routes[off + 1] : (d.loop ? d.routes[off] : -1);
-    const int mc = move_class(d, e, e2);
-    const int M = lane_mask(mc, L.lanes);
-    const unsigned ep = d.ctl->occ_epoch;
-    int bl = -1;
-    float brs = 0.0f;
-    for (int l = 0; l < L.lanes; l++) {
-      if (!((M >> l) & 1)) continue;
-      const int g = L.lane_base + l;
-      if (epoch_current(d.best[g], t)) continue;
-      const RearRec r = d.rear[g];
-      const float rs = r.tag == ep ? r.x - veh_len<TYPES>(d, r.vid) : INFINITY;
-      if (bl < 0 || rs > brs) {
-        bl = l;
-        brs = rs;
-      }
-    }
-    if (bl < 0) continue;
-    const float need = d.cls[L.cls].s0 + veh_len<TYPES>(d, h);
-    if (!(brs >= need)) continue;
-    const int slot = nB + atomicAdd(&d.ctl->n_ins, 1);
-    if (slot >= d.n_trips) { set_err(d, kErrSlot, slot); continue; }
-    d.A.x[slot] = 0.0f;
-    d.A.v[slot] = 0.0f;
-    d.A.vid[slot] = h;
-    d.A.link[slot] = e;
-    d.A.nxt[slot] = e2;
-    d.A.cur[slot] = 0;
-    d.A.lane[slot] = bl;
-    d.A.mv[slot] = (uint8_t)mc;
-    d.adec[slot] = 0;
-    d.A.gid[slot] = L.lane_base + bl;
-    d.aidx[slot] = atomicAdd(&d.cnt[L.lane_base + bl], 1);
-    d.status[h] = kActive;
-    d.ins_step[h] = (int32_t)t;
-    if (OUT && d.enter) d.enter[h] = t;
-    d.q_head[e] = hd + 1;
-  }
-}
-
-
 // Move and departures touch disjoint slots of buffer A (departures append after the
 // sorted vehicles) and read only state of step t, so they share one launch.
 template <bool TAPE, bool OUT, bool TYPES>
 __global__ void k_move_insert(Dev d) {
   griddep_wait();
+  if (step_timed_out(d)) return;
   ph_move<TAPE, OUT, TYPES>(d);
   if (d.n_qlinks > 0) ph_insert<OUT, TYPES>(d);
 }
@@ -878,183 +710,10 @@ __device__ __forceinline__ void ph_finish(const Dev& d) {
 
 __global__ void k_finish(Dev d) {
   griddep_wait();
+  if (step_timed_out(d)) return;
   ph_finish(d);
 }
 
-
-// ------------------------------------------------------------------ bulk-copy staging
-// The sorted state is read in tiles of kTile consecutive positions; one thread of the
-// block copies a tile's arrays into shared memory with cp.async.bulk (completion
-// counted on an mbarrier), kStages - 1 tiles ahead of the tile being computed.
-constexpr int kTile = 256, kStages = 3;
-constexpr long long kWaitLimit = kDefaultWaitCycles;   // drain of issued copies
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred P1;\n\tmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\tselp.u32 %0, 1, 0, P1;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred P1;\n\tmbarrier.test_wait.parity.shared::cta.b64 P1, [%1], %2;\n\tselp.u32 %0, 1, 0, P1;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Wait for phase `parity` of bar for at most `limit` SM cycles (false when it runs out).
-// The first probe does not suspend the thread, so that a limit shorter than a copy's
-// latency runs out at once.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
-  const long long t0 = clock64();
-  if (mbar_test_wait(bar, parity)) return true;
-  while (clock64() - t0 <= limit)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-
-// bytes: a multiple of 16; src and dst 16-byte aligned
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_addr(dst)),
-               "l"(src), "r"(bytes), "r"(smem_addr(bar))
-               : "memory");
-}
-
-struct __align__(16) OwnTile {
-  float x[kTile + 4], v[kTile + 4];
-  int32_t vid[kTile + 4], tg[kTile + 4];
-  int32_t link[kTile], lane[kTile], nxt[kTile];
-};
-constexpr uint32_t kOwnTileBytes = 4 * (kTile + 4) * 4 + 3 * kTile * 4;
-static_assert(sizeof(OwnTile) == kOwnTileBytes, "OwnTile must be packed");
-
-__device__ __forceinline__ void own_issue(const Dev& d, OwnTile* tl, uint64_t* bar, int tile) {
-  const size_t b = (size_t)tile * kTile;
-  mbar_expect_tx(bar, kOwnTileBytes);
-  bulk_g2s(tl->x, d.B.x + b, (kTile + 4) * 4, bar);
-  bulk_g2s(tl->v, d.B.v + b, (kTile + 4) * 4, bar);
-  bulk_g2s(tl->vid, d.B.vid + b, (kTile + 4) * 4, bar);
-  bulk_g2s(tl->tg, d.tg + b, (kTile + 4) * 4, bar);
-  bulk_g2s(tl->link, d.B.link + b, kTile * 4, bar);
-  bulk_g2s(tl->lane, d.B.lane + b, kTile * 4, bar);
-  bulk_g2s(tl->nxt, d.B.nxt + b, kTile * 4, bar);
-}
-
-// Lane-change candidates of one warp, gathered in shared memory and appended to the
-// global list kListCap - 32 or more at a time (one atomic on the list counter per
-// flush).  Every lane of the warp takes part in each call.
-constexpr int kListCap = 256;
-
-__device__ __forceinline__ void warp_list_flush(const Dev& d, const int* buf, int& qn) {
-  __syncwarp();
-  const int ln = threadIdx.x & 31;
-  int base = 0;
-  if (ln == 0 && qn > 0) base = atomicAdd(&d.ctl->n_elig, qn);
-  base = __shfl_sync(0xffffffffu, base, 0);
-  for (int i = ln; i < qn; i += 32) d.elig[base + i] = buf[i];
-  __syncwarp();
-  qn = 0;
-}
-
-__device__ __forceinline__ void warp_list_push(const Dev& d, int* buf, int& qn, bool pred, int pos) {
-  const unsigned m = __ballot_sync(0xffffffffu, pred);
-  if (pred) buf[qn + __popc(m & ((1u << (threadIdx.x & 31)) - 1u))] = pos;
-  qn += __popc(m);
-  if (qn > kListCap - 32) warp_list_flush(d, buf, qn);
-}
-
-// Own-lane step with the sorted state staged tile by tile (blocks of kTile threads,
-// one resident wave walking the tiles).  A wait for a tile that runs out (d.wait_limit
-// cycles) sets kErrTimeout; the block then lets the copies it issued land (waiting up
-// to kWaitLimit cycles for each) and returns.
-template <bool TYPES>
-__global__ void __launch_bounds__(kTile) k_own_tiled(Dev d) {
-  griddep_wait();
-  __shared__ OwnTile tl[kStages];
-  __shared__ __align__(8) uint64_t bar[kStages];
-  __shared__ int lists[kTile / 32][kListCap];
-  int* lbuf = lists[threadIdx.x >> 5];
-  int lq = 0;   // warp-uniform
-  const int nB = d.ctl->nB;
-  const int t = (int)d.ctl->t;
-  const unsigned ep = d.ctl->occ_epoch;
-  const int ntiles = (nB + kTile - 1) / kTile;
-  const int n_my = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; s++) mbar_init(&bar[s], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    for (int k = 0; k < kStages - 1 && k < n_my; k++) own_issue(d, &tl[k], &bar[k], blockIdx.x + k * gridDim.x);
-  }
-  __syncthreads();
-  for (int k = 0; k < n_my; k++) {
-    const int kn = k + kStages - 1;
-    if (threadIdx.x == 0 && kn < n_my) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      own_issue(d, &tl[kn % kStages], &bar[kn % kStages], blockIdx.x + kn * gridDim.x);
-    }
-    const int s = k % kStages;
-    const bool ok = mbar_wait(&bar[s], (uint32_t)(k / kStages) & 1u, d.wait_limit);
-    if (!__syncthreads_and(ok)) {
-      if (threadIdx.x == 0) {
-        set_err(d, kErrTimeout, blockIdx.x);
-        // let the copies already issued (tiles k .. k + kStages - 1) land before the
-        // block's shared memory goes away
-        for (int j = k; j < n_my && j < k + kStages; j++)
-          mbar_wait(&bar[j % kStages], (uint32_t)(j / kStages) & 1u, kWaitLimit);
-      }
-      __syncthreads();
-      return;
-    }
-    const OwnTile& T = tl[s];
-    const int i = threadIdx.x;
-    const int p = (blockIdx.x + k * gridDim.x) * kTile + i;
-    bool el = false;
-    if (p < nB) {
-      const bool front = p + 1 == nB || T.tg[i + 1] != T.tg[i];
-      el = own_core<false, TYPES>(d, p, front, t, ep, T.link[i], T.x[i], T.v[i], T.vid[i], T.lane[i], T.nxt[i],
-                                  T.x[i + 1], T.v[i + 1], T.vid[i + 1]);
-    }
-    warp_list_push(d, lbuf, lq, el, p);
-    __syncthreads();   // the reads of stage s end before it is refilled
-  }
-  warp_list_flush(d, lbuf, lq);
-}
-
-// blocks of the decision kernel resident on one SM (plain, with vehicle types)
-int decide_blocks_per_sm(bool types) {
-  int nb = 0;
-  cudaError_t e = types ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_decide<false, true>, 256, 0)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_decide<false, false>, 256, 0);
-  return e == cudaSuccess ? nb : 0;
-}
-
-// blocks of the tiled own-lane kernel resident on one SM (plain, with vehicle types)
-int own_tiled_blocks_per_sm(bool types) {
-  int nb = 0;
-  cudaError_t e = types ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_own_tiled<true>, kTile, 0)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_own_tiled<false>, kTile, 0);
-  return e == cudaSuccess ? nb : 0;
-}
 
 // ------------------------------------------------------------------ launch sequence
 // Launch with programmatic stream serialization (the kernel starts with griddep_wait),
@@ -1085,10 +744,14 @@ void launch_occupancy(const Dev& d, int grid, cudaStream_t s) {
 }
 
 // Kernels of one step, in launch order (names reported by the timed step).  The
-// lane counts the scan starts from are made by the previous step's move and insert
-// kernels (or by k_count after a state is loaded).
-const char* const kKernelNames[kNumKernels] = {"scan_sum", "scan_fin", "scatter", "rank", "own", "decide",
-                                               "move_insert", "finish"};
+// lane counts the scan starts from are made by the previous step's chunk kernel (or by
+// k_count after a state is loaded).  With the adjoint's tape on, "front" and "chunk"
+// are the plain-load own-lane, decision and move kernels that write the tape.
+const char* const kKernelNames[kNumKernels] = {"scan_sum", "scan_fin", "scatter", "rank", "front", "chunk",
+                                               "finish"};
+
+void launch_front(const Dev& d, int grid, cudaStream_t s);
+void launch_chunk(const Dev& d, cudaStream_t s);
 
 bool kernel_enabled(int k, const Dev& d, bool has_stop) {
   (void)k;
@@ -1104,31 +767,20 @@ void launch_kernel(int k, const Dev& d, int grid, cudaStream_t s) {
     case kKScanFin: launch_pdl(k_scan_fin, nb, kScanThreads, s, d); break;
     case kKScatter: launch_pdl(k_scatter, grid, 256, s, d); break;
     case kKRank: launch_pdl(k_rank, grid, 256, s, d); break;
-    case kKOwn:
-      // the per-edge sample (when enabled) reads the sorted state, like own; its time
-      // is counted with own's
+    case kKFront:
+      // the per-edge sample (when enabled) reads the sorted state of step t; its time
+      // is counted with the fronts'
       if (d.acc_u) launch_pdl(k_edge_sample, grid, 256, s, d);
+      if (d.tape) launch_pdl(k_own<true, false>, grid, 256, s, d);
+      else launch_front(d, grid, s);
+      break;
+    case kKChunk:
       if (d.tape) {
-        launch_pdl(k_own<true, false>, grid, 256, s, d);
+        launch_pdl(k_decide<true, false>, grid, 256, s, d);
+        launch_pdl(k_move_insert<true, false, false>, grid, 256, s, d);
       } else {
-        // one resident wave of tile-walking blocks
-        const int g2 = d.vtype ? d.own_grid[1] : d.own_grid[0];
-        if (d.vtype) launch_pdl(k_own_tiled<true>, g2, kTile, s, d);
-        else launch_pdl(k_own_tiled<false>, g2, kTile, s, d);
+        launch_chunk(d, s);
       }
-      break;
-    case kKDecide:
-      // one resident wave: the candidate list's length is known on the device only
-      if (d.tape) launch_pdl(k_decide<true, false>, grid, 256, s, d);
-      else if (d.vtype) launch_pdl(k_decide<false, true>, d.dec_grid[1], 256, s, d);
-      else launch_pdl(k_decide<false, false>, d.dec_grid[0], 256, s, d);
-      break;
-    case kKMoveInsert:
-      if (d.tape) launch_pdl(k_move_insert<true, false, false>, grid, 256, s, d);
-      else if (d.vtype && outputs_on(d)) launch_pdl(k_move_insert<false, true, true>, grid, 256, s, d);
-      else if (d.vtype) launch_pdl(k_move_insert<false, false, true>, grid, 256, s, d);
-      else if (outputs_on(d)) launch_pdl(k_move_insert<false, true, false>, grid, 256, s, d);
-      else launch_pdl(k_move_insert<false, false, false>, grid, 256, s, d);
       break;
     case kKFinish: launch_pdl(k_finish, 1, 1, s, d); break;
     default: break;
@@ -1208,7 +860,7 @@ __device__ __forceinline__ bool grid_barrier(GridSync* gs, int* err, long long l
   return s_ok != 0;
 }
 
-__global__ void k_persistent(Dev d, GridSync* gs, int n_steps, long long limit) {
+__global__ void __launch_bounds__(1024, 1) k_persistent(Dev d, GridSync* gs, int n_steps, long long limit) {
   int* err = &d.ctl->err;
   for (int step = 0; step < n_steps; step++) {
     // the previous step's counter update (block 0) needs no barrier of its own: nothing

@@ -20,7 +20,6 @@ ERR_NAMES = {0: "SIM_OK", -1: "SIM_EINVAL", -2: "SIM_ENOMEM", -3: "SIM_ECUDA", -
 F_STATUS, F_LINK, F_LANE, F_CURSOR, F_X, F_V, F_INSERT, F_ARRIVE, F_LANECHANGE = (1 << k for k in range(9))
 F_ALL = (1 << 9) - 1
 
-N_KERNELS = 8
 EXPORTS = ["sim_create", "sim_create_batch", "sim_set_stream", "sim_route", "sim_set_routes", "sim_route_size",
            "sim_read_routes", "sim_step", "sim_step_timed", "sim_kernel_name", "sim_read_state", "sim_write_state", "sim_occupancy", "sim_n_lanes",
            "sim_counters", "sim_last_error", "sim_destroy", "sim_set_class_params", "sim_observe", "sim_adjoint",
@@ -29,6 +28,14 @@ EXPORTS = ["sim_create", "sim_create_batch", "sim_set_stream", "sim_route", "sim
            "sim_reroute", "sim_equilibrium", "sim_assign_static", "sim_set_vehicle_types", "sim_loss"]
 OUT_EMISSIONS, OUT_LINK_TIMES, OUT_EDGE_SAMPLES = 1, 2, 4
 SIM_EXEC_GRAPH, SIM_EXEC_PERSISTENT = 0, 1
+
+
+def n_kernels():
+    """Kernels of one step (the names sim_kernel_name reports, in launch order)."""
+    n = 0
+    while lib().sim_kernel_name(n):
+        n += 1
+    return n
 
 
 class sim_network(C.Structure):
@@ -279,9 +286,10 @@ class Sim:
 
     def step_timed(self, n=1):
         """Advance n steps with an event after every kernel; returns {kernel name: ms}."""
-        ms = np.zeros(N_KERNELS, np.float32)
+        nk = n_kernels()
+        ms = np.zeros(nk, np.float32)
         self._check(lib().sim_step_timed(self.h, int(n), _p(ms)))
-        return {lib().sim_kernel_name(k).decode(): float(ms[k]) for k in range(N_KERNELS)}
+        return {lib().sim_kernel_name(k).decode(): float(ms[k]) for k in range(nk)}
 
     def state(self, fields=F_ALL):
         n = self.n_trips
