@@ -87,6 +87,8 @@ def parse():
     ap.add_argument("--no-assign", action="store_true", help="skip the static-assignment timing")
     ap.add_argument("--no-outputs", action="store_true",
                     help="skip the measured-output overhead and the equilibrium timing")
+    ap.add_argument("--no-day", action="store_true", help="skip the natural 24 h metro run")
+    ap.add_argument("--no-jam", action="store_true", help="skip the standing-queue (jammed lanes) case")
     ap.add_argument("--workload", default="metro", choices=["metro", "metro-walk"],
                     help="metro: GPU-planned shortest-path routes; metro-walk: the first --trips trips on "
                          "random-walk routes (no trip planning; smaller cases for profiling)")
@@ -425,6 +427,73 @@ def measure_assignment(G, S, torch, iters=2):
             "objective": [float(x) for x in r["objective"]]}
 
 
+# ---------------------------------------------------------------------------- natural day, queues
+def measure_natural_day(G, S, torch, stream):
+    """The metro network with its natural demand (3,000,000 gravity-OD trips, bimodal
+    departures): trip planning on the GPU, then all 172,800 steps of the day from t = 0.
+    Vehicle-steps/s over the stepping (CUDA events), wall time with and without routing,
+    the active count every 30 simulated minutes."""
+    g = G.Sim(S.metro())
+    g.set_stream(stream.cuda_stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.route()
+    torch.cuda.synchronize()
+    route_s = time.perf_counter() - t0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    samples = []
+    step_ms = 0.0
+    t1 = time.perf_counter()
+    for _ in range(48):
+        e0.record(stream)
+        g.step(3600)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms += e0.elapsed_time(e1)
+        samples.append(int(g.counters()["active"]))
+    wall = time.perf_counter() - t1
+    c = g.counters()
+    g.close()
+    return {"workload": "metro, 3000000 trips, gravity OD, bimodal departures, GPU-planned routes, 172800 steps "
+                        "(24 h at 0.5 s)",
+            "value": c["veh_steps"] / (step_ms / 1e3), "unit": UNIT, "vehicle_steps": int(c["veh_steps"]),
+            "step_seconds": step_ms / 1e3, "wall_seconds": wall, "routing_seconds": route_s,
+            "end_to_end_seconds": wall + route_s, "peak_active_30min_samples": max(samples),
+            "active_every_30min": samples, "arrived": int(c["arrived"]), "departed": int(c["departed"])}
+
+
+def measure_jam(G, S, torch, stream, steps=300):
+    """Standing queues: 1000 corridors, each a 2 km two-lane link into a signalised node
+    (15 s of green per minute) holding about 285 vehicles per lane at rest.  Device time
+    per step and per kernel (the in-lane rank of the occupancy rebuild grows with the
+    queue length)."""
+    sc = S.jammed_corridors(n_corr=1000)
+    g = G.Sim(sc)
+    g.set_stream(stream.cuda_stream)
+    g.set_routes(sc["routes"]["offsets"], sc["routes"]["links"])
+    g.write_state(sc["init_state"])
+    g.step(10)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0 = g.counters()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    g.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    c1 = g.counters()
+    lane_start, _ = g.occupancy()
+    g.write_state(sc["init_state"])
+    g.step(10)
+    kms = g.step_timed(steps)
+    g.close()
+    vs = (c1["veh_steps"] - c0["veh_steps"]) / steps
+    return {"workload": "1000 corridors x 2 lanes x 2 km, queues at rest behind signals (green 15 s / 60 s)",
+            "ms_per_step": ms, "value": vs / (ms / 1e3), "unit": UNIT, "avg_active": vs,
+            "longest_lane_queue": int(np.diff(lane_start).max()),
+            "per_kernel_ms_per_step": {k: v / steps for k, v in kms.items()}}
+
+
 # ---------------------------------------------------------------------------- cuda arm
 def run_cuda(args):
     import torch
@@ -553,6 +622,11 @@ def run_cuda(args):
                "steps": e_steps, "pattern": "sim_write_state(host snapshot) then per step sim_step(1) + "
                                             "sim_read_state(x, v -> pinned host)"}
 
+    day = jam = None
+    if not args.no_day:
+        day = measure_natural_day(G, S, torch, stream)
+    if not args.no_jam:
+        jam = measure_jam(G, S, torch, stream)
     outputs = equilibrium = assignment = None
     if not args.no_outputs:
         outputs = measure_outputs(G, g, snap, args, stream, torch, ms / args.steps)
@@ -618,6 +692,8 @@ def run_cuda(args):
                     "origins_trees": int(len(np.unique(m["demand"]["origin"]))),
                     "trees_per_s": int(len(np.unique(m["demand"]["origin"]))) / route_s,
                     "trips": m["demand"]["n_trips"], "hops": int(off[-1])},
+        "natural_day": day,
+        "jammed_lanes": jam,
         "outputs": outputs,
         "equilibrium": equilibrium,
         "static_assignment": assignment,

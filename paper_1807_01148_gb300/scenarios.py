@@ -410,6 +410,46 @@ def random_walk_routes(sc: dict, min_hops: int = 20, max_hops: int = 120, seed: 
     return offsets.astype(np.int32), links.astype(np.int32)
 
 
+def jammed_corridors(n_corr: int = 1000, length: float = 2000.0, lanes: int = 2, spacing: float = 7.0,
+                     fill: float = 1.0, seed: int = BASE_SEED + 30) -> dict:
+    """Standing queues: n_corr separate corridors A -> B -> C, each a ``length`` m link
+    of ``lanes`` lanes into a signalised node B (cycle 60 s, the corridor's east-west
+    approach green 15 s, offsets uniform) and a 200 m exit link.  Every lane of the
+    long link holds a queue at rest, one vehicle per ``spacing`` m from the stop line
+    back over ``fill`` of the link (about 285 per lane at the defaults), routed A -> B
+    -> C; nothing departs later.  Returns a scenario with routes and initial state."""
+    rng = np.random.default_rng(seed)
+    n_nodes = 3 * n_corr
+    y = np.repeat(np.arange(n_corr) * 500.0, 3)
+    x = np.tile([0.0, length, length + 200.0], n_corr)
+    ctrl = np.tile([CTRL_NONE, CTRL_SIGNAL, CTRL_NONE], n_corr)
+    off = np.zeros(n_nodes, np.int64)
+    off[1::3] = rng.integers(0, 600, n_corr)
+    cyc = np.full(n_nodes, 600)
+    grn = np.full(n_nodes, 450)   # north-south green 45 s: the east-west corridor gets 15 s
+    a = np.arange(n_corr) * 3
+    lf = np.stack([a, a + 1], 1).ravel()
+    lt = np.stack([a + 1, a + 2], 1).ravel()
+    length_m = np.tile([length, 200.0], n_corr)
+    net = _net(n_nodes, np.round(x * 10), np.round(y * 10), ctrl, off, cyc, grn, lf, lt, length_m,
+               np.full(2 * n_corr, 13.9), np.full(2 * n_corr, lanes), np.zeros(2 * n_corr))
+    per_lane = int(np.floor(length * fill / spacing))
+    n_per = per_lane * lanes
+    nt = n_corr * n_per
+    corr = np.repeat(np.arange(n_corr), n_per)
+    k = np.tile(np.arange(n_per), n_corr)
+    lane = (k % lanes).astype(np.int32)
+    pos = k // lanes
+    xq = length - 1.0 - pos * spacing
+    routes_links = np.stack([2 * corr, 2 * corr + 1], 1).ravel().astype(np.int32)
+    offsets = (np.arange(nt + 1) * 2).astype(np.int32)
+    dem = _demand(3 * corr, 3 * corr + 2, np.zeros(nt, np.int64))
+    st = dict(status=np.full(nt, ST_ACTIVE, np.uint8), link=(2 * corr).astype(np.int32), lane=lane,
+              cursor=np.zeros(nt, np.int32), x=xq.astype(np.float32), v=np.zeros(nt, np.float32))
+    return dict(name=f"jam{n_corr}", network=net, demand=dem, params=default_params(1, seed=seed),
+                routes=dict(offsets=offsets, links=routes_links), init_state=st, steps=600)
+
+
 def saturate(sc: dict, offsets, links, spacing: float = 8.0, v_frac: float = 0.5,
              seed: int = BASE_SEED + 21) -> dict:
     """A saturated snapshot: every trip on the road at once.  Trip i sits on hop

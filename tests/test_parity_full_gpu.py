@@ -7,6 +7,11 @@
 - one full-size metro step: 3,000,000 vehicles on the 550,000-link network, every bit;
 - full-size metro trip planning (225k trees, 3M routes) on the GPU against oracle
   routes of trips from sampled origins;
+- the metro network with its natural demand pattern in a window: the trips of 900
+  sampled origins on their GPU-planned routes (against the oracle's own routes), with
+  departures compressed into the first 2,400 steps, 4,000 steps checked every 500:
+  departures, signals, stop signs, merges and arrivals at metro scale;
+- standing queues of about 285 vehicles per lane on 2 km links behind red lights;
 - empty and one-trip demands, error codes."""
 import numpy as np
 import pytest
@@ -102,6 +107,34 @@ def test_metro_full_size_one_step_bitexact(G, O):
         g.step(1)
         o.step(1)
         compare(g, o, f"metro step {k + 1}", check_occ=(k == 1))
+
+
+def test_metro_natural_window_bitexact(G, O):
+    sc = S.metro()
+    dem = sc["demand"]
+    rng = np.random.default_rng(1807)
+    origins = rng.choice(np.unique(dem["origin"]), 900, replace=False)
+    keep = np.flatnonzero(np.isin(dem["origin"], origins))
+    dep = dem["depart_step"][keep].astype(np.int64) * 2400 // 172_800   # same order, first 20 minutes
+    sc["demand"] = S._demand(dem["origin"][keep], dem["dest"][keep], dep)
+    assert sc["demand"]["n_trips"] > 8000
+    g, o = setup_pair(sc, G.Sim, O.OracleSim)
+    go, gl = g.routes()
+    oo, ol = o.routes()
+    assert np.array_equal(go, oo) and np.array_equal(gl, ol)
+    run_lockstep(g, o, 4000, 500)
+    c = o.counters()
+    assert c["departed"] == sc["demand"]["n_trips"] and c["arrived"] > c["departed"] // 2
+    assert c["lc_evals"] > 0
+
+
+def test_jammed_corridors_bitexact(G, O):
+    sc = S.jammed_corridors(n_corr=6)
+    g, o = setup_pair(sc, G.Sim, O.OracleSim)
+    lg, _ = g.occupancy()
+    assert np.diff(lg).max() >= 280          # hundreds of vehicles queued in one lane
+    run_lockstep(g, o, 600, 100)
+    assert o.counters()["arrived"] > 0
 
 
 def test_metro_full_size_routes_sampled(G, O):
