@@ -483,6 +483,7 @@ int create_from_flat(Flat& F, sim_handle** out) {
     TRY(dalloc(h, &d.fr, (size_t)nlan));
     TRY(dalloc(h, &d.cr, (size_t)nlan));
     TRY(dalloc(h, &d.chunks, chunk_table_size(F.nt)));
+    TRY(dalloc(h, &d.long_list, (size_t)nlan));
     {
       std::vector<int32_t> ll((size_t)nlan);
       for (int e = 0; e < F.nl; e++)

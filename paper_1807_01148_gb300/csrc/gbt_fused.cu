@@ -191,7 +191,8 @@ __global__ void __launch_bounds__(256) k_front(Dev d) {
       // the state after crossing, used if this bid wins (a bidding front never changes
       // lanes: its own-lane move reaches the link end, lane changers stay short of it)
       const int off = d.roff[f.vid], len = d.rlen[f.vid];
-      const int ncur = d.loop ? (f.cur + 1) % len : f.cur + 1;
+      const int cur = d.B.cur[s1 - 1];
+      const int ncur = d.loop ? (cur + 1) % len : cur + 1;
       const int k2 = ncur + 1;
       const int nnxt = k2 < len ? d.routes[off + k2] : (d.loop ? d.routes[off + k2 % len] : -1);
       const int m = lane < Lnx.lanes - 1 ? lane : Lnx.lanes - 1;

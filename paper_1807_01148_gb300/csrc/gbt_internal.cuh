@@ -77,8 +77,7 @@ struct __align__(16) RearRec {
 // occupied lane: what the lane-front kernel needs of it.
 struct __align__(16) FrontRec {
   float x, v;
-  int32_t vid, nxt, cur;
-  int32_t pad[3];
+  int32_t vid, nxt;
 };
 
 // State after crossing of a lane front that bids for admission (written by the lane-front
@@ -117,6 +116,7 @@ struct Ctl {
   int n_arr;
   int n_elig;      // lane-change candidates listed this step
   int chunk_next;  // next chunk of the fused step kernel to take
+  int n_long;      // long lane segments listed by the lane-start scan
 };
 
 // Forms of Eq. 7 an acceleration can come from (adjoint tape).
@@ -188,6 +188,7 @@ struct Dev {
   const int32_t* lane_link;   // per lane: its link
   CrossRec* cr;               // per lane: the bidding front's state after crossing
   ChunkInfo* chunks;          // chunks of the fused step kernel (this step's)
+  int32_t* long_list;         // lanes with long segments (sorted by a block each)
   int32_t* elig;              // sorted positions of this step's lane-change candidates
   TapeRec* tape;              // adjoint tape of the current segment (nullptr: not taping)
   TapeForm* tform;            // lane-change forms of the current step (taping only)

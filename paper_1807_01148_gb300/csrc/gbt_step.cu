@@ -35,6 +35,10 @@ __global__ void k_count(Dev d) {
 
 constexpr int kScanThreads = 256, kScanItems = 8, kScanChunk = kScanThreads * kScanItems;
 
+// Lane segments longer than this are sorted by k_rank_long (one block per segment);
+// the per-vehicle count of k_rank is quadratic in the segment length.
+constexpr int kLongSeg = 64;
+
 __device__ __forceinline__ int block_excl_scan(int val, int* smem_warp, int& total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int inc = val;
@@ -68,6 +72,7 @@ int scan_blocks(int n_lanes) { return (n_lanes + kScanChunk - 1) / kScanChunk; }
 // Per-chunk sums of the lane counts (chunks of kScanChunk lanes, one per block pass).
 __device__ __forceinline__ void ph_scan_sum(const Dev& d) {
   __shared__ int sw[33];
+  if (blockIdx.x == 0 && threadIdx.x == 0) d.ctl->n_long = 0;   // listed again by the scan
   const int nb = (d.n_lanes + kScanChunk - 1) / kScanChunk;
   for (int b = blockIdx.x; b < nb; b += gridDim.x) {
     int base = b * kScanChunk + threadIdx.x * kScanItems;
@@ -129,6 +134,10 @@ __device__ __forceinline__ void ph_scan_fin(const Dev& d) {
     for (int k = 0; k < kScanItems; k++) s += v[k];
     int tot;
     int ex = block_excl_scan(s, sw, tot) + tot_before;
+    // lanes whose segment the long-segment rank kernel sorts
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++)
+      if (v[k] > kLongSeg) d.long_list[atomicAdd(&d.ctl->n_long, 1)] = base + k;
     if (full) {
       int o[kScanItems];
 #pragma unroll
@@ -197,6 +206,32 @@ __global__ void k_scatter(Dev d) {
 // The vehicle that lands last is the lane's front: if its link ends at a free stop-
 // controlled node, it bids for the node here (Sec. 6.3.2 stop signs, one vehicle at
 // a time): the bid with the smallest (round-robin rank of its link, lane) acquires it.
+// The vehicle of scatter position p (buffer A slot src) lands at sorted position dst,
+// rank r of its lane segment [s0, s1).
+__device__ __forceinline__ void rank_emit(const Dev& d, int src, float xp, int vp, int g, int dst, int s1, bool first,
+                                          int t, unsigned ep) {
+  const int e = d.A.link[src], nxt = d.A.nxt[src], lane = d.A.lane[src], cur = d.A.cur[src];
+  const float vv = d.A.v[src];
+  d.B.x[dst] = xp;
+  d.B.v[dst] = vv;
+  d.B.vid[dst] = vp;
+  d.B.link[dst] = e;
+  d.B.nxt[dst] = nxt;
+  d.B.cur[dst] = cur;
+  d.B.lane[dst] = lane;
+  d.B.mv[dst] = d.A.mv[src];
+  if (first) d.rear[g] = RearRec{xp, vv, vp, ep};
+  if (dst + 1 == s1) {
+    d.fr[g] = FrontRec{xp, vv, vp, nxt};
+    if (nxt >= 0) {
+      const LinkRec& L = d.links[e];
+      if (L.ctrl == kCtrlStop && d.holder[L.to] == -1 && (L.len - xp) <= d.stop_acq)
+        atomicMin(&d.acq[L.to], epoch_key(t, rr_rank(L, t), lane));
+    }
+  }
+}
+
+template <bool SKIP_LONG>
 __device__ __forceinline__ void ph_rank(const Dev& d) {
   const int nB = d.ctl->nB;
   const int t = (int)d.ctl->t;
@@ -211,6 +246,7 @@ __device__ __forceinline__ void ph_rank(const Dev& d) {
     const float vv = d.A.v[src];
     const uint8_t mv = d.A.mv[src];
     const int s0 = d.lane_start[g], s1 = d.lane_start[g + 1];
+    if (SKIP_LONG && s1 - s0 > kLongSeg) continue;
     int rank = 0;
     for (int q = s0; q < s1; q++) {
       const float xq = d.tx[q];
@@ -226,7 +262,7 @@ __device__ __forceinline__ void ph_rank(const Dev& d) {
     d.B.lane[dst] = lane;
     d.B.mv[dst] = mv;
     if (rank == 0) d.rear[g] = RearRec{xp, vv, vp, ep};
-    if (dst + 1 == s1) d.fr[g] = FrontRec{xp, vv, vp, nxt, cur, {0, 0, 0}};
+    if (dst + 1 == s1) d.fr[g] = FrontRec{xp, vv, vp, nxt};
     if (dst + 1 == s1 && nxt >= 0) {
       const LinkRec& L = d.links[e];
       if (L.ctrl == kCtrlStop && d.holder[L.to] == -1 && (L.len - xp) <= d.stop_acq)
@@ -235,10 +271,79 @@ __device__ __forceinline__ void ph_rank(const Dev& d) {
   }
 }
 
+// Long lane segments (queues): one block per segment sorts its (x, vid) keys in shared
+// memory with a bitonic network (Batcher 1968) and moves the vehicles to their sorted
+// positions; segments beyond the shared-memory capacity fall back to the per-vehicle
+// count.
+constexpr int kLongCap = 2048;
+
+__global__ void __launch_bounds__(256) k_rank_long(Dev d) {
+  griddep_wait();
+  if (step_timed_out(d)) return;
+  __shared__ float sx[kLongCap];
+  __shared__ int32_t sv[kLongCap];
+  __shared__ int16_t si[kLongCap];
+  const int nl = d.ctl->n_long;
+  const int t = (int)d.ctl->t;
+  const unsigned ep = d.ctl->occ_epoch;
+  for (int j = blockIdx.x; j < nl; j += gridDim.x) {
+    const int g = d.long_list[j];
+    const int s0 = d.lane_start[g], s1 = d.lane_start[g + 1], k = s1 - s0;
+    if (k > kLongCap) {
+      for (int p = s0 + threadIdx.x; p < s1; p += blockDim.x) {
+        const float xp = d.tx[p];
+        const int vp = d.tvid[p];
+        int rank = 0;
+        for (int q = s0; q < s1; q++) {
+          const float xq = d.tx[q];
+          rank += (xq < xp || (xq == xp && d.tvid[q] < vp)) ? 1 : 0;
+        }
+        rank_emit(d, d.tsrc[p], xp, vp, g, s0 + rank, s1, rank == 0, t, ep);
+      }
+      continue;
+    }
+    int n = 1;
+    while (n < k) n <<= 1;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const bool in = i < k;
+      sx[i] = in ? d.tx[s0 + i] : INFINITY;
+      sv[i] = in ? d.tvid[s0 + i] : INT32_MAX;
+      si[i] = (int16_t)i;
+    }
+    __syncthreads();
+    for (int size = 2; size <= n; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int i = threadIdx.x; i < (n >> 1); i += blockDim.x) {
+          const int lo = 2 * stride * (i / stride) + (i % stride), hi = lo + stride;
+          const bool up = (lo & size) == 0;
+          const float xa = sx[lo], xb = sx[hi];
+          const int va = sv[lo], vb = sv[hi];
+          const bool gt = xa > xb || (xa == xb && va > vb);
+          if (gt == up) {
+            sx[lo] = xb;
+            sx[hi] = xa;
+            sv[lo] = vb;
+            sv[hi] = va;
+            const int16_t ia = si[lo];
+            si[lo] = si[hi];
+            si[hi] = ia;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int r = threadIdx.x; r < k; r += blockDim.x) {
+      const int p = s0 + si[r];
+      rank_emit(d, d.tsrc[p], sx[r], sv[r], g, s0 + r, s1, r == 0, t, ep);
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void __launch_bounds__(256, 8) k_rank(Dev d) {
   griddep_wait();
   if (step_timed_out(d)) return;
-  ph_rank(d);
+  ph_rank<true>(d);
 }
 
 
@@ -766,7 +871,10 @@ void launch_kernel(int k, const Dev& d, int grid, cudaStream_t s) {
     case kKScanSum: k_scan_sum<<<nb, kScanThreads, 0, s>>>(d); break;
     case kKScanFin: launch_pdl(k_scan_fin, nb, kScanThreads, s, d); break;
     case kKScatter: launch_pdl(k_scatter, grid, 256, s, d); break;
-    case kKRank: launch_pdl(k_rank, grid, 256, s, d); break;
+    case kKRank:
+      launch_pdl(k_rank, grid, 256, s, d);
+      launch_pdl(k_rank_long, grid, 256, s, d);
+      break;
     case kKFront:
       // the per-edge sample (when enabled) reads the sorted state of step t; its time
       // is counted with the fronts'
@@ -871,7 +979,7 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(Dev d, GridSync* gs, int
     if (!grid_barrier(gs, err, limit)) return;
     ph_scatter(d);
     if (!grid_barrier(gs, err, limit)) return;
-    ph_rank(d);
+    ph_rank<false>(d);
     if (!grid_barrier(gs, err, limit)) return;
     // the edge sample and own read the sorted state and write disjoint arrays
     if (d.acc_u) ph_edge_sample(d);
