@@ -272,7 +272,10 @@ __device__ __forceinline__ int chunk_own(const Dev& d, const ChunkView& V, int n
       } else {
         const float sg = (V.x[i + 1] - x) - (TYPES ? veh_len<true>(d, V.vid[i + 1]) : d.vlen);
         a = idm_om(P, om, d.s_min, sg, v, V.v[i + 1]);
-        fl = (L.ctrl == kCtrlStop && d.holder[L.to] == vid) ? kFlagHolder : 0;
+        // a stop-sign holder acquired the node within stop_acquire_m of the line and has
+        // not moved back since (positions never decrease on a link): farther vehicles
+        // cannot hold it, and skip the read
+        fl = (L.ctrl == kCtrlStop && L.len - x <= d.stop_acq && d.holder[L.to] == vid) ? kFlagHolder : 0;
       }
       V.om[i] = om;
       float xo, vo;
@@ -384,7 +387,7 @@ __device__ __forceinline__ void chunk_decide_one(const Dev& d, const ChunkView& 
         } else {
           const int vF = V.vid[F];
           const int nF = V.nxt[F];
-          const bool holdF = is_holder(d, L, t, vF, lane, false);
+          const bool holdF = L.len - V.x[F] <= d.stop_acq && is_holder(d, L, t, vF, lane, false);
           const bool closedF = nF >= 0 && line_closed(d, L, t, holdF);
           ao = acc_front<TYPES>(d, ep, L, PF, v0F, vF, nF, lane, V.x[F], V.v[F], closedF);
         }

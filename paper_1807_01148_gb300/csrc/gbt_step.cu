@@ -271,11 +271,18 @@ __device__ __forceinline__ void ph_rank(const Dev& d) {
   }
 }
 
-// Long lane segments (queues): one block per segment sorts its (x, vid) keys in shared
-// memory with a bitonic network (Batcher 1968) and moves the vehicles to their sorted
-// positions; segments beyond the shared-memory capacity fall back to the per-vehicle
-// count.
-constexpr int kLongCap = 2048;
+// Long lane segments (queues): one block per segment, keys (x, vid) staged in shared
+// memory.  The scatter leaves a segment as a few ascending runs (each warp of the move
+// kernel counts its vehicles of a lane in order; the warps' atomics interleave), so the
+// rank of a key is its index in its own run plus, for every other run, the number of
+// keys below it there (a binary search): an exact merge count.  Segments with more
+// than kMaxRuns runs are sorted with a bitonic network (Batcher 1968) instead, and
+// segments beyond the shared-memory capacity fall back to the per-vehicle count.
+constexpr int kLongCap = 2048, kMaxRuns = 64;
+
+__device__ __forceinline__ bool key_less(float xa, int va, float xb, int vb) {
+  return xa < xb || (xa == xb && va < vb);
+}
 
 __global__ void __launch_bounds__(256) k_rank_long(Dev d) {
   griddep_wait();
@@ -283,6 +290,8 @@ __global__ void __launch_bounds__(256) k_rank_long(Dev d) {
   __shared__ float sx[kLongCap];
   __shared__ int32_t sv[kLongCap];
   __shared__ int16_t si[kLongCap];
+  __shared__ int16_t run_start[kMaxRuns + 1];
+  __shared__ int s_runs;
   const int nl = d.ctl->n_long;
   const int t = (int)d.ctl->t;
   const unsigned ep = d.ctl->occ_epoch;
@@ -302,19 +311,74 @@ __global__ void __launch_bounds__(256) k_rank_long(Dev d) {
       }
       continue;
     }
+    if (threadIdx.x == 0) s_runs = 0;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+      sx[i] = d.tx[s0 + i];
+      sv[i] = d.tvid[s0 + i];
+    }
+    __syncthreads();
+    // run starts: positions whose key is below the previous one (and position 0)
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+      if (i == 0 || key_less(sx[i], sv[i], sx[i - 1], sv[i - 1])) {
+        const int r = atomicAdd(&s_runs, 1);
+        if (r < kMaxRuns) run_start[r] = (int16_t)i;
+      }
+    }
+    __syncthreads();
+    const int R = s_runs;
+    if (R <= kMaxRuns) {
+      if (threadIdx.x == 0) {   // order the few run starts; the segment end closes the last
+        for (int a = 1; a < R; a++) {
+          const int16_t v = run_start[a];
+          int b = a - 1;
+          while (b >= 0 && run_start[b] > v) {
+            run_start[b + 1] = run_start[b];
+            b--;
+          }
+          run_start[b + 1] = v;
+        }
+        run_start[R] = (int16_t)k;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        const float x = sx[i];
+        const int v = sv[i];
+        int rank = 0;
+        for (int r = 0; r < R; r++) {
+          const int a = run_start[r], b = run_start[r + 1];
+          if (i >= a && i < b) {
+            rank += i - a;
+            continue;
+          }
+          int lo = a, hi = b;   // keys of run r below (x, v)
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (key_less(sx[mid], sv[mid], x, v)) lo = mid + 1;
+            else hi = mid;
+          }
+          rank += lo - a;
+        }
+        rank_emit(d, d.tsrc[s0 + i], x, v, g, s0 + rank, s1, rank == 0, t, ep);
+      }
+      __syncthreads();
+      continue;
+    }
     int n = 1;
     while (n < k) n <<= 1;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const bool in = i < k;
-      sx[i] = in ? d.tx[s0 + i] : INFINITY;
-      sv[i] = in ? d.tvid[s0 + i] : INT32_MAX;
+      if (i >= k) {
+        sx[i] = INFINITY;
+        sv[i] = INT32_MAX;
+      }
       si[i] = (int16_t)i;
     }
     __syncthreads();
     for (int size = 2; size <= n; size <<= 1) {
       for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        // pair i compares lo and lo + stride, lo = i with a zero bit inserted at the
+        // stride's position (stride is a power of two)
         for (int i = threadIdx.x; i < (n >> 1); i += blockDim.x) {
-          const int lo = 2 * stride * (i / stride) + (i % stride), hi = lo + stride;
+          const int lo = ((i & ~(stride - 1)) << 1) | (i & (stride - 1)), hi = lo + stride;
           const bool up = (lo & size) == 0;
           const float xa = sx[lo], xb = sx[hi];
           const int va = sv[lo], vb = sv[hi];

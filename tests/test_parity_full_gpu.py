@@ -137,6 +137,31 @@ def test_jammed_corridors_bitexact(G, O):
     assert o.counters()["arrived"] > 0
 
 
+def _permute_trips(sc, perm):
+    """The same scenario with trip i renamed perm[i] (demand, routes, initial state)."""
+    inv = np.argsort(perm)
+    d = sc["demand"]
+    out = dict(sc, demand=S._demand(d["origin"][inv], d["dest"][inv], d["depart_step"][inv]))
+    off, links = sc["routes"]["offsets"], sc["routes"]["links"]
+    lens = np.diff(off)[inv]
+    noff = np.zeros(len(lens) + 1, np.int32)
+    noff[1:] = np.cumsum(lens)
+    nlinks = np.concatenate([links[off[i]:off[i + 1]] for i in inv]).astype(np.int32)
+    out["routes"] = dict(offsets=noff, links=nlinks)
+    out["init_state"] = {k: np.ascontiguousarray(v[inv]) for k, v in sc["init_state"].items()}
+    return out
+
+
+def test_jammed_corridors_random_slot_order_bitexact(G, O):
+    # trip ids shuffled against positions: the first occupancy rebuild sees long lane
+    # segments in random order (many runs), the later ones in the few-run order of the
+    # step kernels; both orders of the long-segment rank are exercised
+    sc = S.jammed_corridors(n_corr=4)
+    sc = _permute_trips(sc, np.random.default_rng(4).permutation(sc["demand"]["n_trips"]))
+    g, o = setup_pair(sc, G.Sim, O.OracleSim)
+    run_lockstep(g, o, 300, 50)
+
+
 def test_metro_full_size_routes_sampled(G, O):
     sc = S.metro()
     g = G.Sim(sc)
