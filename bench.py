@@ -62,7 +62,7 @@ PROFILED_STEP_TRAFFIC = None
 def kernel_source_sha():
     import hashlib
     h = hashlib.sha256()
-    for f in ("gbt_fused.cu", "gbt_stepdev.cuh", "gbt_internal.cuh"):
+    for f in ("gbt_fused.cu", "gbt_rebuild.cuh", "gbt_stepdev.cuh", "gbt_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1807_01148_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -563,6 +563,7 @@ def run_cuda(args):
     g.write_state(snap)
     g.step(args.warmup)
     c0 = g.counters()
+    n_launch0 = g.launch_count()
     barrier()
     clocks.mark("t0")
     ev0.record(stream)
@@ -573,7 +574,7 @@ def run_cuda(args):
     ms = ev0.elapsed_time(ev1)
     c1 = g.counters()
     veh_steps = c1["veh_steps"] - c0["veh_steps"]
-    kernels_per_step = G.n_kernels()
+    launches = g.launch_count() - n_launch0
     clk = clocks.stop()
 
     # -- per-kernel device times over the same K steps (events after every kernel),
@@ -733,7 +734,7 @@ def run_cuda(args):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk,
-        "gpu_launches": kernels_per_step * args.steps,
+        "gpu_launches": launches,
     }
     print(json.dumps(line), flush=True)
 

@@ -175,7 +175,8 @@ int sim_read_routes(sim_handle* h, int32_t* offsets, int32_t* links);
  * SIM_EINVAL when the horizon would pass 2^31 deciseconds of simulated time. */
 int sim_step(sim_handle* h, int32_t n_steps);
 
-/* Number of kernels in one step (see sim_kernel_name). */
+/* Size of sim_step_timed's kernel_ms array: at least the number of kernel groups of a
+ * step that sim_kernel_name names (the rest of the array stays zero). */
 #define SIM_N_KERNELS 8
 
 /* Advance n_steps like sim_step, but launch every kernel directly with a CUDA event
@@ -184,18 +185,25 @@ int sim_step(sim_handle* h, int32_t n_steps);
  * to sim_step.  For profiling; slower than sim_step's graph launch. */
 int sim_step_timed(sim_handle* h, int32_t n_steps, float* kernel_ms);
 
-/* Name of kernel k of a step (0 <= k < SIM_N_KERNELS), "" otherwise. */
+/* Name of kernel group k of a step (0 <= k < SIM_N_KERNELS), "" past the last group. */
 const char* sim_kernel_name(int32_t k);
+
+/* Kernel launches sim_step has made on this handle since its creation, into *launches:
+ * in graph execution the kernels of the captured step graph, per step; in persistent
+ * execution one cooperative launch per sim_step call.  (Launches of the other calls
+ * are not counted.)  Errors: SIM_EINVAL on a NULL argument. */
+int sim_launch_count(sim_handle* h, int64_t* launches);
 
 /* How sim_step runs the steps.  SIM_EXEC_GRAPH: one CUDA graph of the step's kernels
  * per step, grid = grid_per_sm x SMs blocks of 256 threads for the kernels that do not
- * size their own grid (the own-lane and decision kernels run one resident wave); the
- * own-lane kernel's waits for its shared-memory tiles are bounded by
+ * size their own grid (the chunk kernel runs one resident wave); the chunk kernel's
+ * waits for its staged chunks (bulk copies into shared memory) are bounded by
  * barrier_timeout_cycles SM cycles (<= 0: 2e9), after which sim_step returns
  * SIM_ETIMEOUT (the state is then undefined until the next sim_write_state /
  * sim_route, and stepping calls return SIM_ESTATE until then).  SIM_EXEC_PERSISTENT: all
  * n steps in one cooperative launch of blocks_per_sm x SMs blocks of `threads`
- * threads, the phases of a step separated by a grid barrier whose wait is bounded by
+ * threads (the same phases as the graph's kernels), the phases of a step separated by a
+ * grid barrier whose wait, like the chunk staging wait, is bounded by
  * barrier_timeout_cycles SM cycles (<= 0: 2e9, about a second); a wait that runs out
  * makes sim_step return SIM_ETIMEOUT (the state is then undefined until the next
  * sim_write_state / sim_route).  Every configuration gives identical results. */
@@ -206,7 +214,7 @@ typedef struct {
   int32_t blocks_per_sm;            /* persistent: 1 .. co-resident limit */
   int32_t grid_per_sm;              /* graph: 1 .. 64 */
   int64_t barrier_timeout_cycles;   /* persistent: bound of a barrier wait; graph: bound of a
-                                       tile wait of the own-lane kernel */
+                                       staging wait of the chunk kernel */
 } sim_exec;
 
 int sim_set_exec(sim_handle* h, const sim_exec* e);
@@ -214,7 +222,8 @@ int sim_get_exec(sim_handle* h, sim_exec* e);
 
 /* Pick the fastest execution configuration for this handle: time trial_steps steps
  * from the current state under every candidate (graph with 2/4/8/16 blocks per SM;
- * persistent with 256/512/1024 threads and 1..4 co-resident blocks per SM), restore
+ * persistent with 256/512/1024 threads and co-resident blocks per SM up to 1024
+ * threads per SM), restore
  * the state, and keep the best.  cache_path (or NULL): a JSON-lines file keyed by
  * device name, SM count and a hash of the network and demand sizes; a hit skips the
  * trials, a new result is appended.  *chosen (or NULL) receives the choice. */

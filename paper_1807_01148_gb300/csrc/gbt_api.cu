@@ -51,7 +51,8 @@ void launch_fw_final_time(const double* t0, const double* x, const double* cap, 
                           int n, cudaStream_t s);
 void launch_compact_routes(const int32_t* roff, const int32_t* rlen, const int32_t* src, const int32_t* new_off,
                            int32_t* dst, int n, cudaStream_t s);
-void chunk_setup(int blocks_per_sm[4]);
+void chunk_setup(int blocks_per_sm[8]);
+bool chunk_split_needed(const double* lane_m, int n_links, float vlen_min);
 size_t chunk_table_size(int n_trips);
 int persistent_max_blocks_per_sm(int threads);
 cudaError_t launch_persistent(const Dev& d, GridSync* gs, int blocks, int threads, int n_steps, long long limit,
@@ -94,6 +95,9 @@ struct sim_handle {
   // sizes
   int nn = 0, nl = 0, nt = 0, n_lanes = 0, ncls = 0;
   bool has_stop = false;
+  std::vector<double> lane_m;   // lanes x length per link (chunk_split_needed)
+  long long launches = 0;    // kernel launches made by sim_step (sim_launch_count)
+  size_t graph_nodes = 0, graph_samp_nodes = 0;   // kernels per step of the step graphs
   // host copies
   std::vector<int32_t> lfrom, lto, depart, origin, dest;
   std::vector<float> len, spd;
@@ -330,9 +334,9 @@ int create_from_flat(Flat& F, sim_handle** out) {
   h->d.wait_limit = kDefaultWaitCycles;
   {
     // one resident wave of chunk-taking blocks per variant of the chunk kernel
-    int bps[4];
+    int bps[8];
     chunk_setup(bps);
-    for (int v = 0; v < 4; v++) h->d.chunk_grid[v] = std::max(1, bps[v]) * h->sm_count;
+    for (int v = 0; v < 8; v++) h->d.chunk_grid[v] = std::max(1, bps[v]) * h->sm_count;
   }
 
   // in-links of every node in ascending link id -> round-robin index, in-degree
@@ -345,6 +349,7 @@ int create_from_flat(Flat& F, sim_handle** out) {
     }
   std::vector<LinkRec> recs(F.nl);
   h->lane_base.resize(F.nl + 1);
+  h->lane_m.resize(F.nl);
   int nlan = 0;
   for (int e = 0; e < F.nl; e++) {
     LinkRec& r = recs[e];
@@ -367,6 +372,7 @@ int create_from_flat(Flat& F, sim_handle** out) {
     r.sig_off = F.off[n];
     r.sig_grn = (uint16_t)(F.ctrl[n] == SIM_CTRL_SIGNAL ? F.grn[n] : 0);
     if (F.ctrl[n] == SIM_CTRL_STOP) h->has_stop = true;
+    h->lane_m[e] = (double)F.len[e] * (double)F.lanes[e];
   }
   h->lane_base[F.nl] = nlan;
   h->n_lanes = nlan;
@@ -429,6 +435,7 @@ int create_from_flat(Flat& F, sim_handle** out) {
     d.hdt2 = (0.5f * P.dt) * P.dt;
     d.vlen = P.veh_len;
     d.vlen_max = P.veh_len;
+    d.chunk_split = chunk_split_needed(h->lane_m.data(), F.nl, P.veh_len) ? 1 : 0;
     d.s_min = P.s_min;
     d.zone = 2.0f * P.veh_len;
     d.mp = P.mobil_p;
@@ -484,6 +491,7 @@ int create_from_flat(Flat& F, sim_handle** out) {
     TRY(dalloc(h, &d.cr, (size_t)nlan));
     TRY(dalloc(h, &d.chunks, chunk_table_size(F.nt)));
     TRY(dalloc(h, &d.long_list, (size_t)nlan));
+    TRY(dalloc(h, &d.big_chunks, chunk_table_size(F.nt)));
     {
       std::vector<int32_t> ll((size_t)nlan);
       for (int e = 0; e < F.nl; e++)
@@ -1115,11 +1123,13 @@ int sim_step(sim_handle* h, int32_t n_steps) {
     launch_step(dn, h->grid, h->has_stop, h->cap_stream);
     CK(cudaStreamEndCapture(h->cap_stream, &h->graph));
     CK(cudaGraphInstantiate(&h->gexec, h->graph, 0));
+    CK(cudaGraphGetNodes(h->graph, nullptr, &h->graph_nodes));
     if (h->d.acc_u) {
       CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
       launch_step(h->d, h->grid, h->has_stop, h->cap_stream);
       CK(cudaStreamEndCapture(h->cap_stream, &h->graph_samp));
       CK(cudaGraphInstantiate(&h->gexec_samp, h->graph_samp, 0));
+      CK(cudaGraphGetNodes(h->graph_samp, nullptr, &h->graph_samp_nodes));
     }
     h->graph_dirty = false;
   }
@@ -1157,11 +1167,13 @@ int sim_step(sim_handle* h, int32_t n_steps) {
     }
     if (h->pexec) CK(cudaGraphLaunch(h->pexec, h->stream));
     else CK(launch_persistent(h->d, h->gs, blocks, x.threads, n_steps, limit, h->stream));
+    h->launches += 1;
   } else {
     const long long every = h->d.acc_u ? h->d.samp_every : 0;
     for (int s = 0; s < n_steps; s++) {
       const bool samp = every > 0 && (t0 + s) % every == 0;
       CK(cudaGraphLaunch(samp ? h->gexec_samp : h->gexec, h->stream));
+      h->launches += (long long)(samp ? h->graph_samp_nodes : h->graph_nodes);
     }
   }
   return check_device(h);
@@ -1179,6 +1191,7 @@ int sim_set_exec(sim_handle* h, const sim_exec* e) {
   h->pgraph_n = -1;
     h->tape_graph_dirty = true;
   } else if (x.mode == SIM_EXEC_PERSISTENT) {
+    // the lane-start scan gives each block 2048 lanes, 8 to each of 256 threads
     if (x.threads != 256 && x.threads != 512 && x.threads != 1024)
       return fail(h, SIM_EINVAL, "persistent threads must be 256, 512 or 1024");
     const int mx = persistent_max_blocks_per_sm(x.threads);
@@ -1207,6 +1220,12 @@ int sim_step_timed(sim_handle* h, int32_t n_steps, float* kernel_ms) {
   if (int rc = check_horizon(h, n_steps)) return rc;
   CK(launch_steps_timed(h->d, h->grid, h->has_stop, h->stream, n_steps, kernel_ms));
   return check_device(h);
+}
+
+int sim_launch_count(sim_handle* h, int64_t* launches) {
+  if (!h || !launches) return SIM_EINVAL;
+  *launches = h->launches;
+  return SIM_OK;
 }
 
 const char* sim_kernel_name(int32_t k) { return (k >= 0 && k < kNumKernels) ? kKernelNames[k] : ""; }
@@ -1405,6 +1424,7 @@ int sim_set_vehicle_types(sim_handle* h, int32_t n_types, const sim_vehicle_type
   d.vty_len = d.vty_vmax = nullptr;
   d.n_vty = 0;
   d.vlen_max = d.vlen;
+  d.chunk_split = chunk_split_needed(h->lane_m.data(), h->nl, d.vlen) ? 1 : 0;
   h->vty_len.clear();
   h->vty_ascale.clear();
   h->vty_vmax.clear();
@@ -1431,6 +1451,8 @@ int sim_set_vehicle_types(sim_handle* h, int32_t n_types, const sim_vehicle_type
   d.vty_vmax = vm;
   d.n_vty = n_types;
   d.vlen_max = *std::max_element(h->vty_len.begin(), h->vty_len.end());
+  d.chunk_split =
+      chunk_split_needed(h->lane_m.data(), h->nl, *std::min_element(h->vty_len.begin(), h->vty_len.end())) ? 1 : 0;
   return upload_type_params(h);
 }
 
@@ -1734,7 +1756,7 @@ int sim_autotune(sim_handle* h, int32_t trial_steps, const char* cache_path, sim
   for (int g : {2, 4, 8, 16}) cand.push_back(sim_exec{SIM_EXEC_GRAPH, 256, 0, g, 0});
   for (int t : {256, 512, 1024}) {
     const int mx = persistent_max_blocks_per_sm(t);
-    for (int b = 1; b <= mx && b <= 4; b++) cand.push_back(sim_exec{SIM_EXEC_PERSISTENT, t, b, 8, 0});
+    for (int b = 1; b <= mx && b * t <= 1024; b++) cand.push_back(sim_exec{SIM_EXEC_PERSISTENT, t, b, 8, 0});
   }
   const CkptLayout CL = ckpt_layout(h);
   unsigned char* ck;

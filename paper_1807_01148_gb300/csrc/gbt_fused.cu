@@ -27,7 +27,7 @@
 // the bids of this step) and is written to the state at t+1 (A), so the result does not
 // depend on the order in which blocks run; ties are broken by vehicle id or by the
 // rotating round-robin rank exactly as in the oracle.
-#include "gbt_stepdev.cuh"
+#include "gbt_rebuild.cuh"
 
 namespace gbt {
 
@@ -60,19 +60,27 @@ constexpr uint8_t kFlagElig = 8;             // lane-change candidate (chunk-loc
 // Shared-memory layout of one staged chunk (dynamic shared memory, 16-byte aligned
 // arrays; the bulk copies start at a position rounded down to 16, lane starts at one
 // rounded down to 4).
-struct ChunkSmem {
-  float x[kChunkPad], v[kChunkPad];
-  int32_t vid[kChunkPad], g[kChunkPad], link[kChunkPad], nxt[kChunkPad], cur[kChunkPad];
-  float a[kChunkPad], at[kChunkPad], om[kChunkPad];
+template <int CAP>
+struct ChunkSmemT {
+  static constexpr int kCap = CAP, kPad = CAP + 32;
+  float x[kPad], v[kPad];
+  int32_t vid[kPad], g[kPad], link[kPad], nxt[kPad], cur[kPad];
+  float a[kPad], at[kPad], om[kPad];
   LinkRec lk[kChunkLinks];
   int32_t ls[kChunkLanes + 8];
   ClassPar cls[kChunkClasses];
-  uint8_t mv[kChunkPad], fl[kChunkPad];
-  int8_t it[kChunkPad];
-  int16_t list[kChunkCap];
+  uint8_t mv[kPad], fl[kPad];
+  int8_t it[kPad];
+  int16_t list[CAP];
   uint64_t bar;
 };
+using ChunkSmem = ChunkSmemT<kChunkCap>;
 constexpr size_t kChunkSmemBytes = sizeof(ChunkSmem);
+// Chunks beyond kChunkCap (a link with more vehicles than that, as in a long standing
+// queue) go to a second launch that stages up to kBigCap positions per block.
+constexpr int kBigCap = 2048, kBigThreads = 256;
+using ChunkSmemBig = ChunkSmemT<kBigCap>;
+constexpr size_t kBigSmemBytes = sizeof(ChunkSmemBig);
 
 // The arrays of a chunk, indexed by position - c0: staged copies in shared memory, or
 // B and the per-position scratch in global memory for an oversized chunk; plus the
@@ -157,10 +165,10 @@ __device__ __forceinline__ int chunk_cut(const Dev& d, int b, int nB) {
 // behind the rearmost vehicle of the mapped lane of the next link or the stop line,
 // and a bid for the target lane when the move reaches the end and lands behind that
 // vehicle.
+// split: chunks beyond kChunkCap go to the big-chunk launch (their entry in the chunk
+// table is left empty, their record goes to the big-chunk list).
 template <bool TYPES>
-__global__ void __launch_bounds__(256) k_front(Dev d) {
-  griddep_wait();
-  if (step_timed_out(d)) return;
+__device__ __forceinline__ void ph_front(const Dev& d, bool split) {
   const int t = (int)d.ctl->t;
   const unsigned ep = d.ctl->occ_epoch;
   GRID_STRIDE(g, d.n_lanes) {
@@ -217,8 +225,19 @@ __global__ void __launch_bounds__(256) k_front(Dev d) {
       const LinkRec& Lh = d.links[c.e_hi];
       c.g_hi = Lh.lane_base + Lh.lanes;
     }
+    if (split && c.c1 - c.c0 > kChunkCap) {
+      d.big_chunks[atomicAdd(&d.ctl->n_big, 1)] = c;
+      c.c1 = c.c0;
+    }
     d.chunks[k] = c;
   }
+}
+
+template <bool TYPES>
+__global__ void __launch_bounds__(256) k_front(Dev d) {
+  griddep_wait();
+  if (step_timed_out(d)) return;
+  ph_front<TYPES>(d, d.chunk_split != 0);
 }
 
 // ------------------------------------------------------------------ chunks
@@ -536,12 +555,14 @@ __device__ __forceinline__ void chunk_step(const Dev& d, const ChunkView& V, int
   __syncthreads();   // the chunk's staged arrays are read before the next chunk refills them
 }
 
-template <bool OUT, bool TYPES>
-__global__ void __launch_bounds__(kChunkThreads, kChunkMinBlocks) k_chunk(Dev d) {
-  griddep_wait();
-  if (step_timed_out(d)) return;
-  extern __shared__ __align__(16) unsigned char chunk_smem[];
-  ChunkSmem& S = *reinterpret_cast<ChunkSmem*>(chunk_smem);
+// Which chunks a launch takes.  BIG = false: every chunk of the chunk table from the
+// atomic counter (one beyond kChunkCap on global memory), then the departures.  BIG =
+// true: the chunks the lane-front phase moved to the big-chunk list, by index, and no
+// departures.  S: the block's staging area (dynamic shared memory).  Returns early
+// (error word set) when a staging wait runs out.
+template <bool OUT, bool TYPES, bool BIG, typename SMT>
+__device__ __forceinline__ void ph_chunk(const Dev& d, SMT& S) {
+  constexpr int CAP = SMT::kCap;
   // the chunk being processed and the next one (taken by thread 0 while the current
   // chunk's copies are in flight), alternating between two slots
   __shared__ int s_k[2], s_cnt;
@@ -556,29 +577,38 @@ __global__ void __launch_bounds__(kChunkThreads, kChunkMinBlocks) k_chunk(Dev d)
   if (threadIdx.x == 0) {
     mbar_init(&S.bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    const int k = atomicAdd(&d.ctl->chunk_next, 1);
-    s_k[0] = k;
-    if (k < n_chunks) s_info[0] = d.chunks[k];
+    if (!BIG) {
+      const int k = atomicAdd(&d.ctl->chunk_next, 1);
+      s_k[0] = k;
+      if (k < n_chunks) s_info[0] = d.chunks[k];
+    }
   }
   __syncthreads();
-  int slot = 0;
+  int slot = 0, kb = blockIdx.x;
   uint32_t phase = 0;
   for (;;) {
-    const int k = s_k[slot];
-    if (k >= n_chunks) break;
-    const ChunkInfo c = s_info[slot];
-    const int c0 = c.c0, n = c.c1 - c.c0;
-    slot ^= 1;
-    if (n <= 0) {
-      if (threadIdx.x == 0) {
-        const int k2 = atomicAdd(&d.ctl->chunk_next, 1);
-        s_k[slot] = k2;
-        if (k2 < n_chunks) s_info[slot] = d.chunks[k2];
+    ChunkInfo c;
+    if (BIG) {   // the chunks the front phase listed as oversized
+      if (kb >= d.ctl->n_big) break;
+      c = d.big_chunks[kb];
+      kb += gridDim.x;
+    } else {
+      const int k = s_k[slot];
+      if (k >= n_chunks) break;
+      c = s_info[slot];
+      slot ^= 1;
+      if (c.c1 - c.c0 <= 0) {   // empty, or left to the big-chunk launch
+        if (threadIdx.x == 0) {
+          const int k2 = atomicAdd(&d.ctl->chunk_next, 1);
+          s_k[slot] = k2;
+          if (k2 < n_chunks) s_info[slot] = d.chunks[k2];
+        }
+        __syncthreads();
+        continue;
       }
-      __syncthreads();
-      continue;
     }
-    const bool fast = n <= kChunkCap;
+    const int c0 = c.c0, n = c.c1 - c.c0;
+    const bool fast = n <= CAP;
     const int nlk = fast && c.e_hi - c.e_lo < kChunkLinks ? c.e_hi - c.e_lo + 1 : 0;
     const int g_la = c.g_lo & ~3;
     const int nls_a = ((c.g_hi + 1 - g_la) + 3) & ~3;   // lane starts g_la .. g_hi, a multiple of 4
@@ -607,9 +637,11 @@ __global__ void __launch_bounds__(kChunkThreads, kChunkMinBlocks) k_chunk(Dev d)
         if (nls) bulk_g2s(S.ls, d.lane_start + g_la, (uint32_t)nls * 4, &S.bar);
       }
       // the next chunk, into the other slot (read after this chunk's last barrier)
-      const int k2 = atomicAdd(&d.ctl->chunk_next, 1);
-      s_k[slot] = k2;
-      if (k2 < n_chunks) s_info[slot] = d.chunks[k2];
+      if (!BIG) {
+        const int k2 = atomicAdd(&d.ctl->chunk_next, 1);
+        s_k[slot] = k2;
+        if (k2 < n_chunks) s_info[slot] = d.chunks[k2];
+      }
     }
     if (fast) {
       const bool ok = mbar_wait(&S.bar, phase, d.wait_limit);
@@ -639,7 +671,118 @@ __global__ void __launch_bounds__(kChunkThreads, kChunkMinBlocks) k_chunk(Dev d)
   }
   // departures (appended after the sorted vehicles; they read only state of step t and
   // this step's admission bids, complete since k_front)
-  if (d.n_qlinks > 0) ph_insert<OUT, TYPES>(d);
+  if (!BIG && d.n_qlinks > 0) ph_insert<OUT, TYPES>(d);
+}
+
+template <bool OUT, bool TYPES>
+__global__ void __launch_bounds__(kChunkThreads, kChunkMinBlocks) k_chunk(Dev d) {
+  griddep_wait();
+  if (step_timed_out(d)) return;
+  extern __shared__ __align__(16) unsigned char chunk_smem[];
+  ph_chunk<OUT, TYPES, false>(d, *reinterpret_cast<ChunkSmem*>(chunk_smem));
+}
+
+// The chunks beyond kChunkCap (launched after the chunk kernel when chunk_split).
+template <bool OUT, bool TYPES>
+__global__ void __launch_bounds__(kBigThreads, 2) k_chunk_big(Dev d) {
+  griddep_wait();
+  if (step_timed_out(d)) return;
+  extern __shared__ __align__(16) unsigned char chunk_smem[];
+  ph_chunk<OUT, TYPES, true>(d, *reinterpret_cast<ChunkSmemBig*>(chunk_smem));
+}
+
+// ------------------------------------------------------------------ persistent step
+// All phases of n steps in one cooperative launch (the rebuild, the lane fronts, the
+// chunks with the departures, the counters): every block runs each phase's share,
+// then waits at a grid barrier.  The barrier's wait is bounded:
+// after `limit` SM cycles (about a second by default) a block sets kErrTimeout in the
+// error word and leaves; every waiting block also leaves as soon as it sees the flag,
+// so the launch always ends and the host reports SIM_ETIMEOUT.
+__device__ __forceinline__ bool grid_barrier(GridSync* gs, int* err, long long limit) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned* vgen = &gs->gen;
+    volatile int* verr = err;
+    const unsigned g = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&gs->count, 1u);
+    if (arrived == gridDim.x - 1) {
+      gs->count = 0;
+      __threadfence();
+      atomicAdd(&gs->gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == g) {
+        if ((*verr & kErrTimeout) || clock64() - t0 > limit) {
+          atomicOr(err, kErrTimeout);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    if (*verr & kErrTimeout) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <bool OUT, bool TYPES>
+__device__ __forceinline__ void persistent_steps(const Dev& d, GridSync* gs, int n_steps, long long limit,
+                                                 ChunkSmem& S) {
+  int* err = &d.ctl->err;
+  for (int step = 0; step < n_steps; step++) {
+    // the previous step's counter update (block 0) needs no barrier of its own: nothing
+    // before this step's scatter reads what it writes
+    ph_scan_sum(d);
+    if (!grid_barrier(gs, err, limit)) return;
+    ph_scan_fin(d);
+    if (!grid_barrier(gs, err, limit)) return;
+    ph_scatter(d);
+    if (!grid_barrier(gs, err, limit)) return;
+    ph_rank<false>(d);
+    if (!grid_barrier(gs, err, limit)) return;
+    // the edge sample and the lane fronts read the sorted state and write disjoint arrays
+    if (d.acc_u) ph_edge_sample(d);
+    ph_front<TYPES>(d, false);   // every chunk stays in the table
+    if (!grid_barrier(gs, err, limit)) return;
+    ph_chunk<OUT, TYPES, false>(d, S);
+    if (!grid_barrier(gs, err, limit)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ph_finish(d);
+  }
+  // the last counter update is visible when the launch ends
+}
+
+__global__ void __launch_bounds__(1024, 1) k_persistent(Dev d, GridSync* gs, int n_steps, long long limit) {
+  extern __shared__ __align__(16) unsigned char chunk_smem[];
+  ChunkSmem& S = *reinterpret_cast<ChunkSmem*>(chunk_smem);
+  const bool out = d.emis || d.tt_sum;
+  if (d.vtype) {
+    if (out) persistent_steps<true, true>(d, gs, n_steps, limit, S);
+    else persistent_steps<false, true>(d, gs, n_steps, limit, S);
+  } else {
+    if (out) persistent_steps<true, false>(d, gs, n_steps, limit, S);
+    else persistent_steps<false, false>(d, gs, n_steps, limit, S);
+  }
+}
+
+// Largest co-resident grid of the persistent kernel for a block size (0 if none).
+int persistent_max_blocks_per_sm(int threads) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent, threads, kChunkSmemBytes) != cudaSuccess)
+    return 0;
+  return nb;
+}
+
+cudaError_t launch_persistent(const Dev& d, GridSync* gs, int blocks, int threads, int n_steps, long long limit,
+                              cudaStream_t s) {
+  Dev dd = d;
+  void* args[] = {&dd, &gs, &n_steps, &limit};
+  return cudaLaunchCooperativeKernel((const void*)k_persistent, dim3(blocks), dim3(threads), args, kChunkSmemBytes,
+                                     s);
 }
 
 // ------------------------------------------------------------------ launch
@@ -654,16 +797,31 @@ static int chunk_blocks(K kern) {
   return nb;
 }
 
+template <typename K>
+static int chunk_big_blocks(K kern) {
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBigSmemBytes) != cudaSuccess ||
+      cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
+          cudaSuccess)
+    return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kBigThreads, kBigSmemBytes) != cudaSuccess) return 0;
+  return nb;
+}
+
 // Entries of the chunk table for up to n_trips vehicles.
 size_t chunk_table_size(int n_trips) { return (size_t)n_trips / kChunkT + 2; }
 
 // Resident blocks per SM of the chunk kernel (plain / outputs x vehicle types); also
 // raises the kernels' dynamic shared-memory limit.  Called once per handle.
-void chunk_setup(int blocks_per_sm[4]) {
+void chunk_setup(int blocks_per_sm[8]) {
   blocks_per_sm[0] = chunk_blocks(k_chunk<false, false>);
   blocks_per_sm[1] = chunk_blocks(k_chunk<true, false>);
   blocks_per_sm[2] = chunk_blocks(k_chunk<false, true>);
   blocks_per_sm[3] = chunk_blocks(k_chunk<true, true>);
+  blocks_per_sm[4] = chunk_big_blocks(k_chunk_big<false, false>);
+  blocks_per_sm[5] = chunk_big_blocks(k_chunk_big<true, false>);
+  blocks_per_sm[6] = chunk_big_blocks(k_chunk_big<false, true>);
+  blocks_per_sm[7] = chunk_big_blocks(k_chunk_big<true, true>);
 }
 
 template <typename... KArgs, typename... Args>
@@ -686,16 +844,39 @@ void launch_front(const Dev& d, int grid, cudaStream_t s) {
   else launch_pdl2(k_front<false>, grid, 256, 0, s, d);
 }
 
+template <bool OUT, bool TYPES>
+static void launch_chunk_v(const Dev& d, int v, cudaStream_t s) {
+  launch_pdl2(k_chunk<OUT, TYPES>, d.chunk_grid[v], kChunkThreads, kChunkSmemBytes, s, d);
+  if (d.chunk_split) launch_pdl2(k_chunk_big<OUT, TYPES>, d.chunk_grid[4 + v], kBigThreads, kBigSmemBytes, s, d);
+}
+
+// The chunk kernel, and the big-chunk kernel when the network has links that can hold
+// more than kChunkCap vehicles (chunk_split; otherwise an oversized chunk, should one
+// ever form, runs on global memory inside the chunk kernel: the same results either way).
 void launch_chunk(const Dev& d, cudaStream_t s) {
   const bool out = d.emis || d.tt_sum;
   const int v = (out ? 1 : 0) + (d.vtype ? 2 : 0);
-  const int grid = d.chunk_grid[v];
   switch (v) {
-    case 0: launch_pdl2(k_chunk<false, false>, grid, kChunkThreads, kChunkSmemBytes, s, d); break;
-    case 1: launch_pdl2(k_chunk<true, false>, grid, kChunkThreads, kChunkSmemBytes, s, d); break;
-    case 2: launch_pdl2(k_chunk<false, true>, grid, kChunkThreads, kChunkSmemBytes, s, d); break;
-    default: launch_pdl2(k_chunk<true, true>, grid, kChunkThreads, kChunkSmemBytes, s, d); break;
+    case 0: launch_chunk_v<false, false>(d, v, s); break;
+    case 1: launch_chunk_v<true, false>(d, v, s); break;
+    case 2: launch_chunk_v<false, true>(d, v, s); break;
+    default: launch_chunk_v<true, true>(d, v, s); break;
   }
+}
+
+// Whether the big-chunk launch is worth its place in the step: at least a quarter of
+// the network's lane-metres lie on links that hold more than kChunkCap vehicles when
+// their lanes are packed bumper to bumper with the shortest vehicle (lane_m[e]: lanes x
+// length of link e).  Where such links are rare, their chunks run on global memory
+// inside the chunk kernel, overlapped with the others, which costs less than a launch.
+bool chunk_split_needed(const double* lane_m, int n_links, float vlen_min) {
+  if (!(vlen_min > 0.0f)) return false;
+  double all = 0.0, big = 0.0;
+  for (int e = 0; e < n_links; e++) {
+    all += lane_m[e];
+    if (lane_m[e] / (double)vlen_min > (double)kChunkCap) big += lane_m[e];
+  }
+  return big >= 0.25 * all && big > 0.0;
 }
 
 }  // namespace gbt

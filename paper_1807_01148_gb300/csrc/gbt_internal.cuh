@@ -117,6 +117,7 @@ struct Ctl {
   int n_elig;      // lane-change candidates listed this step
   int chunk_next;  // next chunk of the fused step kernel to take
   int n_long;      // long lane segments listed by the lane-start scan
+  int n_big;       // chunks beyond the chunk kernel's staging capacity (lane-front phase)
 };
 
 // Forms of Eq. 7 an acceleration can come from (adjoint tape).
@@ -189,6 +190,7 @@ struct Dev {
   CrossRec* cr;               // per lane: the bidding front's state after crossing
   ChunkInfo* chunks;          // chunks of the fused step kernel (this step's)
   int32_t* long_list;         // lanes with long segments (sorted by a block each)
+  ChunkInfo* big_chunks;       // chunks beyond the chunk kernel's staging capacity
   int32_t* elig;              // sorted positions of this step's lane-change candidates
   TapeRec* tape;              // adjoint tape of the current segment (nullptr: not taping)
   TapeForm* tform;            // lane-change forms of the current step (taping only)
@@ -224,7 +226,9 @@ struct Dev {
   int32_t* q_head;
   const int32_t* q_items;
   Ctl* ctl;
-  int chunk_grid[4];               // blocks of the chunk kernel (plain, outputs, types, both)
+  int chunk_split;                 // oversized chunks go to the big-chunk launch
+  int chunk_grid[8];               // blocks of the chunk kernel (plain, outputs, types, both), then of
+                                   // the big-chunk kernel (same order)
   long long wait_limit;            // SM cycles a staging wait of the chunk kernel may take
 };
 

@@ -25,7 +25,8 @@ EXPORTS = ["sim_create", "sim_create_batch", "sim_set_stream", "sim_route", "sim
            "sim_counters", "sim_last_error", "sim_destroy", "sim_set_class_params", "sim_observe", "sim_adjoint",
            "sim_set_exec", "sim_get_exec", "sim_autotune", "sim_set_outputs", "sim_reset_outputs",
            "sim_read_emissions", "sim_read_link_times", "sim_read_edge_samples", "sim_measured_costs",
-           "sim_reroute", "sim_equilibrium", "sim_assign_static", "sim_set_vehicle_types", "sim_loss"]
+           "sim_reroute", "sim_equilibrium", "sim_assign_static", "sim_set_vehicle_types", "sim_loss",
+           "sim_launch_count"]
 OUT_EMISSIONS, OUT_LINK_TIMES, OUT_EDGE_SAMPLES = 1, 2, 4
 SIM_EXEC_GRAPH, SIM_EXEC_PERSISTENT = 0, 1
 
@@ -123,6 +124,7 @@ def lib(path: str | None = None):
         L.sim_step_timed.argtypes = [vp, i32, vp]
         L.sim_kernel_name.argtypes = [i32]
         L.sim_kernel_name.restype = C.c_char_p
+        L.sim_launch_count.argtypes = [vp, C.POINTER(i64)]
         L.sim_read_state.argtypes = [vp, C.POINTER(sim_state_view), C.c_uint32, C.c_int]
         L.sim_write_state.argtypes = [vp] * 7
         L.sim_occupancy.argtypes = [vp, vp, vp]
@@ -430,6 +432,12 @@ class Sim:
         obj = np.zeros(max_iter + 1, np.float64)
         self._check(lib().sim_assign_static(self.h, C.byref(spec), _p(flow), _p(time), _p(gap), _p(step), _p(obj)))
         return dict(flow=flow, time=time, gap=gap[:max_iter], step=step[:max_iter], objective=obj)
+
+    def launch_count(self):
+        """Kernel launches sim_step has made on this handle (sim_launch_count)."""
+        n = C.c_int64()
+        self._check(lib().sim_launch_count(self.h, C.byref(n)))
+        return int(n.value)
 
     def counters(self):
         c = sim_counters_t()

@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 CONFIGS = [dict(mode=0, grid_per_sm=2), dict(mode=0, grid_per_sm=16), dict(mode=1, threads=256, blocks_per_sm=1),
            dict(mode=1, threads=256, blocks_per_sm=2), dict(mode=1, threads=512, blocks_per_sm=1),
-           dict(mode=1, threads=1024, blocks_per_sm=1)]
+           dict(mode=1, threads=1024, blocks_per_sm=1), dict(mode=1, threads=256, blocks_per_sm=4)]
 
 
 @pytest.fixture(scope="module")
@@ -75,6 +75,30 @@ def test_autotune_choice_and_cache(G, tmp_path):
     assert len(open(cache).readlines()) == 1
 
 
+def test_launch_count(G):
+    # graph execution: the kernels of the step graph per step (two scan kernels, scatter,
+    # rank, long segments, lane fronts, chunks, counters; plus the big-chunk kernel where
+    # most of the road lies on links that hold more vehicles than a staged chunk);
+    # persistent execution: one launch per sim_step call
+    g = G.Sim(S.small_grid(n=5, n_trips=200, steps=200))
+    g.route()
+    n0 = g.launch_count()
+    g.step(10)
+    assert g.launch_count() - n0 == 10 * 8
+    jam = S.jammed_corridors(n_corr=2)
+    j = G.Sim(jam)
+    j.set_routes(jam["routes"]["offsets"], jam["routes"]["links"])
+    j.write_state(jam["init_state"])
+    n0 = j.launch_count()
+    j.step(4)
+    assert j.launch_count() - n0 == 4 * 9
+    g.set_exec(mode=1, threads=256, blocks_per_sm=1)
+    n0 = g.launch_count()
+    g.step(10)
+    g.step(5)
+    assert g.launch_count() - n0 == 2
+
+
 def test_barrier_timeout_returns_error_and_handle_recovers(G):
     sc = S.small_grid(n=6, n_trips=400, steps=300)
     g = G.Sim(sc)
@@ -97,10 +121,10 @@ def test_barrier_timeout_returns_error_and_handle_recovers(G):
 
 
 def test_tile_wait_timeout_returns_error_and_handle_recovers(G):
-    # graph execution with a one-cycle bound on the own-lane kernel's waits for its
-    # bulk-copied tiles: the first wait runs out while the copy is in flight, the kernel
-    # reports it and returns after its copies have landed; the handle is usable again
-    # after the state is reset
+    # graph execution with a one-cycle bound on the chunk kernel's waits for its
+    # bulk-copied chunks: the first wait runs out while the copy is in flight, the kernel
+    # reports it and returns after its copies have landed, every later kernel of the
+    # step returns at entry; the handle is usable again after the state is reset
     sc = S.small_grid(n=6, n_trips=400, steps=300)
     g = G.Sim(sc)
     g.route()

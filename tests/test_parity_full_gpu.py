@@ -137,6 +137,18 @@ def test_jammed_corridors_bitexact(G, O):
     assert o.counters()["arrived"] > 0
 
 
+def test_jammed_corridors_persistent_bitexact(G, O):
+    # the persistent launch stages no chunk beyond the chunk kernel's capacity: the
+    # queued links (each more than 512 vehicles) run on global memory there, and the
+    # lane starts come from the two-phase scan between grid barriers
+    sc = S.jammed_corridors(n_corr=3)
+    g, o = setup_pair(sc, G.Sim, O.OracleSim)
+    g.set_exec(mode=1, threads=256, blocks_per_sm=2)
+    lg, _ = g.occupancy()
+    assert np.diff(lg).max() >= 280
+    run_lockstep(g, o, 300, 100)
+
+
 def _permute_trips(sc, perm):
     """The same scenario with trip i renamed perm[i] (demand, routes, initial state)."""
     inv = np.argsort(perm)
