@@ -55,8 +55,8 @@ IMPL_BYTES = {
 # DRAM bytes (read + write) per active vehicle per launch of the plain step kernel
 # (front + chunk), from the ncu capture summarised under profiles/, valid only for the
 # kernel sources it was taken on.
-PROFILED_SRC_SHA = None
-PROFILED_STEP_TRAFFIC = None
+PROFILED_SRC_SHA = "348ebc9644bba0b5"
+PROFILED_STEP_TRAFFIC = 149.1   # k_front 67.5 + k_chunk 81.6 B per active vehicle (987,466 vehicles)
 
 
 def kernel_source_sha():
@@ -281,12 +281,14 @@ def measure_batched(G, S, torch, steps):
     b = G.Sim.batch(scs)
     b.set_stream(stream.cuda_stream)
     b.route()
-    # block shape / execution mode picked by the autotuner on warm-up steps of a copy
+    # block shape / execution mode picked by the autotuner on a copy advanced to the middle
+    # of the run (the early steps, with few vehicles, favour the persistent launch; the
+    # busy ones the graph)
     tune = G.Sim.batch(scs)
     tune.set_stream(stream.cuda_stream)
     tune.route()
-    tune.step(600)
-    choice = tune.autotune(trial_steps=50)
+    tune.step(steps // 2)
+    choice = tune.autotune(trial_steps=100)
     tune.close()
     # both execution modes over the whole run, the autotuner's pick for the headline
     modes = {}

@@ -223,8 +223,10 @@ int sim_get_exec(sim_handle* h, sim_exec* e);
 /* Pick the fastest execution configuration for this handle: time trial_steps steps
  * from the current state under every candidate (graph with 2/4/8/16 blocks per SM;
  * persistent with 256/512/1024 threads and co-resident blocks per SM up to 1024
- * threads per SM), restore
- * the state, and keep the best.  cache_path (or NULL): a JSON-lines file keyed by
+ * threads per SM), each after an untimed run of the same length from the same state
+ * (which builds its launch graphs), restore the state, and keep the best.  The choice
+ * holds for states like the current one: few vehicles favour the persistent launch,
+ * many the graph.  cache_path (or NULL): a JSON-lines file keyed by
  * device name, SM count and a hash of the network and demand sizes; a hit skips the
  * trials, a new result is appended.  *chosen (or NULL) receives the choice. */
 int sim_autotune(sim_handle* h, int32_t trial_steps, const char* cache_path, sim_exec* chosen);

@@ -642,6 +642,8 @@ int reset_dynamic(sim_handle* h) {
   CK(cudaMemsetAsync(d.best, 0xFF, (size_t)h->n_lanes * 8, h->stream));
   CK(cudaMemsetAsync(d.cnt, 0, (size_t)h->n_lanes * 4, h->stream));
   CK(cudaMemsetAsync(d.ctl, 0, sizeof(Ctl), h->stream));
+  // a persistent launch that timed out left its barrier counts behind
+  CK(cudaMemsetAsync(h->gs, 0, sizeof(GridSync), h->stream));
   return clear_outputs(h, 0);
 }
 
@@ -1773,7 +1775,7 @@ int sim_autotune(sim_handle* h, int32_t trial_steps, const char* cache_path, sim
     if (sim_set_exec(h, &c) != SIM_OK) continue;
     err = ckpt_copy(h, ck, false);
     if (err != cudaSuccess) break;
-    if ((rc = sim_step(h, 1))) break;   // warm-up (builds the graph)
+    if ((rc = sim_step(h, trial_steps))) break;   // warm-up (builds the graphs of this step count)
     err = ckpt_copy(h, ck, false);
     if (err != cudaSuccess) break;
     cudaEventRecord(e0, h->stream);

@@ -28,8 +28,8 @@ constexpr int kErrLane = 1, kErrLink = 2, kErrSlot = 4, kErrRoute = 8, kErrUnrea
 
 // Grid barrier of the persistent step kernel (one per handle, in device memory).
 struct GridSync {
-  unsigned count;
-  unsigned gen;
+  alignas(128) unsigned count;   // arrivals (atomics)
+  alignas(128) unsigned gen;     // generation (polled): a line of its own
 };
 
 // Per-link record, 32 bytes: everything a vehicle step needs about its link and
