@@ -293,7 +293,7 @@ def measure_batched(G, S, torch, steps):
     # both execution modes over the whole run, the autotuner's pick for the headline
     modes = {}
     for name, ex in (("graph", dict(mode=0, grid_per_sm=8)),
-                     ("persistent", choice if choice["mode"] == 1 else dict(mode=1, threads=512, blocks_per_sm=2))):
+                     ("persistent", choice if choice["mode"] == 1 else dict(mode=1, threads=256, blocks_per_sm=4))):
         m = G.Sim.batch(scs)
         m.set_stream(stream.cuda_stream)
         m.route()

@@ -52,6 +52,7 @@ void launch_fw_final_time(const double* t0, const double* x, const double* cap, 
 void launch_compact_routes(const int32_t* roff, const int32_t* rlen, const int32_t* src, const int32_t* new_off,
                            int32_t* dst, int n, cudaStream_t s);
 void chunk_setup(int blocks_per_sm[8]);
+void front_setup(int blocks_per_sm[2]);
 bool chunk_split_needed(const double* lane_m, int n_links, float vlen_min);
 size_t chunk_table_size(int n_trips);
 int persistent_max_blocks_per_sm(int threads);
@@ -337,6 +338,9 @@ int create_from_flat(Flat& F, sim_handle** out) {
     int bps[8];
     chunk_setup(bps);
     for (int v = 0; v < 8; v++) h->d.chunk_grid[v] = std::max(1, bps[v]) * h->sm_count;
+    int fbs[2];
+    front_setup(fbs);
+    for (int v = 0; v < 2; v++) h->d.front_grid[v] = std::max(1, fbs[v]) * h->sm_count;
   }
 
   // in-links of every node in ascending link id -> round-robin index, in-degree

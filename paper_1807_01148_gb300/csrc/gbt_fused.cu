@@ -839,9 +839,18 @@ static void launch_pdl2(void (*kern)(KArgs...), int grid, int block, size_t smem
   cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-void launch_front(const Dev& d, int grid, cudaStream_t s) {
-  if (d.vtype) launch_pdl2(k_front<true>, grid, 256, 0, s, d);
-  else launch_pdl2(k_front<false>, grid, 256, 0, s, d);
+// Resident 256-thread blocks per SM of the lane-front kernel (without / with vehicle
+// types): its grid is one resident wave, every thread taking lanes in a grid stride (a
+// partial second wave of blocks would take as long as the first).
+void front_setup(int blocks_per_sm[2]) {
+  blocks_per_sm[0] = blocks_per_sm[1] = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[0], k_front<false>, 256, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[1], k_front<true>, 256, 0);
+}
+
+void launch_front(const Dev& d, cudaStream_t s) {
+  if (d.vtype) launch_pdl2(k_front<true>, d.front_grid[1], 256, 0, s, d);
+  else launch_pdl2(k_front<false>, d.front_grid[0], 256, 0, s, d);
 }
 
 template <bool OUT, bool TYPES>

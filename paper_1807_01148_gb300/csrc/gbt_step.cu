@@ -654,7 +654,7 @@ void launch_occupancy(const Dev& d, int grid, cudaStream_t s) {
 const char* const kKernelNames[kNumKernels] = {"scan_sum", "scan_fin", "scatter", "rank", "front", "chunk",
                                                "finish"};
 
-void launch_front(const Dev& d, int grid, cudaStream_t s);
+void launch_front(const Dev& d, cudaStream_t s);
 void launch_chunk(const Dev& d, cudaStream_t s);
 
 bool kernel_enabled(int k, const Dev& d, bool has_stop) {
@@ -679,7 +679,7 @@ void launch_kernel(int k, const Dev& d, int grid, cudaStream_t s) {
       // is counted with the fronts'
       if (d.acc_u) launch_pdl(k_edge_sample, grid, 256, s, d);
       if (d.tape) launch_pdl(k_own<true, false>, grid, 256, s, d);
-      else launch_front(d, grid, s);
+      else launch_front(d, s);
       break;
     case kKChunk:
       if (d.tape) {
