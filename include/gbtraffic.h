@@ -235,7 +235,11 @@ int sim_autotune(sim_handle* h, int32_t trial_steps, const char* cache_path, sim
  * pointers are device pointers (e.g. from torch tensors) of n_trips elements each;
  * on_device = 0: host pointers (pinned host memory copies fastest); the first host read
  * of a field allocates a device staging buffer of n_trips elements that the handle keeps
- * until sim_destroy.  The call synchronises the stream. */
+ * until sim_destroy.  Both synchronise the stream before returning.  on_device = 2:
+ * device pointers as for 1, but the gather is only enqueued on the handle's stream
+ * (sim_set_stream) and the call returns at once: the buffers hold the state once that
+ * stream reaches this point, and must not be reused before (order other streams after
+ * an event recorded on it).  Other values: SIM_EINVAL. */
 int sim_read_state(sim_handle* h, const sim_state_view* out, uint32_t fields, int on_device);
 
 /* Replace the vehicle state (resume, tests).  Host arrays [n_trips]: status,

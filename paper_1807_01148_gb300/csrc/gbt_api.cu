@@ -1238,7 +1238,7 @@ const char* sim_kernel_name(int32_t k) { return (k >= 0 && k < kNumKernels) ? kK
 
 int sim_read_state(sim_handle* h, const sim_state_view* out, uint32_t fields, int on_device) {
   NvtxRange nvtx_("sim_read_state");
-  if (!h || !out) return SIM_EINVAL;
+  if (!h || !out || on_device < 0 || on_device > 2) return SIM_EINVAL;
   const size_t nt = (size_t)h->nt;
   void* ptr[9] = {out->status, out->link, out->lane, out->cursor, out->x, out->v,
                   out->insert_step, out->arrive_step, out->lane_change};
@@ -1268,6 +1268,11 @@ int sim_read_state(sim_handle* h, const sim_state_view* out, uint32_t fields, in
   if (!on_device)
     for (int f = 0; f < 9 && e == cudaSuccess; f++)
       if (dptr[f] && nt) e = cudaMemcpyAsync(ptr[f], dptr[f], nt * esz[f], cudaMemcpyDeviceToHost, h->stream);
+  if (on_device == 2) {   // enqueued only
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "read_state");
+    return SIM_OK;
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "read_state");
   return SIM_OK;

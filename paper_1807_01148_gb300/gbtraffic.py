@@ -304,11 +304,12 @@ class Sim:
         self._check(lib().sim_read_state(self.h, C.byref(view), fields, 0))
         return {k: out[k] for i, k in enumerate(names) if (fields >> i) & 1}
 
-    def state_device(self, tensors: dict, fields: int):
-        """Read fields into caller-owned device buffers (e.g. torch CUDA tensors)."""
+    def state_device(self, tensors: dict, fields: int, wait: bool = True):
+        """Read fields into caller-owned device buffers (e.g. torch CUDA tensors).  wait
+        False: only enqueued on the handle's stream (sim_read_state mode 2)."""
         names = ("status", "link", "lane", "cursor", "x", "v", "insert_step", "arrive_step", "lane_change")
         view = sim_state_view(*[tensors[k].data_ptr() if (fields >> i) & 1 else None for i, k in enumerate(names)])
-        self._check(lib().sim_read_state(self.h, C.byref(view), fields, 1))
+        self._check(lib().sim_read_state(self.h, C.byref(view), fields, 1 if wait else 2))
 
     def write_state(self, st):
         self._check(lib().sim_write_state(

@@ -52,6 +52,13 @@ def test_host_device_and_partial_reads_agree():
         torch.cuda.synchronize()
         for k in NAMES:
             assert np.array_equal(_bits(tens[k].cpu().numpy()), _bits(full[k])), k
+        # enqueued only (mode 2) on the handle's stream, which is torch's current one:
+        # torch's later reads are ordered after the gather
+        late = {k: torch.zeros_like(v) for k, v in tens.items()}
+        g.state_device(late, G.F_X | G.F_V | G.F_LINK, wait=False)
+        for k in ("x", "v", "link"):
+            assert np.array_equal(_bits(late[k].cpu().numpy()), _bits(full[k])), k
+        assert not late["status"].any()                     # not requested, untouched
 
 
 def test_requested_field_without_buffer_is_rejected():
@@ -63,5 +70,6 @@ def test_requested_field_without_buffer_is_rejected():
     view = G.sim_state_view(None, None, None, None, None, None, None, None, None)
     rc = G.lib().sim_read_state(g.h, ctypes.byref(view), G.F_X, 0)
     assert rc == G.SIM_EINVAL
+    assert G.lib().sim_read_state(g.h, ctypes.byref(view), G.F_X, 3) == G.SIM_EINVAL   # no such mode
     g.step(10)                                     # the handle stays usable
     assert g.counters()["t"] == 20
