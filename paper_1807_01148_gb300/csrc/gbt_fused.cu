@@ -213,7 +213,10 @@ __device__ __forceinline__ void ph_front(const Dev& d, bool split) {
   // the chunks of the chunk kernel: sorted positions, link and lane ranges
   const int nB = d.ctl->nB;
   const int n_chunks = (nB + kChunkT - 1) / kChunkT;
-  GRID_STRIDE(k, n_chunks) {
+  // chunk k goes to thread T - 1 - k: the last threads of the grid, which have one lane
+  // fewer than the first ones in the lane loop above
+  const int T = gridDim.x * blockDim.x;
+  for (int k = T - 1 - (int)(blockIdx.x * blockDim.x + threadIdx.x); k < n_chunks; k += T) {
     ChunkInfo c;
     c.c0 = chunk_cut(d, k * kChunkT, nB);
     c.c1 = chunk_cut(d, (k + 1) * kChunkT, nB);
