@@ -55,8 +55,8 @@ IMPL_BYTES = {
 # DRAM bytes (read + write) per active vehicle per launch of the plain step kernel
 # (front + chunk), from the ncu capture summarised under profiles/, valid only for the
 # kernel sources it was taken on.
-PROFILED_SRC_SHA = "348ebc9644bba0b5"
-PROFILED_STEP_TRAFFIC = 149.1   # k_front 67.5 + k_chunk 81.6 B per active vehicle (987,466 vehicles)
+PROFILED_SRC_SHA = "3ad9a7957d6f8c8c"
+PROFILED_STEP_TRAFFIC = 149.2   # k_front 67.5 + k_chunk 81.7 B per active vehicle (987,466 vehicles)
 
 
 def kernel_source_sha():
