@@ -448,36 +448,62 @@ def measure_assignment(G, S, torch, iters=2):
 # ---------------------------------------------------------------------------- natural day, queues
 def measure_natural_day(G, S, torch, stream):
     """The metro network with its natural demand (3,000,000 gravity-OD trips, bimodal
-    departures): trip planning on the GPU, then all 172,800 steps of the day from t = 0.
-    Vehicle-steps/s over the stepping (CUDA events), wall time with and without routing,
-    the active count every 30 simulated minutes."""
-    g = G.Sim(S.metro())
+    departures): trip planning on the GPU, then all 172,800 steps of the day from t = 0,
+    in the execution configuration the autotuner picks on a copy advanced to 8 h (the
+    morning peak), and again with the per-step graph.  Vehicle-steps/s over the stepping
+    (CUDA events), wall time with and without routing, the active count every 30
+    simulated minutes."""
+    sc = S.metro()
+    g = G.Sim(sc)
     g.set_stream(stream.cuda_stream)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     g.route()
     torch.cuda.synchronize()
     route_s = time.perf_counter() - t0
+    off, links = g.routes()
+    tune = G.Sim(sc)
+    tune.set_stream(stream.cuda_stream)
+    tune.set_routes(off, links)
+    tune.step(57600)
+    choice = tune.autotune(trial_steps=200)
+    tune.close()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    samples = []
-    step_ms = 0.0
-    t1 = time.perf_counter()
-    for _ in range(48):
-        e0.record(stream)
-        g.step(3600)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        step_ms += e0.elapsed_time(e1)
-        samples.append(int(g.counters()["active"]))
-    wall = time.perf_counter() - t1
+
+    def day(h):
+        samples = []
+        step_ms = 0.0
+        t1 = time.perf_counter()
+        for _ in range(48):
+            e0.record(stream)
+            h.step(3600)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            step_ms += e0.elapsed_time(e1)
+            samples.append(int(h.counters()["active"]))
+        return step_ms, time.perf_counter() - t1, samples
+
+    g.set_exec(**choice)
+    step_ms, wall, samples = day(g)
     c = g.counters()
     g.close()
+    gg = G.Sim(sc)
+    gg.set_stream(stream.cuda_stream)
+    gg.set_routes(off, links)
+    gg.set_exec(mode=0, grid_per_sm=8)
+    graph_ms, _, _ = day(gg)
+    cg = gg.counters()
+    gg.close()
+    assert cg["veh_steps"] == c["veh_steps"] and cg["arrived"] == c["arrived"]
     return {"workload": "metro, 3000000 trips, gravity OD, bimodal departures, GPU-planned routes, 172800 steps "
                         "(24 h at 0.5 s)",
             "value": c["veh_steps"] / (step_ms / 1e3), "unit": UNIT, "vehicle_steps": int(c["veh_steps"]),
             "step_seconds": step_ms / 1e3, "wall_seconds": wall, "routing_seconds": route_s,
             "end_to_end_seconds": wall + route_s, "peak_active_30min_samples": max(samples),
-            "active_every_30min": samples, "arrived": int(c["arrived"]), "departed": int(c["departed"])}
+            "active_every_30min": samples, "arrived": int(c["arrived"]), "departed": int(c["departed"]),
+            "exec": choice, "graph_step_seconds": graph_ms / 1e3,
+            "note": "exec: sim_autotune's pick on a copy at 8 h; graph_step_seconds: the same day with one graph "
+                    "of the step kernels per step (identical vehicle-steps and arrivals)"}
 
 
 def measure_jam(G, S, torch, stream, steps=300):
