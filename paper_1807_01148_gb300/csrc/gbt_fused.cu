@@ -563,13 +563,20 @@ __device__ __forceinline__ void chunk_step(const Dev& d, const ChunkView& V, int
 // true: the chunks the lane-front phase moved to the big-chunk list, by index, and no
 // departures.  S: the block's staging area (dynamic shared memory).  Returns early
 // (error word set) when a staging wait runs out.
-template <bool OUT, bool TYPES, bool BIG, typename SMT>
+// INS_FIRST: the departures before the chunks instead of after them (the persistent
+// launch, where it is faster on sparse networks; the per-step kernel keeps them last,
+// where every block's first chunk would wait for its share of the queue checks).
+template <bool OUT, bool TYPES, bool BIG, typename SMT, bool INS_FIRST = false>
 __device__ __forceinline__ void ph_chunk(const Dev& d, SMT& S) {
   constexpr int CAP = SMT::kCap;
   // the chunk being processed and the next one (taken by thread 0 while the current
   // chunk's copies are in flight), alternating between two slots
   __shared__ int s_k[2], s_cnt;
   __shared__ ChunkInfo s_info[2];
+  // departures (appended after the sorted vehicles; they read only state of step t and
+  // this step's admission bids, complete since the lane-front phase, and write slots and
+  // counts that no chunk touches)
+  if (INS_FIRST && !BIG && d.n_qlinks > 0) ph_insert<OUT, TYPES>(d);
   const int nB = d.ctl->nB;
   const int t = (int)d.ctl->t;
   const unsigned ep = d.ctl->occ_epoch;
@@ -672,9 +679,7 @@ __device__ __forceinline__ void ph_chunk(const Dev& d, SMT& S) {
       chunk_step<false, OUT, TYPES>(d, V, c0, n, t, ep, S.list, &s_cnt);
     }
   }
-  // departures (appended after the sorted vehicles; they read only state of step t and
-  // this step's admission bids, complete since k_front)
-  if (!BIG && d.n_qlinks > 0) ph_insert<OUT, TYPES>(d);
+  if (!INS_FIRST && !BIG && d.n_qlinks > 0) ph_insert<OUT, TYPES>(d);
 }
 
 template <bool OUT, bool TYPES>
@@ -752,7 +757,7 @@ __device__ __forceinline__ void persistent_steps(const Dev& d, GridSync* gs, int
     if (d.acc_u) ph_edge_sample(d);
     ph_front<TYPES>(d, false);   // every chunk stays in the table
     if (!grid_barrier(gs, err, limit)) return;
-    ph_chunk<OUT, TYPES, false>(d, S);
+    ph_chunk<OUT, TYPES, false, ChunkSmem, true>(d, S);
     if (!grid_barrier(gs, err, limit)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) ph_finish(d);
   }
