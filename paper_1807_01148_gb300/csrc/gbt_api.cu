@@ -54,6 +54,7 @@ void launch_compact_routes(const int32_t* roff, const int32_t* rlen, const int32
 void chunk_setup(int blocks_per_sm[8]);
 void front_setup(int blocks_per_sm[2]);
 bool chunk_split_needed(const double* lane_m, int n_links, float vlen_min);
+bool rank_long_needed(double max_len, float vlen_min);
 size_t chunk_table_size(int n_trips);
 int persistent_max_blocks_per_sm(int threads);
 cudaError_t launch_persistent(const Dev& d, GridSync* gs, int blocks, int threads, int n_steps, long long limit,
@@ -97,6 +98,7 @@ struct sim_handle {
   int nn = 0, nl = 0, nt = 0, n_lanes = 0, ncls = 0;
   bool has_stop = false;
   std::vector<double> lane_m;   // lanes x length per link (chunk_split_needed)
+  double max_len = 0.0;         // longest link (rank_long_needed)
   long long launches = 0;    // kernel launches made by sim_step (sim_launch_count)
   size_t graph_nodes = 0, graph_samp_nodes = 0;   // kernels per step of the step graphs
   // host copies
@@ -377,6 +379,7 @@ int create_from_flat(Flat& F, sim_handle** out) {
     r.sig_grn = (uint16_t)(F.ctrl[n] == SIM_CTRL_SIGNAL ? F.grn[n] : 0);
     if (F.ctrl[n] == SIM_CTRL_STOP) h->has_stop = true;
     h->lane_m[e] = (double)F.len[e] * (double)F.lanes[e];
+    h->max_len = std::max(h->max_len, (double)F.len[e]);
   }
   h->lane_base[F.nl] = nlan;
   h->n_lanes = nlan;
@@ -440,6 +443,7 @@ int create_from_flat(Flat& F, sim_handle** out) {
     d.vlen = P.veh_len;
     d.vlen_max = P.veh_len;
     d.chunk_split = chunk_split_needed(h->lane_m.data(), F.nl, P.veh_len) ? 1 : 0;
+    d.rank_long = rank_long_needed(h->max_len, P.veh_len) ? 1 : 0;
     d.s_min = P.s_min;
     d.zone = 2.0f * P.veh_len;
     d.mp = P.mobil_p;
@@ -1436,6 +1440,7 @@ int sim_set_vehicle_types(sim_handle* h, int32_t n_types, const sim_vehicle_type
   d.n_vty = 0;
   d.vlen_max = d.vlen;
   d.chunk_split = chunk_split_needed(h->lane_m.data(), h->nl, d.vlen) ? 1 : 0;
+  d.rank_long = rank_long_needed(h->max_len, d.vlen) ? 1 : 0;
   h->vty_len.clear();
   h->vty_ascale.clear();
   h->vty_vmax.clear();
@@ -1462,8 +1467,9 @@ int sim_set_vehicle_types(sim_handle* h, int32_t n_types, const sim_vehicle_type
   d.vty_vmax = vm;
   d.n_vty = n_types;
   d.vlen_max = *std::max_element(h->vty_len.begin(), h->vty_len.end());
-  d.chunk_split =
-      chunk_split_needed(h->lane_m.data(), h->nl, *std::min_element(h->vty_len.begin(), h->vty_len.end())) ? 1 : 0;
+  const float vmin = *std::min_element(h->vty_len.begin(), h->vty_len.end());
+  d.chunk_split = chunk_split_needed(h->lane_m.data(), h->nl, vmin) ? 1 : 0;
+  d.rank_long = rank_long_needed(h->max_len, vmin) ? 1 : 0;
   return upload_type_params(h);
 }
 

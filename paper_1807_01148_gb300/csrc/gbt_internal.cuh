@@ -227,6 +227,7 @@ struct Dev {
   const int32_t* q_items;
   Ctl* ctl;
   int chunk_split;                 // oversized chunks go to the big-chunk launch
+  int rank_long;                   // long lane segments go to k_rank_long
   int front_grid[2];               // blocks of the lane-front kernel (without / with types)
   int chunk_grid[8];               // blocks of the chunk kernel (plain, outputs, types, both), then of
                                    // the big-chunk kernel (same order)

@@ -35,6 +35,12 @@ __global__ void k_count(Dev d) {
 
 int scan_blocks(int n_lanes) { return (n_lanes + kScanChunk - 1) / kScanChunk; }
 
+// Whether a lane of some link can hold more than kLongSeg vehicles (packed bumper to
+// bumper with the shortest vehicle): only then does the step launch k_rank_long.
+bool rank_long_needed(double max_len, float vlen_min) {
+  return !(vlen_min > 0.0f) || max_len / (double)vlen_min > (double)kLongSeg;
+}
+
 __global__ void k_scan_sum(Dev d) {
   griddep_wait();
   if (step_timed_out(d)) return;
@@ -193,10 +199,13 @@ __global__ void __launch_bounds__(256) k_rank_long(Dev d) {
   }
 }
 
+// SKIP_LONG: segments longer than kLongSeg are left to k_rank_long (launched after it);
+// without, every segment is ranked here (networks whose lanes cannot hold that many).
+template <bool SKIP_LONG>
 __global__ void __launch_bounds__(256, 8) k_rank(Dev d) {
   griddep_wait();
   if (step_timed_out(d)) return;
-  ph_rank<true>(d);
+  ph_rank<SKIP_LONG>(d);
 }
 
 
@@ -671,8 +680,12 @@ void launch_kernel(int k, const Dev& d, int grid, cudaStream_t s) {
     case kKScanFin: launch_pdl(k_scan_fin, nb, kScanThreads, s, d); break;
     case kKScatter: launch_pdl(k_scatter, grid, 256, s, d); break;
     case kKRank:
-      launch_pdl(k_rank, grid, 256, s, d);
-      launch_pdl(k_rank_long, grid, 256, s, d);
+      if (d.rank_long) {
+        launch_pdl(k_rank<true>, grid, 256, s, d);
+        launch_pdl(k_rank_long, grid, 256, s, d);
+      } else {
+        launch_pdl(k_rank<false>, grid, 256, s, d);
+      }
       break;
     case kKFront:
       // the per-edge sample (when enabled) reads the sorted state of step t; its time

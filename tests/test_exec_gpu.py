@@ -77,14 +77,20 @@ def test_autotune_choice_and_cache(G, tmp_path):
 
 def test_launch_count(G):
     # graph execution: the kernels of the step graph per step (two scan kernels, scatter,
-    # rank, long segments, lane fronts, chunks, counters; plus the big-chunk kernel where
-    # most of the road lies on links that hold more vehicles than a staged chunk);
-    # persistent execution: one launch per sim_step call
-    g = G.Sim(S.small_grid(n=5, n_trips=200, steps=200))
+    # rank, lane fronts, chunks, counters; the long-segment rank where a lane can hold
+    # more than 64 vehicles; the big-chunk kernel where most of the road lies on links
+    # that hold more vehicles than a staged chunk); persistent execution: one launch per
+    # sim_step call
+    g = G.Sim(S.small_grid(n=5, n_trips=200, steps=200))   # 200 m links
     g.route()
     n0 = g.launch_count()
     g.step(10)
-    assert g.launch_count() - n0 == 10 * 8
+    assert g.launch_count() - n0 == 10 * 7
+    sm = G.Sim(S.small_metro())                             # links up to about 900 m
+    sm.route()
+    n0 = sm.launch_count()
+    sm.step(3)
+    assert sm.launch_count() - n0 == 3 * 8
     jam = S.jammed_corridors(n_corr=2)
     j = G.Sim(jam)
     j.set_routes(jam["routes"]["offsets"], jam["routes"]["links"])
