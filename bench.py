@@ -56,7 +56,7 @@ IMPL_BYTES = {
 # (front + chunk), from the ncu capture summarised under profiles/, valid only for the
 # kernel sources it was taken on.
 PROFILED_SRC_SHA = "ba26b77c53241bc7"
-PROFILED_STEP_TRAFFIC = 149.4   # k_front 67.5 + k_chunk 82.0 B per active vehicle (987,466 vehicles)
+PROFILED_STEP_TRAFFIC = 149.0   # k_front 67.4 + k_chunk 81.5 B per active vehicle (987,466 vehicles)
 
 
 def kernel_source_sha():
