@@ -55,7 +55,7 @@ IMPL_BYTES = {
 # DRAM bytes (read + write) per active vehicle per launch of the plain step kernel
 # (front + chunk), from the ncu capture summarised under profiles/, valid only for the
 # kernel sources it was taken on.
-PROFILED_SRC_SHA = "ba26b77c53241bc7"
+PROFILED_SRC_SHA = "13600078790119c1"
 PROFILED_STEP_TRAFFIC = 149.0   # k_front 67.4 + k_chunk 81.5 B per active vehicle (987,466 vehicles)
 
 

@@ -20,8 +20,11 @@
 // nominal size T, so the lanes of a link are never split and every read of a lane
 // change or a conflict stays inside the block.  A chunk larger than the staging
 // capacity (a link with more vehicles than that) runs the same code on B and on the
-// per-position scratch arrays in global memory.  Blocks take chunks from an atomic
-// counter until none are left (one resident wave).
+// per-position scratch arrays in global memory, or, on networks where such links carry
+// most of the road, in k_chunk_big (a second launch with a larger staging area).
+// Blocks take chunks from an atomic counter until none are left (one resident wave).
+// The persistent launch at the end of this file runs the same phases (and the
+// rebuild's) between grid barriers.
 //
 // Every decision reads the state at t only (B, the fronts' records, the rear records,
 // the bids of this step) and is written to the state at t+1 (A), so the result does not
